@@ -1,0 +1,40 @@
+"""Philox4x32-10 counter-based generator, written from its published definition
+(Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as easy as 1, 2, 3", SC'11).
+
+TEST INFRASTRUCTURE (part of the oracle; see tracker.py).
+
+One round maps the counter (c0, c1, c2, c3) under key (k0, k1) to
+  (hi(M1*c2) ^ c1 ^ k0,  lo(M1*c2),  hi(M0*c0) ^ c3 ^ k1,  lo(M0*c0))
+with the 32x32 -> 64-bit products split into high and low words; the key is bumped
+by the Weyl constants (W0, W1) between rounds; ten rounds make Philox4x32-10.
+
+Parity unpinned: the published known-answer vectors are not available here, so this
+generator is pinned only by its agreement with the independent CUDA implementation
+and by statistical checks (uniformity of the words), not by reference outputs.
+"""
+from __future__ import annotations
+
+MASK32 = 0xFFFFFFFF
+M0 = 0xD2511F53
+M1 = 0xCD9E8D57
+W0 = 0x9E3779B9
+W1 = 0xBB67AE85
+
+
+def philox4x32_round(c, k):
+    c0, c1, c2, c3 = c
+    k0, k1 = k
+    p0 = M0 * c0
+    p1 = M1 * c2
+    return ((p1 >> 32) ^ c1 ^ k0, p1 & MASK32, (p0 >> 32) ^ c3 ^ k1, p0 & MASK32)
+
+
+def philox4x32_10(ctr, key):
+    """Ten rounds; round r uses the key bumped r times."""
+    c = tuple(int(v) & MASK32 for v in ctr)
+    k0, k1 = int(key[0]) & MASK32, int(key[1]) & MASK32
+    for r in range(10):
+        c = philox4x32_round(c, (k0, k1))
+        k0 = (k0 + W0) & MASK32
+        k1 = (k1 + W1) & MASK32
+    return c
