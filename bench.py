@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the online tensor-subspace tracker on the cine-size workload
+(256 x 256 k-space, R = 32, T = 200 frames, 3 MM iterations per frame, informative line
+sampling at 1/8 after 5 fully sampled frames, lambda_forget 0.95, mu 1e-2).
+
+One step = one pass of the whole per-frame path over the 200-frame sequence, from the
+same initial factors: for each frame, S0 draws the lines from the current subspace
+(score + Philox sampler kernel), the frame kernel runs the MM iterations (S1 ridge
+solve, S2 factor updates), and the image kernel forms X_t. `value` has the k-space
+frames resident in HBM (the kernel reads the drawn rows of each frame); `e2e` goes
+through the same C ABI with host buffers: mask to the host, the acquired rows to the
+device, the image back to the host, every frame.
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s and p50/p99 frame latency at image NRMSE<=1e-4 vs plain per-frame path"
+UNIT = "frames/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tts", choices=["tts", "reference"])
+    ap.add_argument("--frames", type=int, default=None, help="frames per step (default: the workload's T)")
+    ap.add_argument("--launch", default="fused", choices=["fused", "phases"])
+    ap.add_argument("--cluster", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--cpu-sample-frames", type=int, default=8)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int, enabled: bool = True):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"tts_clocks_{os.getpid()}.csv")
+        if enabled:
+            try:
+                self.f = open(self.path, "w")
+                self.proc = subprocess.Popen(["nvidia-smi", f"--id={device_index}", f"--query-gpu={self.Q}",
+                                              "--format=csv,noheader,nounits", "-lms", "200"],
+                                             stdout=self.f, stderr=subprocess.DEVNULL)
+            except Exception:
+                self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------
+# the CUDA path
+# ------------------------------------------------------------------------------------
+def run_tts(args, rank, world):
+    import torch
+
+    from paper_1609_04104_gb300 import inputs, tts
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    tts.load()
+    w = inputs.CINE256
+    T = args.frames or w.T
+    L = inputs.phantom(w, T)
+    Yh = inputs.kspace(w, L)
+    A0, B0 = inputs.init_factors(w.Nx, w.Ny, w.R, w.seed)
+    stream = torch.cuda.Stream()
+    launch = tts.TTS_LAUNCH_FUSED if args.launch == "fused" else tts.TTS_LAUNCH_PHASES
+    trk = tts.Tracker(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, mm_iters=w.mm_iters, central_lines=w.central_lines,
+                      policy=tts.TTS_POLICY_INFORMATIVE, launch=launch, cluster_ctas=args.cluster,
+                      stream_id=rank, cuda_stream=stream)
+    Yd = torch.from_numpy(Yh).to(f"cuda:{dev}")
+    ones = torch.ones(w.Nx, dtype=torch.uint8, device=f"cuda:{dev}")
+    mask = torch.zeros(w.Nx, dtype=torch.uint8, device=f"cuda:{dev}")
+    ring = torch.empty((2, w.Nx, w.Ny), dtype=torch.complex64, device=f"cuda:{dev}")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
+    seed = w.seed + 1000 * rank
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(T)]
+
+    def reset():
+        trk.set_factors(A0, B0)
+        trk.set_stats(0.0, 0.0, 0.0, 0)
+
+    def one_step(record: bool):
+        with torch.cuda.stream(stream):
+            for t in range(T):
+                if record:
+                    ev[t][0].record(stream)
+                if t < w.warmup_frames:
+                    m = ones
+                else:
+                    tts.tts_next_mask(trk.h, w.rate, seed, mask)
+                    m = mask
+                if record:
+                    ev[t][1].record(stream)
+                tts.tts_push_frame(trk.h, Yd[t], m, full_frame=True)
+                if record:
+                    ev[t][2].record(stream)
+                tts.tts_image(trk.h, t, ring[t & 1])
+                if record:
+                    ev[t][3].record(stream)
+
+    for _ in range(args.warmup):
+        reset()
+        one_step(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(dev, enabled=not args.no_clocks)
+    step_ms, lat_ms, kern_ms, samp_ms, img_ms = [], [], [], [], []
+    for _ in range(args.steps):
+        reset()
+        flush.zero_()
+        torch.cuda.synchronize()
+        one_step(True)
+        torch.cuda.synchronize()
+        step_ms.append(ev[0][0].elapsed_time(ev[T - 1][3]))
+        for t in range(T):
+            lat_ms.append(ev[t][0].elapsed_time(ev[t][3]))
+            kern_ms.append(ev[t][1].elapsed_time(ev[t][2]))
+            img_ms.append(ev[t][2].elapsed_time(ev[t][3]))
+            if t >= w.warmup_frames:
+                samp_ms.append(ev[t][0].elapsed_time(ev[t][1]))
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    total_ms = float(np.sum(step_ms))
+    if world > 1:
+        tt = torch.tensor([total_ms], device=f"cuda:{dev}")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    frames_total = T * args.steps * world
+    value = frames_total / (total_ms / 1e3)
+
+    # plain per-frame path (one launch per phase) on the same inputs: image agreement
+    nrmse_plain = None
+    if args.launch == "fused":
+        plain = tts.Tracker(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, mm_iters=w.mm_iters,
+                            central_lines=w.central_lines, launch=tts.TTS_LAUNCH_PHASES, stream_id=rank)
+        plain.set_factors(A0, B0)
+        reset()
+        worst = 0.0
+        for t in range(min(T, 20)):
+            m = np.ones(w.Nx, np.uint8) if t < w.warmup_frames else trk.next_mask(w.rate, seed)
+            y = inputs.observed_rows(Yh[t], m)
+            trk.push_frame(y, m)
+            plain.push_frame(y, m)
+            a, b = trk.image(t), plain.image(t)
+            worst = max(worst, float(np.linalg.norm(a - b) / np.linalg.norm(b)))
+        nrmse_plain = worst
+        plain.close()
+
+    # end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        Yp = torch.from_numpy(Yh).pin_memory().numpy()
+        stage = torch.empty((w.Nx, w.Ny), dtype=torch.complex64).pin_memory().numpy()
+        out = torch.empty((w.Nx, w.Ny), dtype=torch.complex64).pin_memory().numpy()
+        mh = torch.empty(w.Nx, dtype=torch.uint8).pin_memory().numpy()
+        full = np.ones(w.Nx, np.uint8)
+        e2e_s, h2d, d2h = [], 0, 0
+        for it in range(args.warmup + args.steps):
+            reset()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hb = db = 0
+            for t in range(T):
+                if t < w.warmup_frames:
+                    m = full
+                else:
+                    trk.next_mask(w.rate, seed, out=mh)
+                    m = mh
+                    db += w.Nx
+                rows = np.flatnonzero(m)
+                s = len(rows)
+                np.take(Yp[t], rows, axis=0, out=stage[:s])
+                trk.push_frame(stage[:s], m)
+                hb += s * w.Ny * 8 + w.Nx
+                trk.image(t, out=out)
+                db += w.Nx * w.Ny * 8
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                e2e_s.append(time.perf_counter() - t0)
+                h2d, d2h = hb, db
+        e2e = {"value": T * world / float(np.mean(e2e_s)), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    # roofline of the dominant kernel (the frame kernel), FP32 ALU bound
+    kmean = float(np.mean(kern_ms)) * 1e-3
+    Nx, Ny, R, K = w.Nx, w.Ny, w.R, w.mm_iters
+    S = w.k_lines
+    nfull = min(w.warmup_frames, T)
+    flops = []
+    for t in range(T):
+        s = Nx if t < w.warmup_frames else S
+        ingest = 8 * (s * Ny * R + s * Nx * R + Ny * R * R) + s * 5 * Ny * math.log2(Ny)
+        it = 8 * (2 * R * R * s + s * R * R + 2 * Nx * s * R + 2 * Ny * s * R + 2 * Ny * R * R)
+        flops.append(ingest + K * it)
+    flops_per_launch = float(np.mean(flops))
+    sm_mhz = (clk or {}).get("sm_max_mhz", 2070.0) if clk else 2070.0
+    peak_tflops = 152 * 128 * 2 * 2070e6 / 1e12
+    achieved = flops_per_launch / kmean / 1e12
+    bytes_per_launch = float(np.mean([(Nx if t < nfull else S) * Ny * 8 + Nx + 2 * K * (Nx + Ny) * R * 8
+                                      for t in range(T)]))
+    roof = {"bound": "alu", "kernel": "frame_kernel", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops, "traffic": None,
+            "flops_per_launch": flops_per_launch, "algorithmic_bytes_per_launch": bytes_per_launch,
+            "achieved_gbs": bytes_per_launch / kmean / 1e9, "avg_launch_us": kmean * 1e6,
+            "peak_note": "FP32 SIMT peak 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived, not measured)"}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 ridge solve)", "data": "synthetic",
+        "config": {"workload": w.name, "Nx": Nx, "Ny": Ny, "R": R, "T": T, "mm_iters": K,
+                   "lambda_forget": w.lambda_forget, "mu": w.mu, "rate": w.rate, "k_lines": S,
+                   "warmup_frames": w.warmup_frames, "launch": args.launch,
+                   "cluster_ctas": trk.cfg.cluster_ctas or None, "parallelism": f"replicas x{world}",
+                   "l2": "256 MiB buffer written before every timed step"},
+        "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                       "frame_kernel_us": kmean * 1e6, "sampler_us": float(np.mean(samp_ms)) * 1e3 if samp_ms else None,
+                       "image_us": float(np.mean(img_ms)) * 1e3},
+        "nrmse_vs_plain_path": nrmse_plain,
+        "e2e": e2e,
+        "gpu_launches": args.steps * (T + T + max(0, T - w.warmup_frames)) *
+                        (1 if args.launch == "fused" else 1),
+        "roofline": roof,
+        "clocks": clk,
+    }
+    if args.launch == "phases":
+        out["gpu_launches"] = args.steps * (T * tts.tts_launches_per_frame(trk.h) + T + max(0, T - w.warmup_frames))
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, tts_images=True, trk_factory=(trk, Yh, A0, B0))
+    trk.close()
+    return out
+
+
+# ------------------------------------------------------------------------------------
+# the FP64 oracle on the host cores (bounded sample)
+# ------------------------------------------------------------------------------------
+def oracle_sample(n_frames):
+    from oracle import tracker as O
+    from paper_1609_04104_gb300 import inputs
+    w = inputs.CINE256
+    L = inputs.phantom(w, n_frames)
+    Y = inputs.kspace(w, L)
+    A0, B0 = inputs.init_factors(w.Nx, w.Ny, w.R, w.seed)
+    tr = O.Tracker(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, w.mm_iters, A=A0, B=B0)
+    t0 = time.perf_counter()
+    imgs, masks = [], []
+    for t in range(n_frames):
+        m = np.ones(w.Nx, np.uint8) if t < w.warmup_frames else tr.next_mask(w.k_lines, w.central_lines, seed=w.seed)
+        imgs.append(tr.push_frame(inputs.observed_rows(Y[t], m), m))
+        masks.append(m)
+    el = time.perf_counter() - t0
+    return el, imgs, masks, Y, A0, B0
+
+
+def cpu_baseline(args, tts_images=False, trk_factory=None):
+    n = args.cpu_sample_frames
+    el, imgs, masks, Y, A0, B0 = oracle_sample(n)
+    res = {"value": n / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"frames 0-{n - 1} of the 200-frame 256x256 R=32 sequence "
+                     f"({min(n, 5)} fully sampled warm-up frames, the rest at 32/256 lines); "
+                     f"numpy FP64, dense DFT matrices, BLAS on all host cores"}
+    if tts_images and trk_factory is not None:
+        # image agreement of the CUDA path with the oracle on the oracle's masks
+        from paper_1609_04104_gb300 import inputs, tts
+        _, _, A, B = trk_factory
+        w = inputs.CINE256
+        g = tts.Tracker(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, mm_iters=w.mm_iters, central_lines=w.central_lines)
+        g.set_factors(A0, B0)
+        worst = 0.0
+        for t in range(n):
+            g.push_frame(inputs.observed_rows(Y[t], masks[t]), masks[t])
+            x = g.image(t)
+            worst = max(worst, float(np.linalg.norm(x - imgs[t]) / np.linalg.norm(imgs[t])))
+        g.close()
+        res["image_nrmse_vs_oracle"] = worst
+    return res
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from paper_1609_04104_gb300 import inputs
+    w = inputs.CINE256
+    n = args.cpu_sample_frames
+    for _ in range(args.warmup):
+        oracle_sample(min(n, 2))
+    times = [oracle_sample(n)[0] for _ in range(args.steps)]
+    value = n / float(np.mean(times))
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(times)) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "Nx": w.Nx, "Ny": w.Ny, "R": w.R, "T": w.T, "mm_iters": w.mm_iters,
+                   "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"frames 0-{n - 1} of the 256x256 R=32 sequence per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group("nccl")
+    out = run_tts(args, rank, world)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

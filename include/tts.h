@@ -1,0 +1,206 @@
+/*
+ * tts.h - C ABI of the GB300 online tensor-subspace tracker for undersampled dynamic
+ * MRI (Mardani, Giannakis, Ugurbil: "Tracking tensor subspaces with informative random
+ * sampling for real-time MR imaging").
+ *
+ * The tracker follows Alg. 3 of the paper with one coil (single-coil model of §IV,
+ * y = [F(L_t)]_{ij} + v on Omega_t), combined with the randomized line sampler of
+ * Alg. 4 in the phase-encode-line form of §VI-C, run in the order of Alg. 5
+ * (S0 draw lines -> S1 ridge for gamma_t -> S2 factor updates). Each frame runs
+ * mm_iters alternating majorization-minimization iterations; past surrogates are
+ * forgotten with factor lambda_forget.
+ *
+ * Conventions used by every call:
+ *   - complex data are interleaved single-precision pairs (tts_c64, 8 bytes);
+ *   - the image / k-space grid is Nx x Ny, row-major; Nx is the phase-encode axis
+ *     (rows, index i), Ny the readout axis (columns, index j);
+ *   - the DFT is unitary with DC at index 0 and no fftshift:
+ *     (F_N)_{k,n} = N^{-1/2} exp(-2 pi i k n / N), F(X) = F_Nx X F_Ny;
+ *   - a sampling set is a set S of phase-encode lines, Omega = S x [Ny], passed as an
+ *     Nx-byte mask (nonzero = acquired); acquired rows are passed in increasing i;
+ *   - factors A (Nx x R) and B (Ny x R) are row-major (A[i*R + r]).
+ *
+ * Memory: the caller owns every buffer it passes; the library owns all state (factors,
+ * surrogate statistics, workspaces, random-number context). Unless a call says
+ * otherwise, pointers are host pointers; with the TTS_DEVICE_PTRS flag they are
+ * device pointers on the handle's device. Sizes are element counts.
+ *
+ * Errors: every call returns TTS_OK (0) or a negative TTS_E* code; tts_last_error()
+ * returns a thread-local message for the last failure. A failed call leaves the
+ * tracker state unchanged. There is no CPU fallback: without a usable CUDA device,
+ * tts_create* fails with TTS_ECUDA.
+ *
+ * Synchronisation: calls are enqueued on the handle's CUDA stream. Calls that return
+ * data in host memory wait for it; calls given device pointers do not.
+ */
+#ifndef TTS_H
+#define TTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { float re, im; } tts_c64;
+
+enum {
+  TTS_OK = 0,
+  TTS_EINVAL = -1,      /* bad argument (size, rate, mask with no line, NULL pointer) */
+  TTS_ENOMEM = -2,      /* device or host allocation failed */
+  TTS_ECUDA = -3,       /* CUDA runtime error, or no usable device */
+  TTS_ERANGE = -4,      /* frame index that is not the most recent frame */
+  TTS_ENONFINITE = -5,  /* NaN/Inf in an input frame; the frame was not applied */
+  TTS_ETIMEOUT = -6,    /* a bounded device wait ran out */
+  TTS_ESTATE = -7       /* call out of order (e.g. NULL mask before any tts_next_mask) */
+};
+
+#define TTS_DEVICE_PTRS 1
+/* tts_push_frame only: y_rows points to a whole Nx x Ny k-space frame; only the rows
+ * the mask selects are read (a scanner buffer that holds the full Cartesian grid). */
+#define TTS_FULL_FRAME 2
+
+/* Sampling policy of tts_next_mask (S0 of Alg. 5). */
+enum {
+  TTS_POLICY_UNIFORM = 0,      /* all non-central lines equally likely */
+  TTS_POLICY_VARDENS = 1,      /* p_i proportional to d_i^vd_alpha, d_i distance from the centre line (§VI) */
+  TTS_POLICY_INFORMATIVE = 2   /* leverage scores of the current subspace (§V, §VI-C) */
+};
+
+/* Order of the factor updates inside one MM iteration. */
+enum {
+  TTS_UPDATE_GAUSS_SEIDEL = 0, /* gamma -> A -> B with the residual refreshed after A */
+  TTS_UPDATE_JACOBI = 1        /* A and B from the same iterate (Alg. 3 (S2) in parallel) */
+};
+
+/* How a frame's MM iterations are launched. */
+enum {
+  TTS_LAUNCH_FUSED = 0,   /* one thread-block-cluster kernel per frame, phases separated by cluster barriers */
+  TTS_LAUNCH_PHASES = 1   /* one kernel launch per phase (same arithmetic, no cluster) */
+};
+
+typedef struct tts_handle tts_handle;
+
+typedef struct {
+  int Nx, Ny, R;            /* grid and PARAFAC rank; 1 <= Nx, Ny <= 512 with prime factors in {2,3,5}; 1 <= R <= 64 */
+  double lambda_forget;     /* forgetting factor in (0, 1] of the surrogate statistics */
+  double mu;                /* Tykhonov weight (> 0): ridge of gamma, and mu / w on the factors */
+  int mm_iters;             /* MM iterations per frame, >= 1 */
+  int central_lines;        /* lines {-c/2 .. c/2-1} mod Nx always acquired by tts_next_mask */
+  int policy;               /* TTS_POLICY_* */
+  double vd_alpha;          /* exponent of TTS_POLICY_VARDENS (the paper uses -1) */
+  int with_replacement;     /* 1: draw k_lines - c times with replacement (fewer lines possible) */
+  int update;               /* TTS_UPDATE_* */
+  int launch;               /* TTS_LAUNCH_* */
+  int cluster_ctas;         /* CTAs per frame kernel, 1..16; 0 = chosen by the library */
+  uint64_t init_seed;       /* seed of the default CN(0, 1/N) initial factors */
+  uint32_t stream_id;       /* enters the line-draw counter so streams draw independently */
+  void* cuda_stream;        /* cudaStream_t to enqueue on; NULL = a stream the handle creates */
+} tts_config;
+
+/* Fill cfg with defaults: mm_iters 1, central_lines 8, TTS_POLICY_INFORMATIVE, vd_alpha -1,
+ * without replacement, Gauss-Seidel, fused launch, cluster_ctas 0, init_seed 0,
+ * stream_id 0, cuda_stream NULL. */
+void tts_config_init(tts_config* cfg, int Nx, int Ny, int R, double lambda_forget, double mu);
+
+/* Create a tracker (problem (P2) of §III for M = 3: factors A, B of the image-domain
+ * tube subspace, temporal factor gamma_t per frame). The factors start i.i.d.
+ * CN(0, 1/N) from init_seed ("initialize at random", Alg. 3); the surrogate statistics
+ * start at zero. On success *out owns device memory until tts_destroy. */
+int tts_create(int Nx, int Ny, int R, double lambda_forget, double mu, tts_handle** out);
+int tts_create_ex(const tts_config* cfg, tts_handle** out);
+void tts_destroy(tts_handle* h);
+
+/* Replace the factors (warm start, §VI; or resuming from another tracker). A is
+ * Nx x R, B is Ny x R, row-major; host pointers unless TTS_DEVICE_PTRS. The
+ * surrogate statistics and frame counter are left as they are. */
+int tts_set_factors(tts_handle* h, const tts_c64* A, const tts_c64* B, int flags);
+/* Copy the current factors out (same layouts). Waits when given host pointers. */
+int tts_get_factors(tts_handle* h, tts_c64* A, tts_c64* B, int flags);
+/* Surrogate statistics: abar_A, abar_B (forgotten sums of the majorization constants
+ * alpha, §III-A), w (forgotten frame count), and t (frames processed). Host scalars;
+ * tts_get_stats waits for queued work. */
+int tts_get_stats(tts_handle* h, double* abar_A, double* abar_B, double* w, int64_t* t);
+int tts_set_stats(tts_handle* h, double abar_A, double abar_B, double w, int64_t t);
+/* gamma_t of the most recent frame (R values, host). Waits. */
+int tts_get_gamma(tts_handle* h, tts_c64* gamma);
+
+/* Process frame t = (frames processed so far): y_rows holds the acquired k-space rows
+ * (|S| x Ny, rows in increasing i) and line_mask the Nx-byte mask of S. line_mask NULL
+ * uses the mask of the last tts_next_mask (TTS_ESTATE if there is none). Runs
+ * mm_iters MM iterations of Alg. 3 (S1: ridge solve for gamma_t from the masked DFTs
+ * of the rank-one images; S2: majorized updates of A then B against the forgotten
+ * surrogate statistics). With host pointers the frame is checked for NaN/Inf first
+ * (TTS_ENONFINITE, nothing applied); with TTS_DEVICE_PTRS the check runs on the
+ * device, the frame is skipped and tts_synchronize reports TTS_ENONFINITE.
+ * With TTS_FULL_FRAME, y_rows is a full Nx x Ny frame of which only the acquired rows
+ * are read. Asynchronous with TTS_DEVICE_PTRS (the buffers must stay valid until the
+ * stream passes this work). */
+int tts_push_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line_mask, int flags);
+
+/* Reconstructed frame X_t = A[t] diag(gamma_t) B[t]^T (Nx x Ny, row-major). Only the
+ * most recent frame is available: any other t gives TTS_ERANGE. With a host pointer
+ * the call waits for the image. */
+int tts_image(tts_handle* h, int64_t t, tts_c64* out, int flags);
+
+/* S0 of Alg. 5 for the next frame: draw its phase-encode lines under the handle's
+ * policy (informative: scores of §V-B marginalised over readout as in §VI-C,
+ * s_i = (Ny ||abar_i||^2 + R) / (R (Nx + Ny)) with abar the rows of the
+ * column-normalised F_Nx A). k_lines = max(central_lines, round(rate * Nx)); the
+ * central lines are always kept. The draws use Philox4x32-10 keyed by seed with the
+ * counter built from (frame index, stream_id). Writes Nx bytes to line_mask_out
+ * (host, or device with TTS_DEVICE_PTRS) and keeps the mask for tts_push_frame(NULL).
+ * rate must lie in (0, 1]. */
+int tts_next_mask(tts_handle* h, double rate, uint64_t seed, uint8_t* line_mask_out, int flags);
+
+/* The line probabilities p (Nx doubles) that tts_next_mask would draw from now. */
+int tts_line_probs(tts_handle* h, double* p, int flags);
+
+/* The line draw of tts_next_mask on given probabilities p (Nx doubles, sum 1): the
+ * central lines are kept; the other lines carry integer weights q_i = floor(p_i 2^52)
+ * with inclusive prefix sums Q; draw d takes the Philox4x32-10 block at counter
+ * (d, 1, ctr_lo, ctr_hi) under key (seed_lo, seed_hi), u = word0 | word1 << 32,
+ * x = floor(u Q_total / 2^64), and selects the first line with Q > x. Without
+ * replacement duplicates are rejected until k_lines lines are held or
+ * 64 (k_lines - central) draws are spent, then the remaining lines are taken in
+ * decreasing q (lower index first). Runs on the current device, synchronously. Pointers
+ * are host pointers unless TTS_DEVICE_PTRS (then p and out are device pointers and the
+ * call is asynchronous on the default stream). */
+int tts_sample_lines_from_probs(const double* p, int Nx, int k_lines, int central, uint64_t seed,
+                                uint64_t ctr, int with_replacement, uint8_t* out, int flags);
+
+/* Checkpoint: the full tracker state (configuration, factors, gamma, surrogate
+ * statistics, frame counter, last mask) as an opaque host byte string. With buf NULL
+ * *len receives the size needed. tts_load restores it into a handle created with the
+ * same Nx, Ny, R. */
+int tts_save(tts_handle* h, void* buf, size_t* len);
+int tts_load(tts_handle* h, const void* buf, size_t len);
+
+/* Wait for the handle's queued work; returns a deferred device status
+ * (TTS_ENONFINITE for a skipped frame) once, then clears it. */
+int tts_synchronize(tts_handle* h);
+
+/* Kernel launches one tts_push_frame enqueues with the handle's settings. */
+int tts_launches_per_frame(tts_handle* h);
+
+/* The ridge step of (S1) on a given system: solves G gamma = h in FP64 by the LDL^H
+ * factorisation the frame kernel uses (§III-A: gamma = (Phi^H Phi + mu I)^{-1} Phi^H y,
+ * here with G = Phi^H Phi + mu I supplied). G is R x R complex128 (interleaved re, im),
+ * row-major, Hermitian positive definite; only its lower triangle is read. h and gamma
+ * hold R complex128 values. Host pointers; runs on the current device, synchronously. */
+int tts_ridge_solve(const double* G, const double* h, int R, double* gamma);
+
+/* Batched unitary 2D DFT (forward: F_Nx X F_Ny; inverse: conj(F_Nx) X conj(F_Ny))
+ * of `batch` row-major Nx x Ny complex images, device pointers, on `cuda_stream`
+ * (NULL = default stream). in == out is allowed. Nx, Ny in [1, 512] with prime factors
+ * in {2, 3, 5}. Asynchronous. */
+int tts_fft2d(const tts_c64* in, tts_c64* out, int batch, int Nx, int Ny, int inverse, void* cuda_stream);
+
+const char* tts_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TTS_H */

@@ -1,0 +1,233 @@
+// Internal declarations of the GB300 tracker library: complex helpers, the
+// shared-memory Stockham FFT, Philox4x32-10, and the per-handle device workspace.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tts.h"
+
+#define TTS_MAX_N 512
+#define TTS_MAX_R 64
+#define TTS_MAX_CLUSTER 16
+#define TTS_THREADS 256
+
+// ------------------------------------------------------------------------------------
+// complex float / double helpers
+// ------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
+// acc += a * b
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+__device__ __forceinline__ void cfmac(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+}
+__host__ __device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 zmulc(double2 a, double2 b) {  // conj(a) * b
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 zsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+// ------------------------------------------------------------------------------------
+// Mixed-radix Stockham autosort FFT in shared memory.
+//
+// Unnormalised DFT  y_k = sum_n x_n w^{nk},  w = exp(sign * 2 pi i / N),
+// N = 4^a 2^b 3^c 5^d (radices taken in the order 4, 2, 3, 5). Stage with radix p and
+// Ns points already combined: work item j in [0, N/p) reads x[j + q N/p], q < p,
+// twiddles element q by w_{Ns p}^{(j mod Ns) q}, takes a p-point DFT and writes
+// y[(j / Ns) Ns p + (j mod Ns) + q Ns]. The result is in natural order.
+//
+// `W` is a shared-memory table of exp(-2 pi i k / N), k < N (forward sign); the inverse
+// uses its conjugate. Several transforms of length N stored back to back (stride N) are
+// processed together. All threads of the block must call it. Returns the buffer
+// (buf or tmp) that holds the result.
+// ------------------------------------------------------------------------------------
+struct FftPlan {
+  int n;
+  int nrad;
+  int rad[12];
+};
+
+__host__ __device__ inline FftPlan fft_plan(int N) {
+  FftPlan p;
+  p.n = N;
+  p.nrad = 0;
+  int n = N;
+  const int order[4] = {4, 2, 3, 5};
+  for (int o = 0; o < 4; ++o) {
+    while (n % order[o] == 0 && p.nrad < 12) {
+      p.rad[p.nrad++] = order[o];
+      n /= order[o];
+    }
+  }
+  if (n != 1) p.nrad = -1;  // unsupported length
+  return p;
+}
+
+__device__ __forceinline__ float2 tw(const float2* W, int idx, int sign) {
+  float2 w = W[idx];
+  return sign < 0 ? w : make_float2(w.x, -w.y);
+}
+
+__device__ inline float2* fft_smem(float2* buf, float2* tmp, const FftPlan& plan, int batch,
+                                   const float2* W, int sign, int tid, int nthreads) {
+  const int N = plan.n;
+  float2* x = buf;
+  float2* y = tmp;
+  int Ns = 1;
+  for (int s = 0; s < plan.nrad; ++s) {
+    const int p = plan.rad[s];
+    const int Np = N / p;
+    const int step = N / (Ns * p);
+    const int items = batch * Np;
+    for (int it = tid; it < items; it += nthreads) {
+      const int b = it / Np;
+      const int j = it - b * Np;
+      const float2* xb = x + b * N;
+      float2* yb = y + b * N;
+      const int k = j % Ns;
+      float2 v[5];
+      for (int q = 0; q < p; ++q) v[q] = xb[j + q * Np];
+      for (int q = 1; q < p; ++q) v[q] = cmul(v[q], tw(W, (k * q * step) % N, sign));
+      const int base = (j / Ns) * Ns * p + k;
+      if (p == 2) {
+        yb[base] = cadd(v[0], v[1]);
+        yb[base + Ns] = csub(v[0], v[1]);
+      } else if (p == 4) {
+        // w_4 = -i (forward) / +i (inverse)
+        float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+        float2 b0 = cadd(v[1], v[3]), b1 = csub(v[1], v[3]);
+        // b1 * w_4: forward (-i) -> (b1.y, -b1.x); inverse (+i) -> (-b1.y, b1.x)
+        float2 b1w = sign < 0 ? make_float2(b1.y, -b1.x) : make_float2(-b1.y, b1.x);
+        yb[base] = cadd(a0, b0);
+        yb[base + Ns] = cadd(a1, b1w);
+        yb[base + 2 * Ns] = csub(a0, b0);
+        yb[base + 3 * Ns] = csub(a1, b1w);
+      } else {
+        // generic p-point DFT (p = 3, 5) with the table: w_p^{qu} = W[((q u) mod p) N/p]
+        for (int u = 0; u < p; ++u) {
+          float2 acc = v[0];
+          for (int q = 1; q < p; ++q) cfma(acc, v[q], tw(W, ((q * u) % p) * Np, sign));
+          yb[base + u * Ns] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    float2* t = x;
+    x = y;
+    y = t;
+    Ns *= p;
+  }
+  return x;
+}
+
+// ------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): round (c0,c1,c2,c3) ->
+// (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)); key += (W0, W1).
+// ------------------------------------------------------------------------------------
+struct U32x4 {
+  uint32_t v[4];
+};
+
+__host__ __device__ __forceinline__ U32x4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                         uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  for (int r = 0; r < 10; ++r) {
+    uint64_t p0 = (uint64_t)M0 * c0;
+    uint64_t p1 = (uint64_t)M1 * c2;
+    uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    uint32_t n1 = (uint32_t)p1;
+    uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    uint32_t n3 = (uint32_t)p0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += W0;
+    k1 += W1;
+  }
+  U32x4 o;
+  o.v[0] = c0; o.v[1] = c1; o.v[2] = c2; o.v[3] = c3;
+  return o;
+}
+
+#define TTS_PURPOSE_LINES 1u
+#define TTS_PURPOSE_INIT 2u
+
+// ------------------------------------------------------------------------------------
+// Per-handle device workspace and the frame kernel's parameters.
+// ------------------------------------------------------------------------------------
+// scalars (double) kept across frames
+enum { SC_W = 0, SC_ABAR_A = 1, SC_ABAR_B = 2, SC_T = 3, SC_COUNT = 8 };
+// scalars of the frame in flight
+enum { SF_W = 0, SF_RHO = 1, SF_ABAR_A = 2, SF_ABAR_B = 3, SF_ALPHA_A = 4, SF_ALPHA_B = 5, SF_COUNT = 8 };
+
+struct FrameParams {
+  int Nx, Ny, R, K, C;
+  int jacobi;
+  double lf, mu;
+  float isx, isy;                 // 1/sqrt(Nx), 1/sqrt(Ny)
+  FftPlan plan_y;                 // length-Ny transform of the acquired rows
+  float2* A;                      // Nx x R (state)
+  float2* B;                      // Ny x R (state)
+  float2* A0;                     // anchors A[t-1], B[t-1]
+  float2* B0;
+  const uint8_t* mask;            // Nx bytes
+  const float2* yrows;            // |S| x Ny acquired rows (or the full Nx x Ny frame)
+  int full_frame;                 // yrows is the full frame: row m of S is yrows[rows[m]]
+  float2* Yt;                     // |S| x Ny: acquired rows times conj(F_Ny)
+  int* rows;                      // S, increasing
+  int* nrows;                     // |S|
+  float2* AhS[2];                 // (F_Nx A)[S,:]  (|S| x R), ping-pong over iterations
+  float* nA[2];                   // ||a_r||^2
+  float2* MB;                     // B^H B (R x R)
+  float2* P;                      // Yt conj(B) (|S| x R)
+  float2* partA;                  // [C][Nx][R] partial sums of AhS over row slices
+  float* partNA;                  // [C][R]
+  float2* partMB;                 // [C][R][R]
+  float2* partP;                  // [C][Nx][R]
+  float2* Q;                      // [C][Nx][R] per-CTA scratch
+  double* sc;                     // SC_* (persistent)
+  double* sf;                     // SF_* (frame in flight)
+  float2* gamma;                  // R
+  double2* gamma_d;               // R
+  int* status;                    // bit 0: non-finite input frame
+  const float2* Wx;               // exp(-2 pi i k / Nx), k < Nx
+  const float2* Wy;               // exp(-2 pi i k / Ny)
+};
+
+// Steps of one frame: 0 = ingest; then per iteration k: 1 + 4k + {0: solve + A update,
+// 1: reduce A partials, 2: B update, 3: reduce B partials}; the last iteration has no
+// step 3.
+__host__ __device__ inline int frame_num_steps(int K) { return 1 + 4 * K - 1; }
+
+// host-side launchers (tts_kernels.cu)
+int launch_frame(const FrameParams& p, int launch_mode, cudaStream_t st);
+int frame_smem_bytes(const FrameParams& p);
+int launch_image(const float2* A, const float2* B, const float2* gamma, float2* X, int Nx, int Ny, int R,
+                 cudaStream_t st);
+int launch_sampler(const float2* A, int Nx, int Ny, int R, const double* p_in, double* p_out, int policy,
+                   double vd_alpha, int k_lines, int central, uint64_t seed, uint64_t ctr, int with_replacement,
+                   const float2* Wx, uint8_t* mask_out, cudaStream_t st);
+int launch_fft2d(const float2* in, float2* out, int batch, int Nx, int Ny, int inverse, const float2* Wx,
+                 const float2* Wy, float2* scratch, cudaStream_t st);
+int launch_ridge(const double2* G, const double2* h, int R, double2* gamma, cudaStream_t st);
+int launch_init_factors(float2* A, int N, int R, uint64_t seed, uint32_t which, cudaStream_t st);

@@ -1,0 +1,385 @@
+// Image formation, line sampler (S0 of Alg. 5), factor initialisation and the
+// batched unitary 2D DFT.
+#include "tts_internal.cuh"
+
+namespace {
+
+// ------------------------------------------------------------------------------------
+// X = A diag(gamma) B^T  (the image of the most recent frame, cf. §IV-A X_t)
+// 32 x 32 output tile per CTA; A and B rows of the tile staged in shared memory.
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) image_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
+                                                    const float2* __restrict__ gamma, float2* __restrict__ X,
+                                                    int Nx, int Ny, int R) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* sA = (float2*)smem_raw;     // 32 x (R+1), A[i][r] gamma_r
+  float2* sB = sA + 32 * (R + 1);     // 32 x (R+1)
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < 32 * R; e += blockDim.x) {
+    const int ii = e / R, r = e - ii * R;
+    const int i = i0 + ii, j = j0 + ii;
+    sA[ii * (R + 1) + r] = i < Nx ? cmul(A[i * R + r], gamma[r]) : make_float2(0.f, 0.f);
+    sB[ii * (R + 1) + r] = j < Ny ? B[j * R + r] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int jj = tid & 31, ib = tid >> 5;  // each thread: column jj, rows ib, ib+8, ib+16, ib+24
+  float2 acc[4];
+  for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
+  for (int r = 0; r < R; ++r) {
+    const float2 b = sB[jj * (R + 1) + r];
+    for (int q = 0; q < 4; ++q) cfma(acc[q], sA[(ib + 8 * q) * (R + 1) + r], b);
+  }
+  for (int q = 0; q < 4; ++q) {
+    const int i = i0 + ib + 8 * q, j = j0 + jj;
+    if (i < Nx && j < Ny) X[(size_t)i * Ny + j] = acc[q];
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Line sampler, one CTA.
+//  (1) probabilities: informative scores of §V-B marginalised over readout (§VI-C),
+//      p_i = (Ny sum_r |Ahat_ir|^2 / ||ahat_r||^2 + R) / (R (Nx + Ny)), Ahat = F_Nx A
+//      (a zero column counts as uniform); or uniform; or variable density d_i^alpha;
+//      or given.
+//  (2) draw (Alg. 4 on lines): central lines kept; integer weights q = floor(p 2^52)
+//      with inclusive prefix sums over the other lines; Philox4x32-10 draws
+//      x = mulhi(u, Q_total), line = first with Q > x; duplicates rejected; fallback
+//      fill by decreasing q.
+// ------------------------------------------------------------------------------------
+constexpr int SAMPLER_THREADS = 512;
+
+__device__ __forceinline__ int upper_bound_u64(const unsigned long long* Q, int n, unsigned long long x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (Q[mid] > x) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(SAMPLER_THREADS) sampler_kernel(
+    const float2* __restrict__ A, int Nx, int Ny, int R, const double* __restrict__ p_in, double* p_out, int policy,
+    double vd_alpha, int k_lines, int central, unsigned long long seed, unsigned long long ctr, int with_replacement,
+    const float2* __restrict__ Wx, uint8_t* mask_out, int fft_cols) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* p = (double*)smem_raw;                                   // Nx
+  unsigned long long* Q = (unsigned long long*)(p + TTS_MAX_N);    // Nx
+  float* rowacc = (float*)(Q + TTS_MAX_N);                          // Nx
+  float* nrm = rowacc + TTS_MAX_N;                                  // fft_cols
+  int* cand = (int*)(nrm + 64);                                     // Nx
+  uint8_t* mask = (uint8_t*)(cand + TTS_MAX_N);                     // Nx
+  int* misc = (int*)(mask + TTS_MAX_N);                             // 8
+  float2* W = (float2*)(misc + 8);                                  // Nx
+  float2* buf = W + TTS_MAX_N;                                      // 2 x fft_cols x Nx
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+
+  // (1) probabilities
+  if (p_in != nullptr) {
+    for (int i = tid; i < Nx; i += blockDim.x) p[i] = p_in[i];
+  } else if (policy == TTS_POLICY_INFORMATIVE) {
+    for (int i = tid; i < Nx; i += blockDim.x) {
+      W[i] = Wx[i];
+      rowacc[i] = 0.f;
+    }
+    __syncthreads();
+    const FftPlan plan = fft_plan(Nx);
+    for (int r0 = 0; r0 < R; r0 += fft_cols) {
+      const int nc = min(fft_cols, R - r0);
+      for (int e = tid; e < nc * Nx; e += blockDim.x) {
+        const int c = e / Nx, n = e - c * Nx;
+        buf[e] = A[n * R + r0 + c];
+      }
+      __syncthreads();
+      float2* res = fft_smem(buf, buf + fft_cols * Nx, plan, nc, W, -1, tid, blockDim.x);
+      for (int c = warp; c < nc; c += nwarp) {
+        float acc = 0.f;
+        for (int n = lane; n < Nx; n += 32) acc += cabs2(res[c * Nx + n]);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) nrm[c] = acc;
+      }
+      __syncthreads();
+      for (int i = tid; i < Nx; i += blockDim.x) {
+        float acc = rowacc[i];
+        for (int c = 0; c < nc; ++c) acc += nrm[c] > 0.f ? cabs2(res[c * Nx + i]) / nrm[c] : 1.f / (float)Nx;
+        rowacc[i] = acc;
+      }
+      __syncthreads();
+    }
+    const double inv = 1.0 / ((double)R * (double)(Nx + Ny));
+    for (int i = tid; i < Nx; i += blockDim.x) p[i] = ((double)Ny * (double)rowacc[i] + (double)R) * inv;
+  } else {
+    // uniform or variable density: weights then a fixed-order tree normalisation
+    for (int i = tid; i < TTS_MAX_N; i += blockDim.x) {
+      double wgt = 0.0;
+      if (i < Nx) {
+        if (policy == TTS_POLICY_UNIFORM) {
+          wgt = 1.0;
+        } else {
+          double d = (double)min(i, Nx - i);
+          d = d < 1.0 ? 1.0 : d;
+          wgt = vd_alpha == -1.0 ? 1.0 / d : (vd_alpha == -0.5 ? 1.0 / sqrt(d) : pow(d, vd_alpha));
+        }
+      }
+      p[i] = wgt;
+      ((double*)Q)[i] = wgt;
+    }
+    __syncthreads();
+    double* tsum = (double*)Q;
+    for (int half = TTS_MAX_N / 2; half > 0; half >>= 1) {
+      for (int i = tid; i < half; i += blockDim.x) tsum[i] += tsum[i + half];
+      __syncthreads();
+    }
+    const double total = tsum[0];
+    __syncthreads();
+    for (int i = tid; i < Nx; i += blockDim.x) p[i] = p[i] / total;
+  }
+  __syncthreads();
+  if (p_out != nullptr)
+    for (int i = tid; i < Nx; i += blockDim.x) p_out[i] = p[i];
+  if (k_lines <= 0) return;
+
+  // (2) draw. Central set {-c/2 .. c/2-1} mod Nx.
+  const int c = min(central, Nx);
+  for (int i = tid; i < Nx; i += blockDim.x) {
+    const int off = (i + c / 2) % Nx;   // i == (k - c/2) mod Nx  <=>  off == k < c
+    mask[i] = off < c ? 1 : 0;
+  }
+  __syncthreads();
+  // candidate list (non-central lines, increasing) and their integer weights
+  if (warp == 0) {
+    int count = 0;
+    for (int base = 0; base < Nx; base += 32) {
+      const int i = base + lane;
+      const bool on = i < Nx && mask[i] == 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, on);
+      if (on) cand[count + __popc(bal & ((1u << lane) - 1u))] = i;
+      count += __popc(bal);
+    }
+    if (lane == 0) misc[0] = count;
+  }
+  __syncthreads();
+  const int ncand = misc[0];
+  const int kl = min(k_lines, Nx);
+  const int need = kl - c;
+  if (need > 0 && ncand > 0) {
+    const double two52 = 4503599627370496.0;
+    for (int k = tid; k < ncand; k += blockDim.x) {
+      const double v = p[cand[k]];
+      Q[k] = v > 0.0 ? (unsigned long long)floor(v * two52) : 0ull;
+    }
+    __syncthreads();
+    // inclusive prefix sum (Hillis-Steele over Nx <= 512 entries; integer, exact)
+    unsigned long long* T = (unsigned long long*)buf;  // scan scratch (>= Nx u64)
+    for (int off = 1; off < ncand; off <<= 1) {
+      for (int k = tid; k < ncand; k += blockDim.x) T[k] = Q[k] + (k >= off ? Q[k - off] : 0ull);
+      __syncthreads();
+      for (int k = tid; k < ncand; k += blockDim.x) Q[k] = T[k];
+      __syncthreads();
+    }
+    const unsigned long long Qtot = Q[ncand - 1];
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const uint32_t c2 = (uint32_t)ctr, c3 = (uint32_t)(ctr >> 32);
+    if (warp == 0) {
+      int got = 0;
+      if (Qtot > 0) {
+        const int ndraws = with_replacement ? need : 64 * need;
+        for (int base = 0; base < ndraws; base += 32) {
+          if (!with_replacement && got >= need) break;
+          const int d = base + lane;
+          const bool valid = d < ndraws;
+          int line = -1 - lane;
+          if (valid) {
+            const U32x4 w = philox4x32_10((uint32_t)d, TTS_PURPOSE_LINES, c2, c3, k0, k1);
+            const unsigned long long u = (unsigned long long)w.v[0] | ((unsigned long long)w.v[1] << 32);
+            const unsigned long long x = __umul64hi(u, Qtot);
+            line = cand[upper_bound_u64(Q, ncand, x)];
+          }
+          if (with_replacement) {
+            if (valid) mask[line] = 1;
+            __syncwarp();
+            continue;
+          }
+          const unsigned peers = __match_any_sync(0xffffffffu, line);
+          const bool first = (__ffs(peers) - 1) == lane;
+          const bool acc0 = valid && first && mask[line] == 0;
+          const unsigned bal = __ballot_sync(0xffffffffu, acc0);
+          const int rank = __popc(bal & ((1u << lane) - 1u));
+          __syncwarp();
+          if (acc0 && got + rank < need) mask[line] = 1;
+          got = min(need, got + __popc(bal));
+          __syncwarp();
+        }
+      }
+      if (lane == 0) misc[1] = got;
+    }
+    __syncthreads();
+    const int got = misc[1];
+    if (!with_replacement && got < need) {
+      // fill by decreasing q, lower index first on ties (q recomputed from p)
+      const int rest = need - got;
+      for (int k = tid; k < ncand; k += blockDim.x) {
+        const int i = cand[k];
+        if (mask[i]) continue;
+        const double vi = p[i];
+        const unsigned long long qi = vi > 0.0 ? (unsigned long long)floor(vi * two52) : 0ull;
+        int rank = 0;
+        for (int k2 = 0; k2 < ncand; ++k2) {
+          const int i2 = cand[k2];
+          if (mask[i2] || i2 == i) continue;
+          const double v2 = p[i2];
+          const unsigned long long q2 = v2 > 0.0 ? (unsigned long long)floor(v2 * two52) : 0ull;
+          if (q2 > qi || (q2 == qi && i2 < i)) ++rank;
+        }
+        rowacc[i] = rank < rest ? 1.f : 0.f;
+      }
+      __syncthreads();
+      for (int k = tid; k < ncand; k += blockDim.x) {
+        const int i = cand[k];
+        if (!mask[i] && rowacc[i] == 1.f) mask[i] = 2;
+      }
+      __syncthreads();
+      for (int i = tid; i < Nx; i += blockDim.x)
+        if (mask[i] == 2) mask[i] = 1;
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < Nx; i += blockDim.x) mask_out[i] = mask[i];
+}
+
+// ------------------------------------------------------------------------------------
+// CN(0, 1/N) factor entries from Philox4x32-10 and the Box-Muller transform.
+// ------------------------------------------------------------------------------------
+__global__ void init_kernel(float2* A, int N, int R, unsigned long long seed, uint32_t which) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * R) return;
+  const U32x4 w = philox4x32_10((uint32_t)e, TTS_PURPOSE_INIT, which, 0u, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const float u1 = ((float)(w.v[0] >> 8) + 1.0f) * (1.0f / 16777216.0f);  // (0, 1]
+  const float u2 = (float)(w.v[1] >> 8) * (1.0f / 16777216.0f);           // [0, 1)
+  const float rad = sqrtf(-2.0f * logf(u1)) * sqrtf(0.5f / (float)N);
+  float sn, cs;
+  sincospif(2.0f * u2, &sn, &cs);
+  A[e] = make_float2(rad * cs, rad * sn);
+}
+
+// ------------------------------------------------------------------------------------
+// Batched unitary 2D DFT, two passes through global memory: row transforms (length Ny,
+// contiguous), then column transforms (length Nx) on column blocks staged in shared
+// memory.
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) fft_rows_kernel(const float2* __restrict__ in, float2* __restrict__ out,
+                                                       long nrows, int Ny, int rows_per_cta, int sign,
+                                                       const float2* __restrict__ Wy, float scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* W = (float2*)smem_raw;
+  float2* buf = W + Ny;
+  float2* tmp = buf + rows_per_cta * Ny;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < Ny; e += blockDim.x) W[e] = Wy[e];
+  const long r0 = (long)blockIdx.x * rows_per_cta;
+  const int nr = (int)min((long)rows_per_cta, nrows - r0);
+  if (nr <= 0) return;
+  const float4* src = (const float4*)(in + r0 * Ny);
+  float4* b4 = (float4*)buf;
+  const int n2 = nr * Ny;
+  if ((Ny & 1) == 0) {
+    for (int e = tid; e < n2 / 2; e += blockDim.x) b4[e] = src[e];
+  } else {
+    for (int e = tid; e < n2; e += blockDim.x) buf[e] = in[r0 * Ny + e];
+  }
+  __syncthreads();
+  const FftPlan plan = fft_plan(Ny);
+  float2* res = fft_smem(buf, tmp, plan, nr, W, sign, tid, blockDim.x);
+  if ((Ny & 1) == 0) {
+    float4* dst = (float4*)(out + r0 * Ny);
+    const float4* r4 = (const float4*)res;
+    for (int e = tid; e < n2 / 2; e += blockDim.x) {
+      float4 v = r4[e];
+      v.x *= scale; v.y *= scale; v.z *= scale; v.w *= scale;
+      dst[e] = v;
+    }
+  } else {
+    for (int e = tid; e < n2; e += blockDim.x) out[r0 * Ny + e] = cscale(res[e], scale);
+  }
+}
+
+__global__ void __launch_bounds__(256) fft_cols_kernel(float2* data, int Nx, int Ny, int cols_per_cta, int sign,
+                                                       const float2* __restrict__ Wx, float scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* W = (float2*)smem_raw;
+  float2* buf = W + Nx;
+  float2* tmp = buf + cols_per_cta * Nx;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < Nx; e += blockDim.x) W[e] = Wx[e];
+  const int nblk = (Ny + cols_per_cta - 1) / cols_per_cta;
+  const long img = blockIdx.x / nblk;
+  const int j0 = (blockIdx.x % nblk) * cols_per_cta;
+  const int nc = min(cols_per_cta, Ny - j0);
+  float2* base = data + img * (long)Nx * Ny;
+  // stage column block transposed: buf[c * Nx + i] = X[i][j0 + c]
+  for (int e = tid; e < Nx * nc; e += blockDim.x) {
+    const int i = e / nc, c = e - i * nc;
+    buf[c * Nx + i] = base[(long)i * Ny + j0 + c];
+  }
+  __syncthreads();
+  const FftPlan plan = fft_plan(Nx);
+  float2* res = fft_smem(buf, tmp, plan, nc, W, sign, tid, blockDim.x);
+  for (int e = tid; e < Nx * nc; e += blockDim.x) {
+    const int i = e / nc, c = e - i * nc;
+    base[(long)i * Ny + j0 + c] = cscale(res[c * Nx + i], scale);
+  }
+}
+
+}  // namespace
+
+int launch_image(const float2* A, const float2* B, const float2* gamma, float2* X, int Nx, int Ny, int R,
+                 cudaStream_t st) {
+  const int smem = 2 * 32 * (R + 1) * (int)sizeof(float2);
+  dim3 grid((Ny + 31) / 32, (Nx + 31) / 32);
+  image_kernel<<<grid, 256, smem, st>>>(A, B, gamma, X, Nx, Ny, R);
+  return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
+}
+
+int launch_sampler(const float2* A, int Nx, int Ny, int R, const double* p_in, double* p_out, int policy,
+                   double vd_alpha, int k_lines, int central, uint64_t seed, uint64_t ctr, int with_replacement,
+                   const float2* Wx, uint8_t* mask_out, cudaStream_t st) {
+  const int fft_cols = max(1, min(min(R, 64), 8192 / max(Nx, 1)));
+  const size_t smem = sizeof(double) * TTS_MAX_N + sizeof(unsigned long long) * TTS_MAX_N +
+                      sizeof(float) * TTS_MAX_N + sizeof(float) * 64 + sizeof(int) * TTS_MAX_N + TTS_MAX_N +
+                      sizeof(int) * 8 + sizeof(float2) * TTS_MAX_N + sizeof(float2) * 2 * fft_cols * Nx + 64;
+  cudaError_t e = cudaFuncSetAttribute(sampler_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return TTS_ECUDA;
+  sampler_kernel<<<1, SAMPLER_THREADS, smem, st>>>(A, Nx, Ny, R, p_in, p_out, policy, vd_alpha, k_lines, central,
+                                                   (unsigned long long)seed, (unsigned long long)ctr,
+                                                   with_replacement, Wx, mask_out, fft_cols);
+  return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
+}
+
+int launch_init_factors(float2* A, int N, int R, uint64_t seed, uint32_t which, cudaStream_t st) {
+  const int n = N * R;
+  init_kernel<<<(n + 255) / 256, 256, 0, st>>>(A, N, R, (unsigned long long)seed, which);
+  return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
+}
+
+int launch_fft2d(const float2* in, float2* out, int batch, int Nx, int Ny, int inverse, const float2* Wx,
+                 const float2* Wy, float2* scratch, cudaStream_t st) {
+  (void)scratch;
+  const int sign = inverse ? +1 : -1;
+  const long nrows = (long)batch * Nx;
+  const int rows_per_cta = max(1, 4096 / Ny);
+  const size_t smem_r = sizeof(float2) * (Ny + 2 * (size_t)rows_per_cta * Ny);
+  cudaError_t e = cudaFuncSetAttribute(fft_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
+  if (e != cudaSuccess) return TTS_ECUDA;
+  const long grid_r = (nrows + rows_per_cta - 1) / rows_per_cta;
+  fft_rows_kernel<<<(unsigned)grid_r, 256, smem_r, st>>>(in, out, nrows, Ny, rows_per_cta, sign, Wy,
+                                                          1.0f / sqrtf((float)Ny));
+  if (cudaGetLastError() != cudaSuccess) return TTS_ECUDA;
+  const int cols_per_cta = max(1, min(Ny, 4096 / Nx));
+  const size_t smem_c = sizeof(float2) * (Nx + 2 * (size_t)cols_per_cta * Nx);
+  e = cudaFuncSetAttribute(fft_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c);
+  if (e != cudaSuccess) return TTS_ECUDA;
+  const long grid_c = (long)batch * ((Ny + cols_per_cta - 1) / cols_per_cta);
+  fft_cols_kernel<<<(unsigned)grid_c, 256, smem_c, st>>>(out, Nx, Ny, cols_per_cta, sign, Wx, 1.0f / sqrtf((float)Nx));
+  return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
+}

@@ -1,0 +1,335 @@
+"""Python binding of the tracker's C ABI (include/tts.h), argument marshalling only.
+
+Every function here has the name of the C entry point it calls; all arithmetic runs in
+the CUDA kernels of libtts.so. Arrays are passed either as numpy arrays (host memory)
+or as torch CUDA tensors (device memory, TTS_DEVICE_PTRS). There is no CPU fallback:
+loading fails loudly when the library or a CUDA device is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtts.so")
+
+TTS_OK = 0
+TTS_EINVAL, TTS_ENOMEM, TTS_ECUDA, TTS_ERANGE, TTS_ENONFINITE, TTS_ETIMEOUT, TTS_ESTATE = -1, -2, -3, -4, -5, -6, -7
+TTS_DEVICE_PTRS = 1
+TTS_FULL_FRAME = 2
+TTS_POLICY_UNIFORM, TTS_POLICY_VARDENS, TTS_POLICY_INFORMATIVE = 0, 1, 2
+TTS_UPDATE_GAUSS_SEIDEL, TTS_UPDATE_JACOBI = 0, 1
+TTS_LAUNCH_FUSED, TTS_LAUNCH_PHASES = 0, 1
+
+EXPORTS = [
+    "tts_config_init", "tts_create", "tts_create_ex", "tts_destroy", "tts_set_factors", "tts_get_factors",
+    "tts_get_stats", "tts_set_stats", "tts_get_gamma", "tts_push_frame", "tts_image", "tts_next_mask",
+    "tts_line_probs", "tts_sample_lines_from_probs", "tts_save", "tts_load", "tts_synchronize",
+    "tts_launches_per_frame", "tts_ridge_solve", "tts_fft2d", "tts_last_error",
+]
+
+
+class TtsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"tts error {code}: {msg}")
+        self.code = code
+
+
+class tts_config(ctypes.Structure):
+    _fields_ = [
+        ("Nx", ctypes.c_int), ("Ny", ctypes.c_int), ("R", ctypes.c_int),
+        ("lambda_forget", ctypes.c_double), ("mu", ctypes.c_double),
+        ("mm_iters", ctypes.c_int), ("central_lines", ctypes.c_int), ("policy", ctypes.c_int),
+        ("vd_alpha", ctypes.c_double), ("with_replacement", ctypes.c_int), ("update", ctypes.c_int),
+        ("launch", ctypes.c_int), ("cluster_ctas", ctypes.c_int), ("init_seed", ctypes.c_uint64),
+        ("stream_id", ctypes.c_uint32), ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libtts.so (building it first if it is missing) and declare the signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        from . import build as _build
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P, I, D, U64, U32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32
+    H = ctypes.c_void_p
+    sig = {
+        "tts_config_init": (None, [ctypes.POINTER(tts_config), I, I, I, D, D]),
+        "tts_create": (I, [I, I, I, D, D, ctypes.POINTER(H)]),
+        "tts_create_ex": (I, [ctypes.POINTER(tts_config), ctypes.POINTER(H)]),
+        "tts_destroy": (None, [H]),
+        "tts_set_factors": (I, [H, P, P, I]),
+        "tts_get_factors": (I, [H, P, P, I]),
+        "tts_get_stats": (I, [H, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D),
+                              ctypes.POINTER(ctypes.c_int64)]),
+        "tts_set_stats": (I, [H, D, D, D, ctypes.c_int64]),
+        "tts_get_gamma": (I, [H, P]),
+        "tts_push_frame": (I, [H, P, P, I]),
+        "tts_image": (I, [H, ctypes.c_int64, P, I]),
+        "tts_next_mask": (I, [H, D, U64, P, I]),
+        "tts_line_probs": (I, [H, P, I]),
+        "tts_sample_lines_from_probs": (I, [P, I, I, I, U64, U64, I, P, I]),
+        "tts_save": (I, [H, P, ctypes.POINTER(ctypes.c_size_t)]),
+        "tts_load": (I, [H, P, ctypes.c_size_t]),
+        "tts_synchronize": (I, [H]),
+        "tts_launches_per_frame": (I, [H]),
+        "tts_ridge_solve": (I, [P, P, I, P]),
+        "tts_fft2d": (I, [P, P, I, I, I, I, P]),
+        "tts_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise TtsError(rc, tts_last_error())
+    return rc
+
+
+def tts_last_error() -> str:
+    return load().tts_last_error().decode(errors="replace")
+
+
+# --- pointer helpers --------------------------------------------------------------
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype=None):
+    """(address, device_flag) of a numpy array (host) or torch CUDA tensor (device)."""
+    if x is None:
+        return None, 0
+    if _is_torch(x):
+        if not x.is_cuda or not x.is_contiguous():
+            raise ValueError("torch tensors must be contiguous CUDA tensors")
+        return x.data_ptr(), TTS_DEVICE_PTRS
+    if not isinstance(x, np.ndarray) or not x.flags.c_contiguous:
+        raise ValueError("host arrays must be C-contiguous numpy arrays")
+    if dtype is not None and x.dtype != dtype:
+        raise ValueError(f"expected dtype {dtype}, got {x.dtype}")
+    return x.ctypes.data, 0
+
+
+def _flags(*flags):
+    fs = {f for f in flags if f is not None}
+    if len(fs) > 1:
+        raise ValueError("mix of host and device buffers in one call")
+    return fs.pop() if fs else 0
+
+
+# --- the C entry points -------------------------------------------------------------
+
+def tts_config_init(Nx, Ny, R, lambda_forget, mu, **overrides) -> tts_config:
+    cfg = tts_config()
+    load().tts_config_init(ctypes.byref(cfg), Nx, Ny, R, lambda_forget, mu)
+    for k, v in overrides.items():
+        if k == "cuda_stream" and v is not None and not isinstance(v, int):
+            v = v.cuda_stream  # torch.cuda.Stream
+        setattr(cfg, k, v)
+    return cfg
+
+
+def tts_create(Nx, Ny, R, lambda_forget, mu) -> int:
+    h = ctypes.c_void_p()
+    _check(load().tts_create(Nx, Ny, R, lambda_forget, mu, ctypes.byref(h)))
+    return h.value
+
+
+def tts_create_ex(cfg: tts_config) -> int:
+    h = ctypes.c_void_p()
+    _check(load().tts_create_ex(ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def tts_destroy(h) -> None:
+    load().tts_destroy(h)
+
+
+def tts_set_factors(h, A, B) -> None:
+    pa, fa = _ptr(A, np.complex64)
+    pb, fb = _ptr(B, np.complex64)
+    _check(load().tts_set_factors(h, pa, pb, _flags(fa, fb)))
+
+
+def tts_get_factors(h, A, B) -> None:
+    pa, fa = _ptr(A, np.complex64)
+    pb, fb = _ptr(B, np.complex64)
+    _check(load().tts_get_factors(h, pa, pb, _flags(fa, fb)))
+
+
+def tts_get_stats(h) -> dict:
+    a, b, w, t = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    _check(load().tts_get_stats(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(w), ctypes.byref(t)))
+    return dict(abar_A=a.value, abar_B=b.value, w=w.value, t=t.value)
+
+
+def tts_set_stats(h, abar_A, abar_B, w, t) -> None:
+    _check(load().tts_set_stats(h, abar_A, abar_B, w, t))
+
+
+def tts_get_gamma(h, R) -> np.ndarray:
+    g = np.zeros(R, np.complex64)
+    _check(load().tts_get_gamma(h, g.ctypes.data))
+    return g
+
+
+def tts_push_frame(h, y_rows, line_mask=None, full_frame=False) -> None:
+    py, fy = _ptr(y_rows, np.complex64)
+    pm, fm = _ptr(line_mask, np.uint8)
+    flags = _flags(fy, fm if line_mask is not None else None)
+    _check(load().tts_push_frame(h, py, pm, flags | (TTS_FULL_FRAME if full_frame else 0)))
+
+
+def tts_image(h, t, out) -> None:
+    po, fo = _ptr(out, np.complex64)
+    _check(load().tts_image(h, t, po, fo))
+
+
+def tts_next_mask(h, rate, seed, out) -> None:
+    po, fo = _ptr(out, np.uint8)
+    _check(load().tts_next_mask(h, rate, seed, po, fo))
+
+
+def tts_line_probs(h, out) -> None:
+    po, fo = _ptr(out, np.float64)
+    _check(load().tts_line_probs(h, po, fo))
+
+
+def tts_sample_lines_from_probs(p, k_lines, central, seed, ctr, with_replacement=False, out=None):
+    Nx = p.shape[0]
+    if out is None:
+        out = np.zeros(Nx, np.uint8)
+    pp, fp = _ptr(p, np.float64)
+    po, fo = _ptr(out, np.uint8)
+    _check(load().tts_sample_lines_from_probs(pp, Nx, k_lines, central, seed, ctr, int(with_replacement), po,
+                                              _flags(fp, fo)))
+    return out
+
+
+def tts_save(h) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(load().tts_save(h, None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(load().tts_save(h, buf, ctypes.byref(n)))
+    return buf.raw[: n.value]
+
+
+def tts_load(h, blob: bytes) -> None:
+    _check(load().tts_load(h, blob, len(blob)))
+
+
+def tts_synchronize(h) -> None:
+    _check(load().tts_synchronize(h))
+
+
+def tts_launches_per_frame(h) -> int:
+    return _check(load().tts_launches_per_frame(h))
+
+
+def tts_ridge_solve(G: np.ndarray, h: np.ndarray) -> np.ndarray:
+    """FP64 LDL^H solve of G gamma = h on the device (G Hermitian positive definite)."""
+    G = np.ascontiguousarray(G, np.complex128)
+    h = np.ascontiguousarray(h, np.complex128)
+    g = np.zeros(h.shape[0], np.complex128)
+    _check(load().tts_ridge_solve(G.ctypes.data, h.ctypes.data, h.shape[0], g.ctypes.data))
+    return g
+
+
+def tts_fft2d(x, out, inverse=False, stream=None) -> None:
+    """Batched unitary 2D DFT of torch CUDA tensors of shape (batch, Nx, Ny), complex64."""
+    if x.dim() == 2:
+        batch, (Nx, Ny) = 1, x.shape
+    else:
+        batch, Nx, Ny = x.shape
+    s = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(load().tts_fft2d(x.data_ptr(), out.data_ptr(), batch, Nx, Ny, int(inverse), s))
+
+
+class Tracker:
+    """Convenience owner of one tracker handle (same calls as the C ABI)."""
+
+    def __init__(self, Nx, Ny, R, lambda_forget, mu, **cfg):
+        self.Nx, self.Ny, self.R = Nx, Ny, R
+        self.cfg = tts_config_init(Nx, Ny, R, lambda_forget, mu, **cfg)
+        self.h = tts_create_ex(self.cfg)
+
+    def close(self):
+        if self.h:
+            tts_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_factors(self, A, B):
+        tts_set_factors(self.h, np.ascontiguousarray(A, np.complex64) if isinstance(A, np.ndarray) else A,
+                        np.ascontiguousarray(B, np.complex64) if isinstance(B, np.ndarray) else B)
+
+    def factors(self):
+        A = np.zeros((self.Nx, self.R), np.complex64)
+        B = np.zeros((self.Ny, self.R), np.complex64)
+        tts_get_factors(self.h, A, B)
+        return A, B
+
+    def stats(self):
+        return tts_get_stats(self.h)
+
+    def set_stats(self, abar_A, abar_B, w, t):
+        tts_set_stats(self.h, abar_A, abar_B, w, t)
+
+    def gamma(self):
+        return tts_get_gamma(self.h, self.R)
+
+    def push_frame(self, y_rows, line_mask=None):
+        if isinstance(y_rows, np.ndarray):
+            y_rows = np.ascontiguousarray(y_rows, np.complex64)
+        if isinstance(line_mask, np.ndarray):
+            line_mask = np.ascontiguousarray(line_mask, np.uint8)
+        tts_push_frame(self.h, y_rows, line_mask)
+
+    def image(self, t=None, out=None):
+        if t is None:
+            t = self.stats()["t"] - 1
+        if out is None:
+            out = np.zeros((self.Nx, self.Ny), np.complex64)
+        tts_image(self.h, t, out)
+        return out
+
+    def next_mask(self, rate, seed, out=None):
+        if out is None:
+            out = np.zeros(self.Nx, np.uint8)
+        tts_next_mask(self.h, rate, seed, out)
+        return out
+
+    def line_probs(self):
+        p = np.zeros(self.Nx, np.float64)
+        tts_line_probs(self.h, p)
+        return p
+
+    def save(self) -> bytes:
+        return tts_save(self.h)
+
+    def load(self, blob: bytes):
+        tts_load(self.h, blob)
+
+    def synchronize(self):
+        tts_synchronize(self.h)

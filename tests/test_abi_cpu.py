@@ -1,0 +1,77 @@
+"""Host-side checks that need no GPU: the library builds/loads and exports every entry
+point of include/tts.h, argument validation, no CPU fallback, and the input recipe."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1609_04104_gb300 import build, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "tts.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tts_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_library_exports_every_declared_entry_point(lib):
+    names = header_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_1609_04104_gb300 import tts
+    assert sorted(tts.EXPORTS) == names
+
+
+def test_config_validation_runs_before_any_cuda_call():
+    from paper_1609_04104_gb300 import tts
+    for bad in (dict(Nx=7), dict(Nx=0), dict(Ny=600), dict(R=0), dict(R=65), dict(lambda_forget=0.0),
+                dict(lambda_forget=1.5), dict(mu=0.0), dict(mm_iters=0), dict(central_lines=99),
+                dict(policy=7), dict(update=3), dict(launch=4), dict(cluster_ctas=17)):
+        kw = dict(Nx=64, Ny=64, R=8, lambda_forget=0.9, mu=1e-2)
+        kw.update(bad)
+        cfg = tts.tts_config_init(kw.pop("Nx"), kw.pop("Ny"), kw.pop("R"), kw.pop("lambda_forget"), kw.pop("mu"))
+        for k, v in bad.items():
+            setattr(cfg, k, v)
+        with pytest.raises(tts.TtsError) as e:
+            tts.tts_create_ex(cfg)
+        assert e.value.code == tts.TTS_EINVAL, bad
+
+
+def test_no_cpu_fallback_without_a_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1609_04104_gb300 import tts
+    with pytest.raises(tts.TtsError) as e:
+        tts.tts_create(64, 64, 8, 0.9, 1e-2)
+    assert e.value.code == tts.TTS_ECUDA
+    assert "no CPU fallback" in tts.tts_last_error() or "CUDA" in tts.tts_last_error()
+
+
+def test_input_recipe_shapes_and_masks():
+    w = inputs.scaled(inputs.CINE256, T=7)
+    L = inputs.phantom(w)
+    assert L.shape == (7, 256, 256) and L.dtype == np.complex64
+    assert np.all(L.imag == 0) and 0 < L.real.max() < 12
+    Y = inputs.kspace(w, L)
+    # the noise is the only difference between Y and the exact transform
+    d = Y - np.fft.fft2(L, norm="ortho")
+    assert abs(np.std(d) - w.sigma) < 0.05 * w.sigma
+    m = inputs.uniform_line_masks(inputs.SMALL_CINE)
+    assert m.shape == (50, 64) and np.all(m.sum(1) == 16)
+    assert np.all(m[:, inputs.central_set(64, 8)] == 1)
+    assert inputs.CINE256.k_lines == 32 and inputs.SMALL_CINE.k_lines == 16
+    A, B = inputs.init_factors(256, 192, 32)
+    assert A.shape == (256, 32) and B.shape == (192, 32)
+    assert abs(np.mean(np.abs(A) ** 2) - 1 / 256) < 0.1 / 256
