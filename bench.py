@@ -99,6 +99,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate_ranks(ms: float, frames: int, world: int, device: str = "cpu") -> tuple[float, int]:
+    """Replicas: every rank runs its own streams. The job time is the slowest rank's
+    time and the work is the sum of all ranks' frames."""
+    if world <= 1:
+        return ms, frames
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    f = torch.tensor([frames], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(f, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(f.item())
+
+
 # ------------------------------------------------------------------------------------
 # the CUDA path
 # ------------------------------------------------------------------------------------
@@ -175,12 +189,7 @@ def run_tts(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    total_ms = float(np.sum(step_ms))
-    if world > 1:
-        tt = torch.tensor([total_ms], device=f"cuda:{dev}")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    frames_total = T * args.steps * world
+    total_ms, frames_total = aggregate_ranks(float(np.sum(step_ms)), T * args.steps, world, f"cuda:{dev}")
     value = frames_total / (total_ms / 1e3)
 
     # plain per-frame path (one launch per phase) on the same inputs: image agreement

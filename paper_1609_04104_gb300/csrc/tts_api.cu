@@ -133,8 +133,16 @@ int tts_create_ex(const tts_config* cfg, tts_handle** out) {
   h->cfg = *cfg;
   cudaGetDevice(&h->dev);
   const int Nx = cfg->Nx, Ny = cfg->Ny, R = cfg->R;
-  int C = cfg->cluster_ctas;
-  if (C == 0) C = std::max(1, std::min(8, std::min(Nx, Ny) / 8));
+  FrameParams& p = h->fp;
+  memset(&p, 0, sizeof(p));
+  p.Nx = Nx;
+  p.Ny = Ny;
+  p.R = R;
+  if (frame_configure(p, cfg->cluster_ctas) != TTS_OK) {
+    delete h;
+    return fail(TTS_EINVAL, "no cluster size fits the shared memory for these Nx, Ny, R%s");
+  }
+  const int C = p.C;
   h->cfg.cluster_ctas = C;
   if (cfg->cuda_stream) {
     h->stream = (cudaStream_t)cfg->cuda_stream;
@@ -151,8 +159,6 @@ int tts_create_ex(const tts_config* cfg, tts_handle** out) {
     void** ptr;
     size_t bytes;
   };
-  FrameParams& p = h->fp;
-  memset(&p, 0, sizeof(p));
   std::vector<Piece> pieces = {
       {(void**)&p.A, sizeof(float2) * Nx * R},          {(void**)&p.B, sizeof(float2) * Ny * R},
       {(void**)&p.A0, sizeof(float2) * Nx * R},         {(void**)&p.B0, sizeof(float2) * Ny * R},
@@ -163,7 +169,7 @@ int tts_create_ex(const tts_config* cfg, tts_handle** out) {
       {(void**)&p.MB, sizeof(float2) * R * R},          {(void**)&p.P, sizeof(float2) * Nx * R},
       {(void**)&p.partA, sizeof(float2) * C * Nx * R},  {(void**)&p.partNA, sizeof(float) * C * R},
       {(void**)&p.partMB, sizeof(float2) * C * R * R},  {(void**)&p.partP, sizeof(float2) * C * Nx * R},
-      {(void**)&p.Q, sizeof(float2) * C * Nx * R},      {(void**)&p.sc, sizeof(double) * SC_COUNT},
+      {(void**)&p.sc, sizeof(double) * SC_COUNT},
       {(void**)&p.sf, sizeof(double) * SF_COUNT},       {(void**)&p.gamma, sizeof(float2) * R},
       {(void**)&p.gamma_d, sizeof(double2) * R},        {(void**)&p.status, sizeof(int) * (1 + TTS_MAX_CLUSTER)},
       {(void**)&p.Wx, sizeof(float2) * Nx},             {(void**)&p.Wy, sizeof(float2) * Ny},
@@ -184,11 +190,8 @@ int tts_create_ex(const tts_config* cfg, tts_handle** out) {
     *pc.ptr = (char*)h->dmem + off;
     off += align_up(pc.bytes);
   }
-  p.Nx = Nx;
-  p.Ny = Ny;
-  p.R = R;
   p.K = cfg->mm_iters;
-  p.C = C;
+  p.refine = 4;
   p.jacobi = cfg->update == TTS_UPDATE_JACOBI;
   p.lf = cfg->lambda_forget;
   p.mu = cfg->mu;
@@ -342,13 +345,13 @@ int tts_next_mask(tts_handle* h, double rate, uint64_t seed, uint8_t* line_mask_
   if (!(rate > 0.0 && rate <= 1.0)) return fail(TTS_EINVAL, "rate must lie in (0, 1]%s");
   const int Nx = h->cfg.Nx;
   const int k_lines = std::max(h->cfg.central_lines, (int)floor(rate * Nx + 0.5));
+  uint8_t* out2 = (flags & TTS_DEVICE_PTRS) ? line_mask_out : nullptr;
   int rc = launch_sampler(h->fp.A, Nx, h->cfg.Ny, h->cfg.R, nullptr, h->dp, h->cfg.policy, h->cfg.vd_alpha, k_lines,
                           h->cfg.central_lines, seed, draw_counter(h), h->cfg.with_replacement, h->fp.Wx,
-                          h->dmask_next, h->stream);
+                          h->dmask_next, out2, h->stream);
   if (rc != TTS_OK) return fail(rc, "sampler kernel launch failed%s");
   h->have_next = true;
   if (flags & TTS_DEVICE_PTRS) {
-    CK(cudaMemcpyAsync(line_mask_out, h->dmask_next, Nx, cudaMemcpyDeviceToDevice, h->stream));
     h->next_on_host = false;
   } else {
     CK(cudaMemcpyAsync(h->next_host.data(), h->dmask_next, Nx, cudaMemcpyDeviceToHost, h->stream));
@@ -364,7 +367,7 @@ int tts_line_probs(tts_handle* h, double* p, int flags) {
   const int Nx = h->cfg.Nx;
   double* dst = (flags & TTS_DEVICE_PTRS) ? p : h->dp;
   int rc = launch_sampler(h->fp.A, Nx, h->cfg.Ny, h->cfg.R, nullptr, dst, h->cfg.policy, h->cfg.vd_alpha, 0,
-                          h->cfg.central_lines, 0, 0, 0, h->fp.Wx, h->dmask_next, h->stream);
+                          h->cfg.central_lines, 0, 0, 0, h->fp.Wx, h->dmask_next, nullptr, h->stream);
   if (rc != TTS_OK) return fail(rc, "sampler kernel launch failed%s");
   if (!(flags & TTS_DEVICE_PTRS)) {
     CK(cudaMemcpyAsync(p, h->dp, sizeof(double) * Nx, cudaMemcpyDeviceToHost, h->stream));
@@ -380,7 +383,7 @@ int tts_sample_lines_from_probs(const double* p, int Nx, int k_lines, int centra
   if (k_lines < 0 || central < 0 || central > Nx) return fail(TTS_EINVAL, "bad k_lines or central%s");
   if (flags & TTS_DEVICE_PTRS) {
     int rc = launch_sampler(nullptr, Nx, 1, 1, p, nullptr, TTS_POLICY_UNIFORM, -1.0, std::max(k_lines, 1), central,
-                            seed, ctr, with_replacement, nullptr, out, 0);
+                            seed, ctr, with_replacement, nullptr, out, nullptr, 0);
     return rc == TTS_OK ? TTS_OK : fail(rc, "sampler kernel launch failed%s");
   }
   for (int i = 0; i < Nx; ++i)
@@ -397,7 +400,7 @@ int tts_sample_lines_from_probs(const double* p, int Nx, int k_lines, int centra
   e = cudaMemcpy(dp, p, sizeof(double) * Nx, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
     rc = launch_sampler(nullptr, Nx, 1, 1, dp, nullptr, TTS_POLICY_UNIFORM, -1.0, std::max(k_lines, 1), central, seed,
-                        ctr, with_replacement, nullptr, dm, 0);
+                        ctr, with_replacement, nullptr, dm, nullptr, 0);
     if (rc == TTS_OK) e = cudaMemcpy(out, dm, Nx, cudaMemcpyDeviceToHost);
   }
   cudaFree(dp);

@@ -1,23 +1,30 @@
 // Per-frame MM iterations of the online tensor-subspace tracker (Alg. 3 with one coil,
 // S1 ridge step for gamma_t and S2 majorized factor steps, §III-A), GB300 design.
 //
-// Everything a frame needs is computed from small factor-sized quantities, using the
+// Everything a frame needs is computed from factor-sized quantities, using the
 // separability of the 2D DFT with Cartesian line masks (Omega = S x [Ny]):
 //   F(a b^T) = (F_Nx a)(F_Ny b)^T, F unitary and symmetric, so with
 //   Ahat_S = (F_Nx A)[S,:] (|S| x R) and Yt = y_S conj(F_Ny) (|S| x Ny, once per frame):
 //     Phi^H Phi = (Ahat_S^H Ahat_S) .* (B^H B)            (Gram of the masked rank-one DFTs)
 //     Phi^H y   = colsum(conj(Ahat_S) .* P),  P = Yt conj(B)
-//     Theta conj(B)   = conj(F_Nx)[:,S] (P - Ahat_S diag(gamma) (B^H B)^T)
+//     Theta conj(B)    = conj(F_Nx)[:,S] (P - Ahat_S diag(gamma) (B^H B)^T)
 //     Theta'^T conj(A) = Yt^T conj(Ahat'_S) - B diag(gamma) (Ahat'_S^H Ahat'_S)^T
 // with Theta = F^{-1}(P_Omega(y - F(A diag(gamma) B^T))) the back-projected residual of
-// Alg. 3 (S2). These are the same quantities as the masked 2D DFTs of the rank-one
-// images and the inverse 2D DFT of the residual, computed in a different order.
+// Alg. 3 (S2). These are the masked 2D DFTs of the rank-one images and the inverse 2D DFT
+// of the residual, evaluated in a different order.
 //
 // The frame runs as one kernel on a thread-block cluster of C CTAs. CTA c owns a slice of
-// the rows of A and of B; reductions over rows go through per-CTA partial sums that one
-// phase writes and the next phase reduces, each CTA reducing a slice of the entries.
-// Phases are separated by cluster barriers (or run as separate launches).
+// the rows of A and of B and keeps them, with their anchors, in shared memory for the
+// whole frame. Sums over rows go through per-CTA partial sums that one phase writes and
+// the next phase reduces (each CTA a slice of the entries). Quantities indexed by the
+// acquired rows m stream through shared memory in chunks of MC rows, so shared memory
+// stays bounded for any |S|. Phases are separated by cluster barriers (or run as
+// separate launches). The R x R ridge system is solved in FP32 (Gauss-Jordan inverse)
+// with iterative refinement whose residuals are formed in float-float arithmetic, which
+// gives FP64-grade solutions on the FP32 pipes.
 #include <cooperative_groups.h>
+
+#include <algorithm>
 
 #include "tts_internal.cuh"
 
@@ -29,144 +36,283 @@ struct Slice {
   int lo, hi;
 };
 __device__ __forceinline__ Slice slice_of(int n, int parts, int idx) {
-  int per = (n + parts - 1) / parts;
-  int lo = min(n, idx * per);
-  int hi = min(n, lo + per);
-  return {lo, hi};
+  const int per = (n + parts - 1) / parts;
+  const int lo = min(n, idx * per);
+  return {lo, min(n, lo + per)};
 }
 
-struct Smem {
-  float2* Wx;     // Nx
-  float2* Wy;     // Ny
-  int* rows;      // Nx
-  int* misc;      // [0] = |S|, [1] = non-finite flag
-  double2* G;     // R x R (lower triangle)
-  double* invd;   // R
-  double2* z;     // R
-  double2* h;     // R
-  float* fs;      // 8 float scalars of the current step
-  double* ds;     // 8 double scalars of the current step
-  float2* gam;    // R
-  float2* gM;     // R x R  (gM[q*R + r] = gamma_q * M[r][q])
-  float* red;     // TTS_THREADS scratch
-  float2* fbuf;   // 2 x fft_rows x Ny
-  int fft_rows;
+struct SM {
+  float2 *Wx, *Wy;
+  int* rows;
+  int* misc;  // [0] |S|, [1] non-finite flag
+  float* red;
+  float2 *A, *A0, *B, *B0;  // this CTA's rows (rA x R, rB x R)
+  float2 *Gf, *GJa, *GJb;   // R x R
+  float2 *gam, *glo, *h, *rr, *tmpv;  // R each
+  double* ds;               // 8 doubles
+  float* fs;                // 8 floats
+  float2* chunk;
 };
 
-__device__ Smem carve(const FrameParams& p, unsigned char* base, int fft_rows) {
-  Smem s;
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    off = (off + 15) & ~size_t(15);
-    void* q = base + off;
-    off += bytes;
-    return q;
-  };
-  s.G = (double2*)take(sizeof(double2) * p.R * p.R);
-  s.z = (double2*)take(sizeof(double2) * p.R);
-  s.invd = (double*)take(sizeof(double) * p.R);
-  s.h = (double2*)take(sizeof(double2) * p.R);
-  s.fs = (float*)take(sizeof(float) * 8);
-  s.ds = (double*)take(sizeof(double) * 8);
-  s.Wx = (float2*)take(sizeof(float2) * p.Nx);
-  s.Wy = (float2*)take(sizeof(float2) * p.Ny);
-  s.gam = (float2*)take(sizeof(float2) * p.R);
-  s.gM = (float2*)take(sizeof(float2) * p.R * p.R);
-  s.rows = (int*)take(sizeof(int) * p.Nx);
-  s.misc = (int*)take(sizeof(int) * 4);
-  s.red = (float*)take(sizeof(float) * TTS_THREADS);
-  s.fbuf = (float2*)take(sizeof(float2) * 2 * fft_rows * p.Ny);
-  s.fft_rows = fft_rows;
+__device__ SM carve(const FrameParams& p, unsigned char* base) {
+  const FrameLayout& L = p.lay;
+  SM s;
+  s.Wx = (float2*)(base + L.Wx);
+  s.Wy = (float2*)(base + L.Wy);
+  s.rows = (int*)(base + L.rows);
+  s.misc = (int*)(base + L.misc);
+  s.red = (float*)(base + L.red);
+  s.A = (float2*)(base + L.myA);
+  s.A0 = (float2*)(base + L.myA0);
+  s.B = (float2*)(base + L.myB);
+  s.B0 = (float2*)(base + L.myB0);
+  s.Gf = (float2*)(base + L.Gf);
+  s.GJa = (float2*)(base + L.GJa);
+  s.GJb = (float2*)(base + L.GJb);
+  float2* v = (float2*)(base + L.vec);
+  const int R = p.R;
+  s.gam = v;
+  s.glo = v + R;
+  s.h = v + 2 * R;
+  s.rr = v + 3 * R;
+  s.tmpv = v + 4 * R;
+  s.ds = (double*)(v + 6 * R);   // vec region holds 8R float2: 6R for vectors, then 8 doubles + 8 floats
+  s.fs = (float*)(s.ds + 8);
+  s.chunk = (float2*)(base + L.chunk);
   return s;
 }
 
-// ----------------------------------------------------------------------------------
-// step 0: ingest the frame and form the reduced quantities of the first iteration
-// ----------------------------------------------------------------------------------
-__device__ void step_ingest(const FrameParams& p, Smem& sm, int cta) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-  const int Nx = p.Nx, Ny = p.Ny, R = p.R, C = p.C;
-  const int s = sm.misc[0];
-  // acquired rows times conj(F_Ny): inverse row transforms of this CTA's rows of S,
-  // then P[m, :] = Yt[m, :] conj(B) for those rows
-  Slice ms = slice_of(s, C, cta);
-  for (int m0 = ms.lo; m0 < ms.hi; m0 += sm.fft_rows) {
-    const int nr = min(sm.fft_rows, ms.hi - m0);
-    float2* buf = sm.fbuf;
-    float2* tmp = sm.fbuf + sm.fft_rows * Ny;
-    int bad = 0;
-    for (int e = tid; e < nr * Ny; e += blockDim.x) {
-      const int mr = e / Ny;
-      const size_t src = p.full_frame ? (size_t)sm.rows[m0 + mr] * Ny + (e - mr * Ny) : (size_t)m0 * Ny + e;
-      float2 v = p.yrows[src];
-      if (!isfinite(v.x) || !isfinite(v.y)) bad = 1;
-      buf[e] = v;
+// ---------------------------------------------------------------------------------
+// float-float helpers (error-free transformations)
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+// (hi, lo) += v, renormalised
+__device__ __forceinline__ void ff_add_f(float& hi, float& lo, float v) {
+  float s, e;
+  two_sum(hi, v, s, e);
+  e += lo;
+  fast_two_sum(s, e, hi, lo);
+}
+__device__ __forceinline__ void ff_add_ff(float& hi, float& lo, float h2, float l2) {
+  float s, e;
+  two_sum(hi, h2, s, e);
+  e += lo + l2;
+  fast_two_sum(s, e, hi, lo);
+}
+
+// ---------------------------------------------------------------------------------
+// Ridge solve (S1): (G_hi + G_lo) gamma = h_hi + h_lo. FP32 Gauss-Jordan inverse of G_hi
+// (pivots on the diagonal; G is Hermitian positive definite), then `iters` refinement
+// sweeps gamma += Ginv (h - G gamma) with the residual in float-float arithmetic and
+// gamma held as a float-float pair (gam + glo). G_hi in sm.Gf, h_hi in sm.h.
+// ---------------------------------------------------------------------------------
+__device__ void ridge_solve(SM& sm, int R, const float2* Glo, const float2* hlo, int iters) {
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+  const int RR = R * R;
+  for (int e = tid; e < RR; e += nth) sm.GJa[e] = sm.Gf[e];
+  __syncthreads();
+  float2* M = sm.GJa;
+  float2* N = sm.GJb;
+  for (int k = 0; k < R; ++k) {
+    const float2 d = M[k * R + k];
+    const float den = d.x * d.x + d.y * d.y;
+    const float2 piv = make_float2(d.x / den, -d.y / den);
+    for (int e = tid; e < RR; e += nth) {
+      const int i = e / R, j = e - (e / R) * R;
+      float2 v;
+      if (i == k && j == k) {
+        v = piv;
+      } else if (i == k) {
+        v = cmul(M[e], piv);
+      } else if (j == k) {
+        const float2 t = cmul(M[e], piv);
+        v = make_float2(-t.x, -t.y);
+      } else {
+        const float2 rk = cmul(M[k * R + j], piv);
+        v = csub(M[e], cmul(M[i * R + k], rk));
+      }
+      N[e] = v;
     }
-    if (bad) atomicOr(&sm.misc[1], 1);
     __syncthreads();
-    float2* res = fft_smem(buf, tmp, p.plan_y, nr, sm.Wy, +1, tid, blockDim.x);
-    for (int e = tid; e < nr * Ny; e += blockDim.x) {
-      res[e] = cscale(res[e], p.isy);
-      p.Yt[(size_t)m0 * Ny + e] = res[e];
+    float2* t = M;
+    M = N;
+    N = t;
+  }
+  const float2* Gi = M;
+  // gamma_0 = Ginv h (one warp per row)
+  for (int i = warp; i < R; i += nwarp) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int j = lane; j < R; j += 32) cfma(acc, Gi[i * R + j], sm.h[j]);
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) {
+      sm.gam[i] = acc;
+      sm.glo[i] = make_float2(0.f, 0.f);
+    }
+  }
+  __syncthreads();
+  for (int it = 0; it < iters; ++it) {
+    // r = h - G gamma in float-float (warp per row)
+    for (int i = warp; i < R; i += nwarp) {
+      float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+      for (int j = lane; j < R; j += 32) {
+        const float2 g = sm.Gf[i * R + j];
+        const float2 x = sm.gam[j], xl = sm.glo[j];
+        float pp, e;
+        two_prod(g.x, x.x, pp, e);
+        ff_add_ff(rh, rl, pp, e);
+        two_prod(-g.y, x.y, pp, e);
+        ff_add_ff(rh, rl, pp, e);
+        two_prod(g.x, x.y, pp, e);
+        ff_add_ff(ih, il, pp, e);
+        two_prod(g.y, x.x, pp, e);
+        ff_add_ff(ih, il, pp, e);
+        float cr = g.x * xl.x - g.y * xl.y, ci = g.x * xl.y + g.y * xl.x;
+        if (Glo) {
+          const float2 gl = Glo[i * R + j];
+          cr += gl.x * x.x - gl.y * x.y;
+          ci += gl.x * x.y + gl.y * x.x;
+        }
+        ff_add_f(rh, rl, cr);
+        ff_add_f(ih, il, ci);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float a = __shfl_xor_sync(0xffffffffu, rh, o), b = __shfl_xor_sync(0xffffffffu, rl, o);
+        const float c = __shfl_xor_sync(0xffffffffu, ih, o), d = __shfl_xor_sync(0xffffffffu, il, o);
+        ff_add_ff(rh, rl, a, b);
+        ff_add_ff(ih, il, c, d);
+      }
+      if (lane == 0) {
+        float sh = sm.h[i].x, sl = hlo ? hlo[i].x : 0.f;
+        ff_add_ff(sh, sl, -rh, -rl);
+        float th = sm.h[i].y, tl = hlo ? hlo[i].y : 0.f;
+        ff_add_ff(th, tl, -ih, -il);
+        sm.rr[i] = make_float2(sh + sl, th + tl);
+      }
     }
     __syncthreads();
-    for (int mr = warp; mr < nr; mr += nwarp) {
-      const float2* yt = res + mr * Ny;
-      for (int r = lane; r < R; r += 32) {
-        float2 acc = make_float2(0.f, 0.f);
-        for (int j = 0; j < Ny; ++j) cfma(acc, yt[j], cconj(p.B[j * R + r]));
-        p.P[(size_t)(m0 + mr) * R + r] = acc;
+    // gamma += Ginv r
+    for (int i = warp; i < R; i += nwarp) {
+      float2 acc = make_float2(0.f, 0.f);
+      for (int j = lane; j < R; j += 32) cfma(acc, Gi[i * R + j], sm.rr[j]);
+      for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
+      if (lane == 0) {
+        float2 g = sm.gam[i], gl = sm.glo[i];
+        ff_add_ff(g.x, gl.x, acc.x, 0.f);
+        ff_add_ff(g.y, gl.y, acc.y, 0.f);
+        sm.gam[i] = g;
+        sm.glo[i] = gl;
       }
     }
     __syncthreads();
   }
-  __syncthreads();
-  if (tid == 0) p.status[1 + cta] = sm.misc[1];
-  // anchors A[t-1], B[t-1] for this CTA's rows
-  Slice as = slice_of(Nx, C, cta), bs = slice_of(Ny, C, cta);
-  for (int e = as.lo * R + tid; e < as.hi * R; e += blockDim.x) p.A0[e] = p.A[e];
-  for (int e = bs.lo * R + tid; e < bs.hi * R; e += blockDim.x) p.B0[e] = p.B[e];
-  // Ahat_S = (F_Nx A)[S,:] for this CTA's rows of S
+}
+
+// twiddles F[S_m, n] (without 1/sqrt(Nx)) for chunk rows m0.. and the rows lo.. of this CTA
+__device__ __forceinline__ void fill_twiddles(const FrameParams& p, SM& sm, float2* TW, int m0, int mc, int lo,
+                                              int nrows) {
+  for (int e = threadIdx.x; e < mc * nrows; e += blockDim.x) {
+    const int mm = e / nrows, nl = e - mm * nrows;
+    const int idx = (sm.rows[m0 + mm] * (lo + nl)) % p.Nx;
+    TW[e] = sm.Wx[idx];
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// step 0: ingest the frame, form Ahat_S, ||a_r||^2, B^H B and P of the first iteration
+// ---------------------------------------------------------------------------------
+__device__ void step_ingest(const FrameParams& p, SM& sm, int cta) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int Nx = p.Nx, Ny = p.Ny, R = p.R, C = p.C;
+  const int s = sm.misc[0];
+  const Slice ms = slice_of(s, C, cta);
+  // acquired rows times conj(F_Ny) for this CTA's slice of S (inverse row transforms)
+  const int fft_rows = max(1, p.lay.chunk_f2 / (2 * Ny));
+  int bad = 0;
+  for (int m0 = ms.lo; m0 < ms.hi; m0 += fft_rows) {
+    const int nr = min(fft_rows, ms.hi - m0);
+    float2* buf = sm.chunk;
+    float2* tmp = sm.chunk + fft_rows * Ny;
+    for (int e = tid; e < nr * Ny; e += nth) {
+      const int mr = e / Ny;
+      const size_t src = p.full_frame ? (size_t)sm.rows[m0 + mr] * Ny + (e - mr * Ny) : (size_t)m0 * Ny + e;
+      const float2 v = p.yrows[src];
+      if (!isfinite(v.x) || !isfinite(v.y)) bad = 1;
+      buf[e] = v;
+    }
+    __syncthreads();
+    float2* res = fft_smem(buf, tmp, p.plan_y, nr, Ny, sm.Wy, +1, tid, nth);
+    for (int e = tid; e < nr * Ny; e += nth) p.Yt[(size_t)m0 * Ny + e] = cscale(res[e], p.isy);
+    __syncthreads();
+  }
+  if (bad) atomicOr(&sm.misc[1], 1);
+  // anchors A[t-1], B[t-1]
+  for (int e = tid; e < p.rA * R; e += nth) sm.A0[e] = sm.A[e];
+  for (int e = tid; e < p.rB * R; e += nth) sm.B0[e] = sm.B[e];
+  const Slice as = slice_of(Nx, C, cta), bs = slice_of(Ny, C, cta);
+  for (int e = as.lo * R + tid; e < as.hi * R; e += nth) p.A0[e] = p.A[e];
+  for (int e = bs.lo * R + tid; e < bs.hi * R; e += nth) p.B0[e] = p.B[e];
+  // one list of outputs, one per thread and pass: P[m][r] and Ahat_S[m][r] for m in this
+  // CTA's slice of S, (B^H B)[q][r] for q in its slice of [0, R), ||a_r||^2 (last CTA)
+  const Slice qs = slice_of(R, C, cta);
+  const int nm = ms.hi - ms.lo, nq = qs.hi - qs.lo;
+  const int nP = nm * R, nAh = nm * R, nMB = nq * R, nNA = (cta == C - 1) ? R : 0;
+  const int total = nP + nAh + nMB + nNA;
   float2* AhS = p.AhS[0];
-  for (int m = ms.lo + warp; m < ms.hi; m += nwarp) {
-    const int i = sm.rows[m];
-    for (int r = lane; r < R; r += 32) {
+  for (int o = tid; o < total; o += nth) {
+    if (o < nP) {
+      const int m = ms.lo + o / R, r = o % R;
+      const float2* yt = p.Yt + (size_t)m * Ny;
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 4
+      for (int j = 0; j < Ny; ++j) cfma(acc, yt[j], cconj(p.B[j * R + r]));
+      p.P[m * R + r] = acc;
+    } else if (o < nP + nAh) {
+      const int q = o - nP;
+      const int m = ms.lo + q / R, r = q % R;
+      const int i = sm.rows[m];
       float2 acc = make_float2(0.f, 0.f);
       int idx = 0;
+#pragma unroll 4
       for (int n = 0; n < Nx; ++n) {
         cfma(acc, sm.Wx[idx], p.A[n * R + r]);
         idx += i;
         if (idx >= Nx) idx -= Nx;
       }
       AhS[m * R + r] = cscale(acc, p.isx);
-    }
-  }
-  // B^H B, rows q of this CTA's slice of [0, R)
-  Slice qs = slice_of(R, C, cta);
-  for (int q = qs.lo + warp; q < qs.hi; q += nwarp) {
-    for (int r = lane; r < R; r += 32) {
+    } else if (o < nP + nAh + nMB) {
+      const int q2 = o - nP - nAh;
+      const int q = qs.lo + q2 / R, r = q2 % R;
       float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 4
       for (int j = 0; j < Ny; ++j) cfmac(acc, p.B[j * R + q], p.B[j * R + r]);
       p.MB[q * R + r] = acc;
-    }
-  }
-  // ||a_r||^2 (last CTA)
-  if (cta == C - 1) {
-    for (int r0 = 0; r0 < R; r0 += 32) {
-      const int r = r0 + lane;
+    } else {
+      const int r = o - nP - nAh - nMB;
       float acc = 0.f;
-      if (r < R)
-        for (int n = warp; n < Nx; n += nwarp) acc += cabs2(p.A[n * R + r]);
-      sm.red[warp * 32 + lane] = acc;
-      __syncthreads();
-      if (warp == 0 && r < R) {
-        float t = 0.f;
-        for (int w = 0; w < nwarp; ++w) t += sm.red[w * 32 + lane];
-        p.nA[0][r] = t;
-      }
-      __syncthreads();
+      for (int n = 0; n < Nx; ++n) acc += cabs2(p.A[n * R + r]);
+      p.nA[0][r] = acc;
     }
   }
+  __syncthreads();
+  if (tid == 0) p.status[1 + cta] = sm.misc[1];
   if (cta == 0 && tid == 0) {
     const double w = p.lf * p.sc[SC_W] + 1.0;
     p.sf[SF_W] = w;
@@ -174,114 +320,76 @@ __device__ void step_ingest(const FrameParams& p, Smem& sm, int cta) {
     p.sf[SF_ABAR_A] = p.sc[SC_ABAR_A];
     p.sf[SF_ABAR_B] = p.sc[SC_ABAR_B];
     *p.nrows = s;
-    for (int m = 0; m < s; ++m) p.rows[m] = sm.rows[m];
   }
+  if (cta == 0)
+    for (int m = tid; m < s; m += nth) p.rows[m] = sm.rows[m];
 }
 
-// ----------------------------------------------------------------------------------
-// LDL^H factorisation and solve of the R x R ridge system in FP64 (lower triangle of
-// sm.G holds G on entry). On exit sm.z holds gamma.
-// ----------------------------------------------------------------------------------
-__device__ void ldl_solve(const FrameParams& p, Smem& sm, const double2* h) {
-  const int R = p.R, tid = threadIdx.x;
-  const int ntri = R * (R + 1) / 2;
-  if (tid == 0) sm.invd[0] = 1.0 / sm.G[0].x;
-  __syncthreads();
-  for (int k = 0; k < R - 1; ++k) {
-    // update G[i][j] -= G[i][k] conj(G[j][k]) / d_k for k < j <= i
-    for (int e = tid; e < ntri; e += blockDim.x) {
-      // e -> (i, j) with j <= i: i = floor((sqrt(8e+1)-1)/2)
-      int i = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
-      while ((i + 1) * (i + 2) / 2 <= e) ++i;
-      while (i * (i + 1) / 2 > e) --i;
-      const int j = e - i * (i + 1) / 2;
-      if (j <= k) continue;
-      const double2 lik = sm.G[i * R + k], ljk = sm.G[j * R + k];
-      const double inv = sm.invd[k];
-      double2 upd = zmul(lik, make_double2(ljk.x, -ljk.y));
-      double2 g = sm.G[i * R + j];
-      g.x -= upd.x * inv;
-      g.y -= upd.y * inv;
-      if (i == j) g.y = 0.0;
-      sm.G[i * R + j] = g;
-      if (i == k + 1 && j == k + 1) sm.invd[k + 1] = 1.0 / g.x;
-    }
-    __syncthreads();
-  }
-  // solve L D L^H gamma = h with L[i][k] = G[i][k] / d_k (one warp)
-  if (tid < 32) {
-    const int lane = tid;
-    for (int i = lane; i < R; i += 32) sm.z[i] = h[i];
-    __syncwarp();
-    for (int k = 0; k < R; ++k) {
-      const double2 zk = sm.z[k];
-      for (int i = k + 1 + lane; i < R; i += 32) {
-        double2 l = sm.G[i * R + k];
-        double2 t = zmul(l, zk);
-        sm.z[i].x -= t.x * sm.invd[k];
-        sm.z[i].y -= t.y * sm.invd[k];
-      }
-      __syncwarp();
-    }
-    for (int i = lane; i < R; i += 32) {
-      sm.z[i].x *= sm.invd[i];
-      sm.z[i].y *= sm.invd[i];
-    }
-    __syncwarp();
-    for (int k = R - 1; k >= 0; --k) {
-      const double2 gk = sm.z[k];
-      for (int i = lane; i < k; i += 32) {
-        double2 l = sm.G[k * R + i];  // L[k][i] d_i
-        double2 t = zmulc(l, gk);     // conj(L[k][i] d_i) gamma_k
-        sm.z[i].x -= t.x * sm.invd[i];
-        sm.z[i].y -= t.y * sm.invd[i];
-      }
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-}
-
-// ----------------------------------------------------------------------------------
-// step "A": ridge solve for gamma (S1), then the majorized A step (S2) on this CTA's
-// rows, then partial sums of Ahat'_S and ||a'_r||^2 over those rows
-// ----------------------------------------------------------------------------------
-__device__ void step_solve_A(const FrameParams& p, Smem& sm, int cta, int k) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-  const int Nx = p.Nx, R = p.R, C = p.C;
+// ---------------------------------------------------------------------------------
+// step A: ridge solve for gamma (S1), majorized A step (S2) on this CTA's rows, then the
+// partial sums of Ahat'_S and ||a'_r||^2 over those rows
+// ---------------------------------------------------------------------------------
+__device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int Nx = p.Nx, R = p.R, C = p.C, MC = p.MC;
   const int s = sm.misc[0];
   const float2* AhS = p.AhS[k & 1];
-  // Gram of the masked rank-one DFTs and the right-hand side
-  const int ntri = R * (R + 1) / 2;
-  for (int e = tid; e < ntri; e += blockDim.x) {
-    int i = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
-    while ((i + 1) * (i + 2) / 2 <= e) ++i;
-    while (i * (i + 1) / 2 > e) --i;
-    const int j = e - i * (i + 1) / 2;
-    float2 acc = make_float2(0.f, 0.f);
-    for (int m = 0; m < s; ++m) cfmac(acc, AhS[m * R + i], AhS[m * R + j]);
-    const float2 g = cmul(acc, p.MB[i * R + j]);
-    double2 gd = make_double2((double)g.x, (double)g.y);
-    if (i == j) {
-      gd.x += p.mu;
-      gd.y = 0.0;
+  const Slice as = slice_of(Nx, C, cta);
+  const int na = as.hi - as.lo;
+  float2* AH = sm.chunk;                 // MC x R
+  float2* PC = AH + MC * R;              // MC x R
+  float2* QC = PC + MC * R;              // MC x R
+  float2* TW = QC + MC * R;              // MC x na
+  const int RR = R * R;
+  // Gram of the masked rank-one DFTs (all R x R entries) and the right-hand side
+  float2 g[TTS_MAX_OWN], hacc = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int o = 0; o < TTS_MAX_OWN; ++o) g[o] = make_float2(0.f, 0.f);
+  for (int m0 = 0; m0 < s; m0 += MC) {
+    const int mc = min(MC, s - m0);
+    for (int e = tid; e < mc * R; e += nth) {
+      AH[e] = AhS[m0 * R + e];
+      PC[e] = p.P[m0 * R + e];
     }
-    sm.G[i * R + j] = gd;
+    __syncthreads();
+#pragma unroll
+    for (int o = 0; o < TTS_MAX_OWN; ++o) {
+      const int e = tid + o * nth;
+      if (e < RR) {
+        const int i = e / R, j = e - (e / R) * R;
+        float2 acc = g[o];
+        for (int mm = 0; mm < mc; ++mm) cfmac(acc, AH[mm * R + i], AH[mm * R + j]);
+        g[o] = acc;
+      }
+    }
+    if (tid < R)
+      for (int mm = 0; mm < mc; ++mm) cfmac(hacc, AH[mm * R + tid], PC[mm * R + tid]);
+    __syncthreads();
   }
-  double2* h = sm.h;
-  for (int r = tid; r < R; r += blockDim.x) {
-    float2 acc = make_float2(0.f, 0.f);
-    for (int m = 0; m < s; ++m) cfmac(acc, AhS[m * R + r], p.P[m * R + r]);
-    h[r] = make_double2((double)acc.x, (double)acc.y);
+  const float fmu = (float)p.mu;
+#pragma unroll
+  for (int o = 0; o < TTS_MAX_OWN; ++o) {
+    const int e = tid + o * nth;
+    if (e < RR) {
+      const int i = e / R, j = e - (e / R) * R;
+      float2 v = cmul(g[o], p.MB[e]);
+      if (i == j) v = make_float2(v.x + fmu, 0.f);
+      sm.Gf[e] = v;
+    }
   }
+  if (tid < R) sm.h[tid] = hacc;
   __syncthreads();
-  ldl_solve(p, sm, h);
-  // gamma, alpha_A = sum |gamma_r|^2 ||b_r||^2 + rho and the step coefficients (one
-  // thread: FP64 is scarce on this part)
+  ridge_solve(sm, R, nullptr, nullptr, p.refine);
+  // alpha_A = sum |gamma_r|^2 ||b_r||^2 + rho and the step coefficients (one thread:
+  // FP64 is scarce on this part)
   if (tid == 0) {
     const double rho = p.sf[SF_RHO], abar = p.sf[SF_ABAR_A];
     double alpha = rho;
-    for (int r = 0; r < R; ++r) alpha += (sm.z[r].x * sm.z[r].x + sm.z[r].y * sm.z[r].y) * (double)p.MB[r * R + r].x;
+    for (int r = 0; r < R; ++r) {
+      const double gx = (double)sm.gam[r].x + (double)sm.glo[r].x;
+      const double gy = (double)sm.gam[r].y + (double)sm.glo[r].y;
+      alpha += (gx * gx + gy * gy) * (double)p.MB[r * R + r].x;
+    }
     const double den = p.lf * abar + alpha;
     sm.ds[0] = alpha;
     sm.fs[0] = (float)(p.lf * abar / den);
@@ -290,86 +398,97 @@ __device__ void step_solve_A(const FrameParams& p, Smem& sm, int cta, int k) {
     sm.fs[3] = (float)rho;
     if (cta == 0) p.sf[SF_ALPHA_A] = alpha;
   }
-  for (int r = tid; r < R; r += blockDim.x) {
-    sm.gam[r] = make_float2((float)sm.z[r].x, (float)sm.z[r].y);
-    if (cta == 0) {
-      p.gamma_d[r] = sm.z[r];
+  if (cta == 0)
+    for (int r = tid; r < R; r += nth) {
       p.gamma[r] = sm.gam[r];
+      p.gamma_d[r] = make_double2((double)sm.gam[r].x + (double)sm.glo[r].x,
+                                  (double)sm.gam[r].y + (double)sm.glo[r].y);
     }
-  }
-  __syncthreads();
   // gM[q][r] = gamma_q (B^H B)[r][q]
-  for (int e = tid; e < R * R; e += blockDim.x) {
+  float2* gM = sm.GJa;
+  for (int e = tid; e < RR; e += nth) {
     const int q = e / R, r = e - q * R;
-    sm.gM[e] = cmul(sm.gam[q], p.MB[r * R + q]);
+    gM[e] = cmul(sm.gam[q], p.MB[r * R + q]);
   }
   __syncthreads();
-  // Q = P - Ahat_S diag(gamma) (B^H B)^T  (this CTA's copy)
-  float2* Q = p.Q + (size_t)cta * Nx * R;
-  for (int m = warp; m < s; m += nwarp) {
-    for (int r = lane; r < R; r += 32) {
-      float2 acc = p.P[m * R + r];
-      for (int q = 0; q < R; ++q) {
-        const float2 t = cmul(AhS[m * R + q], sm.gM[q * R + r]);
-        acc = csub(acc, t);
-      }
-      Q[m * R + r] = acc;
+  // Theta conj(B) on this CTA's rows: T[n][r] = sum_m conj(F[S_m, n]) Q[m][r],
+  // Q = P - Ahat_S diag(gamma) (B^H B)^T, accumulated over chunks of m
+  float2 t[TTS_MAX_OWN];
+#pragma unroll
+  for (int o = 0; o < TTS_MAX_OWN; ++o) t[o] = make_float2(0.f, 0.f);
+  const int NO = na * R;
+  for (int m0 = 0; m0 < s; m0 += MC) {
+    const int mc = min(MC, s - m0);
+    for (int e = tid; e < mc * R; e += nth) {
+      AH[e] = AhS[m0 * R + e];
+      PC[e] = p.P[m0 * R + e];
     }
-  }
-  __syncthreads();
-  // A step on this CTA's rows: grad = rho A - (conj(F)[:,S] Q) diag(conj gamma)
-  const float c0 = sm.fs[0], c1 = sm.fs[1], c2 = sm.fs[2], frho = sm.fs[3];
-  Slice as = slice_of(Nx, C, cta);
-  for (int n = as.lo + warp; n < as.hi; n += nwarp) {
-    for (int r = lane; r < R; r += 32) {
-      float2 t = make_float2(0.f, 0.f);
-      int idx = 0;
-      for (int m = 0; m < s; ++m) {
-        const int i = sm.rows[m];
-        idx = (int)(((long long)i * n) % Nx);
-        cfmac(t, sm.Wx[idx], Q[m * R + r]);
+    fill_twiddles(p, sm, TW, m0, mc, as.lo, na);
+    __syncthreads();
+    for (int e = tid; e < mc * R; e += nth) {
+      const int mm = e / R, r = e - mm * R;
+      float2 acc = PC[e];
+      for (int q = 0; q < R; ++q) acc = csub(acc, cmul(AH[mm * R + q], gM[q * R + r]));
+      QC[e] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int o = 0; o < TTS_MAX_OWN; ++o) {
+      const int e = tid + o * nth;
+      if (e < NO) {
+        const int nl = e / R, r = e - (e / R) * R;
+        float2 acc = t[o];
+        for (int mm = 0; mm < mc; ++mm) cfmac(acc, TW[mm * na + nl], QC[mm * R + r]);
+        t[o] = acc;
       }
-      t = cscale(t, p.isx);
-      const float2 a = p.A[n * R + r];
-      const float2 grad = csub(cscale(a, frho), cmul(t, cconj(sm.gam[r])));
-      const float2 a0 = p.A0[n * R + r];
+    }
+    __syncthreads();
+  }
+  // A step: grad = rho A - T diag(conj gamma); A <- c0 A0 + c1 A - c2 grad
+  const float c0 = sm.fs[0], c1 = sm.fs[1], c2 = sm.fs[2], frho = sm.fs[3];
+#pragma unroll
+  for (int o = 0; o < TTS_MAX_OWN; ++o) {
+    const int e = tid + o * nth;
+    if (e < NO) {
+      const int r = e - (e / R) * R;
+      const float2 a = sm.A[e], a0 = sm.A0[e];
+      const float2 tt = cscale(t[o], p.isx);
+      const float2 grad = csub(cscale(a, frho), cmul(tt, cconj(sm.gam[r])));
       float2 an;
       an.x = c0 * a0.x + c1 * a.x - c2 * grad.x;
       an.y = c0 * a0.y + c1 * a.y - c2 * grad.y;
-      p.A[n * R + r] = an;
+      sm.A[e] = an;
+      p.A[as.lo * R + e] = an;
     }
   }
   __syncthreads();
-  // partial sums over this CTA's rows: Ahat'_S and ||a'_r||^2
+  // partial sums over this CTA's rows: Ahat'_S[m][r] and ||a'_r||^2
   float2* part = p.partA + (size_t)cta * Nx * R;
-  for (int m = warp; m < s; m += nwarp) {
-    const int i = sm.rows[m];
-    for (int r = lane; r < R; r += 32) {
+  for (int m0 = 0; m0 < s; m0 += MC) {
+    const int mc = min(MC, s - m0);
+    fill_twiddles(p, sm, TW, m0, mc, as.lo, na);
+    __syncthreads();
+    for (int e = tid; e < mc * R; e += nth) {
+      const int mm = e / R, r = e - mm * R;
       float2 acc = make_float2(0.f, 0.f);
-      int idx = (int)(((long long)i * as.lo) % Nx);
-      for (int n = as.lo; n < as.hi; ++n) {
-        cfma(acc, sm.Wx[idx], p.A[n * R + r]);
-        idx += i;
-        if (idx >= Nx) idx -= Nx;
-      }
-      part[m * R + r] = cscale(acc, p.isx);
+      for (int nl = 0; nl < na; ++nl) cfma(acc, TW[mm * na + nl], sm.A[nl * R + r]);
+      part[(m0 + mm) * R + r] = cscale(acc, p.isx);
     }
+    __syncthreads();
   }
-  if (warp == 0) {
-    for (int r = lane; r < R; r += 32) {
-      float acc = 0.f;
-      for (int n = as.lo; n < as.hi; ++n) acc += cabs2(p.A[n * R + r]);
-      p.partNA[cta * R + r] = acc;
-    }
+  for (int r = tid; r < R; r += nth) {
+    float acc = 0.f;
+    for (int nl = 0; nl < na; ++nl) acc += cabs2(sm.A[nl * R + r]);
+    p.partNA[cta * R + r] = acc;
   }
 }
 
-// reduce the per-CTA partials of Ahat'_S and ||a'||^2 (this CTA's slice of entries)
-__device__ void step_reduce_A(const FrameParams& p, Smem& sm, int cta, int k) {
+// reduce the per-CTA partials of Ahat'_S and ||a'||^2 (this CTA's slice of the entries)
+__device__ void step_reduce_A(const FrameParams& p, SM& sm, int cta, int k) {
   const int R = p.R, C = p.C, Nx = p.Nx;
   const int s = sm.misc[0];
   const int E = s * R + R;
-  Slice es = slice_of(E, C, cta);
+  const Slice es = slice_of(E, C, cta);
   float2* out = p.AhS[(k + 1) & 1];
   float* nout = p.nA[(k + 1) & 1];
   for (int e = es.lo + threadIdx.x; e < es.hi; e += blockDim.x) {
@@ -386,31 +505,72 @@ __device__ void step_reduce_A(const FrameParams& p, Smem& sm, int cta, int k) {
   }
 }
 
-// ----------------------------------------------------------------------------------
-// step "B": majorized B step (S2) on this CTA's rows, then partials of B^H B and P
-// ----------------------------------------------------------------------------------
-__device__ void step_B(const FrameParams& p, Smem& sm, int cta, int k, bool last) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-  const int Nx = p.Nx, Ny = p.Ny, R = p.R, C = p.C;
+// ---------------------------------------------------------------------------------
+// step B: majorized B step (S2) on this CTA's rows, then partials of B^H B and P
+// ---------------------------------------------------------------------------------
+__device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int Nx = p.Nx, Ny = p.Ny, R = p.R, C = p.C, MC = p.MC;
   const int s = sm.misc[0];
   const int src = p.jacobi ? (k & 1) : ((k + 1) & 1);
   const float2* Ah = p.AhS[src];
   const float* nA = p.nA[src];
-  for (int r = tid; r < R; r += blockDim.x) sm.gam[r] = p.gamma[r];
-  __syncthreads();
-  // gM[q][r] = gamma_q (Ahat^H Ahat)[r][q]
-  for (int e = tid; e < R * R; e += blockDim.x) {
-    const int q = e / R, r = e - q * R;
-    float2 acc = make_float2(0.f, 0.f);
-    for (int m = 0; m < s; ++m) cfmac(acc, Ah[m * R + r], Ah[m * R + q]);
-    sm.gM[e] = cmul(sm.gam[q], acc);
+  const Slice bs = slice_of(Ny, C, cta);
+  const int nb = bs.hi - bs.lo;
+  float2* AH = sm.chunk;                 // MC x R
+  float2* YB = AH + MC * R;              // MC x nb
+  const int RR = R * R;
+  for (int r = tid; r < R; r += nth) sm.gam[r] = p.gamma[r];
+  // MA = Ahat^H Ahat (thread-owned entries) and U[j][r] = sum_m Yt[m][j] conj(Ahat[m][r])
+  float2 ma[TTS_MAX_OWN], u[TTS_MAX_OWN];
+#pragma unroll
+  for (int o = 0; o < TTS_MAX_OWN; ++o) {
+    ma[o] = make_float2(0.f, 0.f);
+    u[o] = make_float2(0.f, 0.f);
+  }
+  const int NO = nb * R;
+  for (int m0 = 0; m0 < s; m0 += MC) {
+    const int mc = min(MC, s - m0);
+    for (int e = tid; e < mc * R; e += nth) AH[e] = Ah[m0 * R + e];
+    for (int e = tid; e < mc * nb; e += nth) {
+      const int mm = e / nb, jl = e - mm * nb;
+      YB[e] = p.Yt[(size_t)(m0 + mm) * Ny + bs.lo + jl];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int o = 0; o < TTS_MAX_OWN; ++o) {
+      const int e = tid + o * nth;
+      if (e < RR) {
+        const int r = e / R, q = e - (e / R) * R;
+        float2 acc = ma[o];
+        for (int mm = 0; mm < mc; ++mm) cfmac(acc, AH[mm * R + r], AH[mm * R + q]);
+        ma[o] = acc;
+      }
+      if (e < NO) {
+        const int jl = e / R, r = e - (e / R) * R;
+        float2 acc = u[o];
+        for (int mm = 0; mm < mc; ++mm) cfmac(acc, AH[mm * R + r], YB[mm * nb + jl]);
+        u[o] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  // gMA[q][r] = gamma_q MA[r][q]
+  float2* gMA = sm.GJa;
+#pragma unroll
+  for (int o = 0; o < TTS_MAX_OWN; ++o) {
+    const int e = tid + o * nth;
+    if (e < RR) {
+      const int r = e / R, q = e - (e / R) * R;
+      gMA[q * R + r] = cmul(sm.gam[q], ma[o]);
+    }
   }
   if (tid == 0) {
     const double rho = p.sf[SF_RHO], abar = p.sf[SF_ABAR_B];
     double alpha = rho;
     for (int r = 0; r < R; ++r) {
-      const float2 g = sm.gam[r];
-      alpha += ((double)g.x * g.x + (double)g.y * g.y) * (double)nA[r];
+      const double gx = p.gamma_d[r].x, gy = p.gamma_d[r].y;
+      alpha += (gx * gx + gy * gy) * (double)nA[r];
     }
     const double den = p.lf * abar + alpha;
     sm.ds[0] = alpha;
@@ -422,35 +582,29 @@ __device__ void step_B(const FrameParams& p, Smem& sm, int cta, int k, bool last
   }
   __syncthreads();
   const float c0 = sm.fs[0], c1 = sm.fs[1], c2 = sm.fs[2], frho = sm.fs[3];
-  Slice bs = slice_of(Ny, C, cta);
-  // one warp per row j: lane holds B[j][lane], B[j][lane+32]
-  for (int j = bs.lo + warp; j < bs.hi; j += nwarp) {
-    float2 b0 = lane < R ? p.B[j * R + lane] : make_float2(0.f, 0.f);
-    float2 b1 = lane + 32 < R ? p.B[j * R + lane + 32] : make_float2(0.f, 0.f);
-    float2 nb[2];
-    const int halves = R > 32 ? 2 : 1;
-    for (int h = 0; h < halves; ++h) {
-      const int r = lane + 32 * h;
-      float2 u = make_float2(0.f, 0.f);
-      if (r < R)
-        for (int m = 0; m < s; ++m) cfmac(u, Ah[m * R + r], p.Yt[(size_t)m * Ny + j]);  // Yt[m][j] conj(Ah[m][r])
-      float2 tb = u;
-      for (int q = 0; q < R; ++q) {
-        const float2 bq = make_float2(__shfl_sync(0xffffffffu, q < 32 ? b0.x : b1.x, q & 31),
-                                      __shfl_sync(0xffffffffu, q < 32 ? b0.y : b1.y, q & 31));
-        if (r < R) tb = csub(tb, cmul(bq, sm.gM[q * R + r]));
-      }
-      const float2 b = h == 0 ? b0 : b1;
-      if (r < R) {
-        const float2 grad = csub(cscale(b, frho), cmul(tb, cconj(sm.gam[r])));
-        const float2 bo = p.B0[j * R + r];
-        nb[h].x = c0 * bo.x + c1 * b.x - c2 * grad.x;
-        nb[h].y = c0 * bo.y + c1 * b.y - c2 * grad.y;
-      }
+  // B step: T_B = U - B diag(gamma) MA^T, grad = rho B - T_B diag(conj gamma)
+  float2 nbv[TTS_MAX_OWN];
+#pragma unroll
+  for (int o = 0; o < TTS_MAX_OWN; ++o) {
+    const int e = tid + o * nth;
+    if (e < NO) {
+      const int jl = e / R, r = e - (e / R) * R;
+      float2 tb = u[o];
+      for (int q = 0; q < R; ++q) tb = csub(tb, cmul(sm.B[jl * R + q], gMA[q * R + r]));
+      const float2 b = sm.B[e], b0 = sm.B0[e];
+      const float2 grad = csub(cscale(b, frho), cmul(tb, cconj(sm.gam[r])));
+      nbv[o].x = c0 * b0.x + c1 * b.x - c2 * grad.x;
+      nbv[o].y = c0 * b0.y + c1 * b.y - c2 * grad.y;
     }
-    __syncwarp();
-    if (lane < R) p.B[j * R + lane] = nb[0];
-    if (lane + 32 < R) p.B[j * R + lane + 32] = nb[1];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int o = 0; o < TTS_MAX_OWN; ++o) {
+    const int e = tid + o * nth;
+    if (e < NO) {
+      sm.B[e] = nbv[o];
+      p.B[bs.lo * R + e] = nbv[o];
+    }
   }
   if (last) {
     if (cta == 0 && tid == 0) {
@@ -464,30 +618,37 @@ __device__ void step_B(const FrameParams& p, Smem& sm, int cta, int k, bool last
   }
   __syncthreads();
   // partials over this CTA's rows: B'^H B' and Yt conj(B')
-  float2* pmb = p.partMB + (size_t)cta * R * R;
-  for (int q = warp; q < R; q += nwarp) {
-    for (int r = lane; r < R; r += 32) {
-      float2 acc = make_float2(0.f, 0.f);
-      for (int j = bs.lo; j < bs.hi; ++j) cfmac(acc, p.B[j * R + q], p.B[j * R + r]);
-      pmb[q * R + r] = acc;
-    }
+  float2* pmb = p.partMB + (size_t)cta * RR;
+  for (int e = tid; e < RR; e += nth) {
+    const int q = e / R, r = e - q * R;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int jl = 0; jl < nb; ++jl) cfmac(acc, sm.B[jl * R + q], sm.B[jl * R + r]);
+    pmb[e] = acc;
   }
   float2* pp = p.partP + (size_t)cta * Nx * R;
-  for (int m = warp; m < s; m += nwarp) {
-    for (int r = lane; r < R; r += 32) {
-      float2 acc = make_float2(0.f, 0.f);
-      for (int j = bs.lo; j < bs.hi; ++j) cfma(acc, p.Yt[(size_t)m * Ny + j], cconj(p.B[j * R + r]));
-      pp[m * R + r] = acc;
+  for (int m0 = 0; m0 < s; m0 += MC) {
+    const int mc = min(MC, s - m0);
+    for (int e = tid; e < mc * nb; e += nth) {
+      const int mm = e / nb, jl = e - mm * nb;
+      YB[e] = p.Yt[(size_t)(m0 + mm) * Ny + bs.lo + jl];
     }
+    __syncthreads();
+    for (int e = tid; e < mc * R; e += nth) {
+      const int mm = e / R, r = e - mm * R;
+      float2 acc = make_float2(0.f, 0.f);
+      for (int jl = 0; jl < nb; ++jl) cfma(acc, YB[mm * nb + jl], cconj(sm.B[jl * R + r]));
+      pp[(m0 + mm) * R + r] = acc;
+    }
+    __syncthreads();
   }
 }
 
 // reduce the per-CTA partials of B^H B and P
-__device__ void step_reduce_B(const FrameParams& p, Smem& sm, int cta) {
+__device__ void step_reduce_B(const FrameParams& p, SM& sm, int cta) {
   const int R = p.R, C = p.C, Nx = p.Nx;
   const int s = sm.misc[0];
   const int E = R * R + s * R;
-  Slice es = slice_of(E, C, cta);
+  const Slice es = slice_of(E, C, cta);
   for (int e = es.lo + threadIdx.x; e < es.hi; e += blockDim.x) {
     float2 acc = make_float2(0.f, 0.f);
     if (e < R * R) {
@@ -501,18 +662,29 @@ __device__ void step_reduce_B(const FrameParams& p, Smem& sm, int cta) {
   }
 }
 
-__global__ void __launch_bounds__(TTS_THREADS) frame_kernel(FrameParams p, int step_begin, int step_end,
-                                                              int fft_rows, int fused) {
+__global__ void __launch_bounds__(TTS_THREADS, 1) frame_kernel(FrameParams p, int step_begin, int step_end,
+                                                               int fused) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem sm = carve(p, smem_raw, fft_rows);
-  const int tid = threadIdx.x;
+  SM sm = carve(p, smem_raw);
+  const int tid = threadIdx.x, nth = blockDim.x;
   const int cta = blockIdx.x;
-  for (int e = tid; e < p.Nx; e += blockDim.x) sm.Wx[e] = p.Wx[e];
-  for (int e = tid; e < p.Ny; e += blockDim.x) sm.Wy[e] = p.Wy[e];
-  if (tid < 4) sm.misc[tid] = 0;
+  const int R = p.R;
+  for (int e = tid; e < p.Nx; e += nth) sm.Wx[e] = p.Wx[e];
+  for (int e = tid; e < p.Ny; e += nth) sm.Wy[e] = p.Wy[e];
+  if (tid < 8) sm.misc[tid] = 0;
+  // this CTA's rows of the factors (and of the anchors after the ingest step)
+  const Slice as = slice_of(p.Nx, p.C, cta), bs = slice_of(p.Ny, p.C, cta);
+  for (int e = tid; e < (as.hi - as.lo) * R; e += nth) {
+    sm.A[e] = p.A[as.lo * R + e];
+    if (step_begin > 0) sm.A0[e] = p.A0[as.lo * R + e];
+  }
+  for (int e = tid; e < (bs.hi - bs.lo) * R; e += nth) {
+    sm.B[e] = p.B[bs.lo * R + e];
+    if (step_begin > 0) sm.B0[e] = p.B0[bs.lo * R + e];
+  }
   __syncthreads();
   if (step_begin == 0) {
-    // compact the line mask into the increasing list S (every CTA, warp 0)
+    // compact the line mask into the increasing list S (warp 0)
     if (tid < 32) {
       int count = 0;
       for (int base = 0; base < p.Nx; base += 32) {
@@ -527,7 +699,7 @@ __global__ void __launch_bounds__(TTS_THREADS) frame_kernel(FrameParams p, int s
   } else {
     if (tid == 0) sm.misc[0] = *p.nrows;
     __syncthreads();
-    for (int e = tid; e < sm.misc[0]; e += blockDim.x) sm.rows[e] = p.rows[e];
+    for (int e = tid; e < sm.misc[0]; e += nth) sm.rows[e] = p.rows[e];
   }
   __syncthreads();
   cg::cluster_group cluster = cg::this_cluster();
@@ -538,7 +710,7 @@ __global__ void __launch_bounds__(TTS_THREADS) frame_kernel(FrameParams p, int s
       else __syncthreads();
     }
     if (step > 0) {
-      // frame rejected when any CTA saw a non-finite input sample
+      // the frame is rejected when any CTA saw a non-finite input sample
       int bad = 0;
       for (int c = 0; c < p.C; ++c) bad |= ((volatile int*)p.status)[1 + c];
       if (bad) {
@@ -548,6 +720,7 @@ __global__ void __launch_bounds__(TTS_THREADS) frame_kernel(FrameParams p, int s
     }
     if (step == 0) {
       step_ingest(p, sm, cta);
+      __syncthreads();
       continue;
     }
     const int k = (step - 1) / 4, sub = (step - 1) % 4;
@@ -559,63 +732,94 @@ __global__ void __launch_bounds__(TTS_THREADS) frame_kernel(FrameParams p, int s
   }
 }
 
-// The ridge solve alone on a given Hermitian positive-definite system (test hook).
-__global__ void __launch_bounds__(TTS_THREADS) ridge_kernel(const double2* G, const double2* h, int R, double2* gamma) {
+// The ridge solve alone on a given Hermitian positive-definite system (test hook): G and
+// h in FP64, split into float hi + lo parts; the same Gauss-Jordan + float-float
+// refinement as the frame kernel.
+__global__ void __launch_bounds__(TTS_THREADS, 1) ridge_kernel(const double2* G, const double2* h, int R, int iters,
+                                                               double2* gamma) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  FrameParams p;
-  p.R = R;
-  Smem sm;
-  sm.G = (double2*)smem_raw;
-  sm.z = sm.G + R * R;
-  sm.h = sm.z + R;
-  sm.invd = (double*)(sm.h + R);
-  for (int e = threadIdx.x; e < R * R; e += blockDim.x) sm.G[e] = G[e];
-  for (int e = threadIdx.x; e < R; e += blockDim.x) sm.h[e] = h[e];
+  SM sm;
+  float2* base = (float2*)smem_raw;
+  const int RR = R * R;
+  sm.Gf = base;
+  sm.GJa = base + RR;
+  sm.GJb = base + 2 * RR;
+  float2* Glo = base + 3 * RR;
+  sm.gam = base + 4 * RR;
+  sm.glo = sm.gam + R;
+  sm.h = sm.gam + 2 * R;
+  sm.rr = sm.gam + 3 * R;
+  float2* hlo = sm.gam + 4 * R;
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    const double2 g = G[e];
+    const float hx = (float)g.x, hy = (float)g.y;
+    sm.Gf[e] = make_float2(hx, hy);
+    Glo[e] = make_float2((float)(g.x - (double)hx), (float)(g.y - (double)hy));
+  }
+  for (int e = threadIdx.x; e < R; e += blockDim.x) {
+    const double2 v = h[e];
+    const float hx = (float)v.x, hy = (float)v.y;
+    sm.h[e] = make_float2(hx, hy);
+    hlo[e] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
+  }
   __syncthreads();
-  ldl_solve(p, sm, sm.h);
-  for (int e = threadIdx.x; e < R; e += blockDim.x) gamma[e] = sm.z[e];
+  ridge_solve(sm, R, Glo, hlo, iters);
+  for (int e = threadIdx.x; e < R; e += blockDim.x)
+    gamma[e] = make_double2((double)sm.gam[e].x + (double)sm.glo[e].x, (double)sm.gam[e].y + (double)sm.glo[e].y);
 }
 
 }  // namespace
 
 int launch_ridge(const double2* G, const double2* h, int R, double2* gamma, cudaStream_t st) {
-  const int smem = (int)(sizeof(double2) * (R * R + 2 * R) + sizeof(double) * R);
-  ridge_kernel<<<1, TTS_THREADS, smem, st>>>(G, h, R, gamma);
+  const int smem = (int)(sizeof(float2) * (4 * R * R + 5 * R));
+  if (cudaFuncSetAttribute(ridge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return TTS_ECUDA;
+  ridge_kernel<<<1, TTS_THREADS, smem, st>>>(G, h, R, 12, gamma);
   return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
 }
 
-int frame_smem_bytes(const FrameParams& p) {
-  const int fft_rows = max(1, min((p.Nx + p.C - 1) / p.C, 4096 / p.Ny));
-  size_t b = 0;
-  auto add = [&](size_t bytes) { b = ((b + 15) & ~size_t(15)) + bytes; };
-  add(sizeof(double2) * p.R * p.R);
-  add(sizeof(double2) * p.R);
-  add(sizeof(double) * p.R);
-  add(sizeof(double2) * p.R);
-  add(sizeof(float) * 8);
-  add(sizeof(double) * 8);
-  add(sizeof(float2) * p.Nx);
-  add(sizeof(float2) * p.Ny);
-  add(sizeof(float2) * p.R);
-  add(sizeof(float2) * p.R * p.R);
-  add(sizeof(int) * p.Nx);
-  add(sizeof(int) * 4);
-  add(sizeof(float) * TTS_THREADS);
-  add(sizeof(float2) * 2 * fft_rows * p.Ny);
-  return (int)b + 16;
+// Choose the cluster size and chunk length so that the shared-memory layout fits.
+int frame_configure(FrameParams& p, int requested_C) {
+  int maxsm = 0;
+  if (cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0) != cudaSuccess || maxsm <= 0)
+    maxsm = 227 * 1024;
+  const int preferred = std::max(1, std::min(8, std::min(p.Nx, p.Ny) / 8));
+  const int cands[] = {1, 2, 4, 8, 16};
+  for (int ci = 0; ci < 5; ++ci) {
+    const int C = requested_C > 0 ? requested_C : cands[ci];
+    if (requested_C == 0 && C < preferred) continue;
+    for (int MC : {32, 16, 8}) {
+      const int rA = (p.Nx + C - 1) / C, rB = (p.Ny + C - 1) / C;
+      if (rA * p.R > TTS_MAX_OWN * TTS_THREADS || rB * p.R > TTS_MAX_OWN * TTS_THREADS) continue;
+      if (p.R * p.R > TTS_MAX_OWN * TTS_THREADS) continue;
+      const FrameLayout L = frame_layout(p.Nx, p.Ny, p.R, rA, rB, MC);
+      if (L.bytes <= maxsm) {
+        p.C = C;
+        p.rA = rA;
+        p.rB = rB;
+        p.MC = MC;
+        p.lay = L;
+        return TTS_OK;
+      }
+    }
+    if (requested_C > 0) break;
+  }
+  return TTS_EINVAL;
 }
 
 int launch_frame(const FrameParams& p, int launch_mode, cudaStream_t st) {
-  const int fft_rows = max(1, min((p.Nx + p.C - 1) / p.C, 4096 / p.Ny));
-  const int smem = frame_smem_bytes(p);
-  cudaError_t e = cudaFuncSetAttribute(frame_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return TTS_ECUDA;
+  static bool attrs = false;
+  cudaError_t e;
+  if (!attrs) {
+    e = cudaFuncSetAttribute(frame_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return TTS_ECUDA;
+    e = cudaFuncSetAttribute(frame_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return TTS_ECUDA;
+    attrs = true;
+  }
+  const int smem = p.lay.bytes;
   const int nsteps = frame_num_steps(p.K);
   if (launch_mode == TTS_LAUNCH_FUSED) {
-    if (p.C > 8) {
-      e = cudaFuncSetAttribute(frame_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      if (e != cudaSuccess) return TTS_ECUDA;
-    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(p.C, 1, 1);
     cfg.blockDim = dim3(TTS_THREADS, 1, 1);
@@ -628,11 +832,11 @@ int launch_frame(const FrameParams& p, int launch_mode, cudaStream_t st) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, frame_kernel, p, 0, nsteps, fft_rows, 1);
+    e = cudaLaunchKernelEx(&cfg, frame_kernel, p, 0, nsteps, 1);
     if (e != cudaSuccess) return TTS_ECUDA;
   } else {
     for (int s = 0; s < nsteps; ++s) {
-      frame_kernel<<<p.C, TTS_THREADS, smem, st>>>(p, s, s + 1, fft_rows, 0);
+      frame_kernel<<<p.C, TTS_THREADS, smem, st>>>(p, s, s + 1, 0);
       if (cudaGetLastError() != cudaSuccess) return TTS_ECUDA;
     }
   }

@@ -10,7 +10,8 @@
 #define TTS_MAX_N 512
 #define TTS_MAX_R 64
 #define TTS_MAX_CLUSTER 16
-#define TTS_THREADS 256
+#define TTS_THREADS 512
+#define TTS_MAX_OWN 8     // register-owned outputs per thread (64 x 64 / 512)
 
 // ------------------------------------------------------------------------------------
 // complex float / double helpers
@@ -90,49 +91,63 @@ __device__ __forceinline__ float2 tw(const float2* W, int idx, int sign) {
   return sign < 0 ? w : make_float2(w.x, -w.y);
 }
 
-__device__ inline float2* fft_smem(float2* buf, float2* tmp, const FftPlan& plan, int batch,
+template <int P>
+__device__ __forceinline__ void fft_stage(const float2* x, float2* y, int N, int Ns, int batch, int bstride,
+                                          const float2* W, int sign, int tid, int nthreads) {
+  const int Np = N / P;
+  const int step = N / (Ns * P);
+  const int items = batch * Np;
+  for (int it = tid; it < items; it += nthreads) {
+    const int b = it / Np;
+    const int j = it - b * Np;
+    const float2* xb = x + b * bstride;
+    float2* yb = y + b * bstride;
+    const int k = j % Ns;
+    float2 v[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) v[q] = xb[j + q * Np];
+#pragma unroll
+    for (int q = 1; q < P; ++q) v[q] = cmul(v[q], tw(W, k * q * step, sign));
+    const int base = (j / Ns) * Ns * P + k;
+    if (P == 2) {
+      yb[base] = cadd(v[0], v[1]);
+      yb[base + Ns] = csub(v[0], v[1]);
+    } else if (P == 4) {
+      const float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+      const float2 b0 = cadd(v[1], v[3]), b1 = csub(v[1], v[3]);
+      // b1 times w_4: forward (-i) -> (b1.y, -b1.x); inverse (+i) -> (-b1.y, b1.x)
+      const float2 b1w = sign < 0 ? make_float2(b1.y, -b1.x) : make_float2(-b1.y, b1.x);
+      yb[base] = cadd(a0, b0);
+      yb[base + Ns] = cadd(a1, b1w);
+      yb[base + 2 * Ns] = csub(a0, b0);
+      yb[base + 3 * Ns] = csub(a1, b1w);
+    } else {
+      // p-point DFT with the table: w_p^{qu} = W[((q u) mod p) N/p]
+#pragma unroll
+      for (int u = 0; u < P; ++u) {
+        float2 acc = v[0];
+#pragma unroll
+        for (int q = 1; q < P; ++q) cfma(acc, v[q], tw(W, ((q * u) % P) * Np, sign));
+        yb[base + u * Ns] = acc;
+      }
+    }
+  }
+}
+
+// Transforms `batch` sequences of length plan.n stored bstride apart in buf; tmp is the
+// ping-pong buffer of the same shape. Every thread of the block must call it.
+__device__ inline float2* fft_smem(float2* buf, float2* tmp, const FftPlan& plan, int batch, int bstride,
                                    const float2* W, int sign, int tid, int nthreads) {
   const int N = plan.n;
   float2* x = buf;
   float2* y = tmp;
   int Ns = 1;
-  for (int s = 0; s < plan.nrad; ++s) {
-    const int p = plan.rad[s];
-    const int Np = N / p;
-    const int step = N / (Ns * p);
-    const int items = batch * Np;
-    for (int it = tid; it < items; it += nthreads) {
-      const int b = it / Np;
-      const int j = it - b * Np;
-      const float2* xb = x + b * N;
-      float2* yb = y + b * N;
-      const int k = j % Ns;
-      float2 v[5];
-      for (int q = 0; q < p; ++q) v[q] = xb[j + q * Np];
-      for (int q = 1; q < p; ++q) v[q] = cmul(v[q], tw(W, (k * q * step) % N, sign));
-      const int base = (j / Ns) * Ns * p + k;
-      if (p == 2) {
-        yb[base] = cadd(v[0], v[1]);
-        yb[base + Ns] = csub(v[0], v[1]);
-      } else if (p == 4) {
-        // w_4 = -i (forward) / +i (inverse)
-        float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
-        float2 b0 = cadd(v[1], v[3]), b1 = csub(v[1], v[3]);
-        // b1 * w_4: forward (-i) -> (b1.y, -b1.x); inverse (+i) -> (-b1.y, b1.x)
-        float2 b1w = sign < 0 ? make_float2(b1.y, -b1.x) : make_float2(-b1.y, b1.x);
-        yb[base] = cadd(a0, b0);
-        yb[base + Ns] = cadd(a1, b1w);
-        yb[base + 2 * Ns] = csub(a0, b0);
-        yb[base + 3 * Ns] = csub(a1, b1w);
-      } else {
-        // generic p-point DFT (p = 3, 5) with the table: w_p^{qu} = W[((q u) mod p) N/p]
-        for (int u = 0; u < p; ++u) {
-          float2 acc = v[0];
-          for (int q = 1; q < p; ++q) cfma(acc, v[q], tw(W, ((q * u) % p) * Np, sign));
-          yb[base + u * Ns] = acc;
-        }
-      }
-    }
+  for (int st = 0; st < plan.nrad; ++st) {
+    const int p = plan.rad[st];
+    if (p == 4) fft_stage<4>(x, y, N, Ns, batch, bstride, W, sign, tid, nthreads);
+    else if (p == 2) fft_stage<2>(x, y, N, Ns, batch, bstride, W, sign, tid, nthreads);
+    else if (p == 3) fft_stage<3>(x, y, N, Ns, batch, bstride, W, sign, tid, nthreads);
+    else fft_stage<5>(x, y, N, Ns, batch, bstride, W, sign, tid, nthreads);
     __syncthreads();
     float2* t = x;
     x = y;
@@ -180,11 +195,54 @@ enum { SC_W = 0, SC_ABAR_A = 1, SC_ABAR_B = 2, SC_T = 3, SC_COUNT = 8 };
 // scalars of the frame in flight
 enum { SF_W = 0, SF_RHO = 1, SF_ABAR_A = 2, SF_ABAR_B = 3, SF_ALPHA_A = 4, SF_ALPHA_B = 5, SF_COUNT = 8 };
 
+// Shared-memory layout of the frame kernel (bytes offsets), computed identically on the
+// host (launch size) and the device (carving).
+struct FrameLayout {
+  int Wx, Wy, rows, misc, red, myA, myA0, myB, myB0, Gf, GJa, GJb, vec, chunk;
+  int chunk_f2;   // capacity of the chunk region in float2
+  int bytes;
+};
+
+__host__ __device__ inline FrameLayout frame_layout(int Nx, int Ny, int R, int rA, int rB, int MC) {
+  FrameLayout L;
+  int off = 0;
+  auto take = [&](int bytes) {
+    off = (off + 15) & ~15;
+    int o = off;
+    off += bytes;
+    return o;
+  };
+  const int f2 = 8;
+  L.Wx = take(f2 * Nx);
+  L.Wy = take(f2 * Ny);
+  L.rows = take(4 * Nx);
+  L.misc = take(4 * 8);
+  L.red = take(4 * 2 * TTS_THREADS);
+  L.myA = take(f2 * rA * R);
+  L.myA0 = take(f2 * rA * R);
+  L.myB = take(f2 * rB * R);
+  L.myB0 = take(f2 * rB * R);
+  L.Gf = take(f2 * R * R);
+  L.GJa = take(f2 * R * R);
+  L.GJb = take(f2 * R * R);
+  L.vec = take(f2 * (6 * R + 16));
+  const int rmax = rA > rB ? rA : rB;
+  int cf = MC * (rmax + rB + 3 * R);
+  if (cf < 2 * Ny) cf = 2 * Ny;     // at least one row transform (ping-pong)
+  L.chunk_f2 = cf;
+  L.chunk = take(f2 * cf);
+  L.bytes = off + 16;
+  return L;
+}
+
 struct FrameParams {
   int Nx, Ny, R, K, C;
+  int rA, rB, MC;                 // rows of A / B per CTA, m-chunk length
   int jacobi;
+  int refine;                     // refinement sweeps of the ridge solve
   double lf, mu;
   float isx, isy;                 // 1/sqrt(Nx), 1/sqrt(Ny)
+  FrameLayout lay;
   FftPlan plan_y;                 // length-Ny transform of the acquired rows
   float2* A;                      // Nx x R (state)
   float2* B;                      // Ny x R (state)
@@ -204,29 +262,28 @@ struct FrameParams {
   float* partNA;                  // [C][R]
   float2* partMB;                 // [C][R][R]
   float2* partP;                  // [C][Nx][R]
-  float2* Q;                      // [C][Nx][R] per-CTA scratch
   double* sc;                     // SC_* (persistent)
   double* sf;                     // SF_* (frame in flight)
   float2* gamma;                  // R
   double2* gamma_d;               // R
-  int* status;                    // bit 0: non-finite input frame
+  int* status;                    // [0] sticky non-finite flag, [1 + c] per-CTA flag of the frame
   const float2* Wx;               // exp(-2 pi i k / Nx), k < Nx
   const float2* Wy;               // exp(-2 pi i k / Ny)
 };
 
-// Steps of one frame: 0 = ingest; then per iteration k: 1 + 4k + {0: solve + A update,
-// 1: reduce A partials, 2: B update, 3: reduce B partials}; the last iteration has no
-// step 3.
-__host__ __device__ inline int frame_num_steps(int K) { return 1 + 4 * K - 1; }
+// Steps of one frame: 0 = ingest; then per MM iteration k: 1 + 4k + {0: ridge solve and
+// A step, 1: reduce the A partials, 2: B step, 3: reduce the B partials}; the last
+// iteration has no step 3.
+__host__ __device__ inline int frame_num_steps(int K) { return 4 * K; }
 
 // host-side launchers (tts_kernels.cu)
 int launch_frame(const FrameParams& p, int launch_mode, cudaStream_t st);
-int frame_smem_bytes(const FrameParams& p);
+int frame_configure(FrameParams& p, int requested_C);
 int launch_image(const float2* A, const float2* B, const float2* gamma, float2* X, int Nx, int Ny, int R,
                  cudaStream_t st);
 int launch_sampler(const float2* A, int Nx, int Ny, int R, const double* p_in, double* p_out, int policy,
                    double vd_alpha, int k_lines, int central, uint64_t seed, uint64_t ctr, int with_replacement,
-                   const float2* Wx, uint8_t* mask_out, cudaStream_t st);
+                   const float2* Wx, uint8_t* mask_out, uint8_t* mask_out2, cudaStream_t st);
 int launch_fft2d(const float2* in, float2* out, int batch, int Nx, int Ny, int inverse, const float2* Wx,
                  const float2* Wy, float2* scratch, cudaStream_t st);
 int launch_ridge(const double2* G, const double2* h, int R, double2* gamma, cudaStream_t st);

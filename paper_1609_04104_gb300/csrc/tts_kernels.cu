@@ -62,7 +62,7 @@ __device__ __forceinline__ int upper_bound_u64(const unsigned long long* Q, int 
 __global__ void __launch_bounds__(SAMPLER_THREADS) sampler_kernel(
     const float2* __restrict__ A, int Nx, int Ny, int R, const double* __restrict__ p_in, double* p_out, int policy,
     double vd_alpha, int k_lines, int central, unsigned long long seed, unsigned long long ctr, int with_replacement,
-    const float2* __restrict__ Wx, uint8_t* mask_out, int fft_cols) {
+    const float2* __restrict__ Wx, uint8_t* mask_out, uint8_t* mask_out2, int fft_cols) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* p = (double*)smem_raw;                                   // Nx
   unsigned long long* Q = (unsigned long long*)(p + TTS_MAX_N);    // Nx
@@ -85,24 +85,26 @@ __global__ void __launch_bounds__(SAMPLER_THREADS) sampler_kernel(
     }
     __syncthreads();
     const FftPlan plan = fft_plan(Nx);
+    const int ld = Nx + 1;   // padded column stride in shared memory
     for (int r0 = 0; r0 < R; r0 += fft_cols) {
       const int nc = min(fft_cols, R - r0);
+      // coalesced along the rows of A, transposed into columns
       for (int e = tid; e < nc * Nx; e += blockDim.x) {
-        const int c = e / Nx, n = e - c * Nx;
-        buf[e] = A[n * R + r0 + c];
+        const int n = e / nc, c = e - n * nc;
+        buf[c * ld + n] = A[n * R + r0 + c];
       }
       __syncthreads();
-      float2* res = fft_smem(buf, buf + fft_cols * Nx, plan, nc, W, -1, tid, blockDim.x);
+      float2* res = fft_smem(buf, buf + fft_cols * ld, plan, nc, ld, W, -1, tid, blockDim.x);
       for (int c = warp; c < nc; c += nwarp) {
         float acc = 0.f;
-        for (int n = lane; n < Nx; n += 32) acc += cabs2(res[c * Nx + n]);
+        for (int n = lane; n < Nx; n += 32) acc += cabs2(res[c * ld + n]);
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) nrm[c] = acc;
+        if (lane == 0) nrm[c] = acc > 0.f ? 1.f / acc : 0.f;
       }
       __syncthreads();
       for (int i = tid; i < Nx; i += blockDim.x) {
         float acc = rowacc[i];
-        for (int c = 0; c < nc; ++c) acc += nrm[c] > 0.f ? cabs2(res[c * Nx + i]) / nrm[c] : 1.f / (float)Nx;
+        for (int c = 0; c < nc; ++c) acc += nrm[c] > 0.f ? cabs2(res[c * ld + i]) * nrm[c] : 1.f / (float)Nx;
         rowacc[i] = acc;
       }
       __syncthreads();
@@ -245,7 +247,10 @@ __global__ void __launch_bounds__(SAMPLER_THREADS) sampler_kernel(
     }
   }
   __syncthreads();
-  for (int i = tid; i < Nx; i += blockDim.x) mask_out[i] = mask[i];
+  for (int i = tid; i < Nx; i += blockDim.x) {
+    mask_out[i] = mask[i];
+    if (mask_out2) mask_out2[i] = mask[i];
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -290,7 +295,7 @@ __global__ void __launch_bounds__(256) fft_rows_kernel(const float2* __restrict_
   }
   __syncthreads();
   const FftPlan plan = fft_plan(Ny);
-  float2* res = fft_smem(buf, tmp, plan, nr, W, sign, tid, blockDim.x);
+  float2* res = fft_smem(buf, tmp, plan, nr, Ny, W, sign, tid, blockDim.x);
   if ((Ny & 1) == 0) {
     float4* dst = (float4*)(out + r0 * Ny);
     const float4* r4 = (const float4*)res;
@@ -308,8 +313,9 @@ __global__ void __launch_bounds__(256) fft_cols_kernel(float2* data, int Nx, int
                                                        const float2* __restrict__ Wx, float scale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* W = (float2*)smem_raw;
+  const int ld = Nx + 1;   // padded column stride in shared memory
   float2* buf = W + Nx;
-  float2* tmp = buf + cols_per_cta * Nx;
+  float2* tmp = buf + cols_per_cta * ld;
   const int tid = threadIdx.x;
   for (int e = tid; e < Nx; e += blockDim.x) W[e] = Wx[e];
   const int nblk = (Ny + cols_per_cta - 1) / cols_per_cta;
@@ -320,14 +326,14 @@ __global__ void __launch_bounds__(256) fft_cols_kernel(float2* data, int Nx, int
   // stage column block transposed: buf[c * Nx + i] = X[i][j0 + c]
   for (int e = tid; e < Nx * nc; e += blockDim.x) {
     const int i = e / nc, c = e - i * nc;
-    buf[c * Nx + i] = base[(long)i * Ny + j0 + c];
+    buf[c * ld + i] = base[(long)i * Ny + j0 + c];
   }
   __syncthreads();
   const FftPlan plan = fft_plan(Nx);
-  float2* res = fft_smem(buf, tmp, plan, nc, W, sign, tid, blockDim.x);
+  float2* res = fft_smem(buf, tmp, plan, nc, ld, W, sign, tid, blockDim.x);
   for (int e = tid; e < Nx * nc; e += blockDim.x) {
     const int i = e / nc, c = e - i * nc;
-    base[(long)i * Ny + j0 + c] = cscale(res[c * Nx + i], scale);
+    base[(long)i * Ny + j0 + c] = cscale(res[c * ld + i], scale);
   }
 }
 
@@ -343,16 +349,16 @@ int launch_image(const float2* A, const float2* B, const float2* gamma, float2* 
 
 int launch_sampler(const float2* A, int Nx, int Ny, int R, const double* p_in, double* p_out, int policy,
                    double vd_alpha, int k_lines, int central, uint64_t seed, uint64_t ctr, int with_replacement,
-                   const float2* Wx, uint8_t* mask_out, cudaStream_t st) {
+                   const float2* Wx, uint8_t* mask_out, uint8_t* mask_out2, cudaStream_t st) {
   const int fft_cols = max(1, min(min(R, 64), 8192 / max(Nx, 1)));
   const size_t smem = sizeof(double) * TTS_MAX_N + sizeof(unsigned long long) * TTS_MAX_N +
                       sizeof(float) * TTS_MAX_N + sizeof(float) * 64 + sizeof(int) * TTS_MAX_N + TTS_MAX_N +
-                      sizeof(int) * 8 + sizeof(float2) * TTS_MAX_N + sizeof(float2) * 2 * fft_cols * Nx + 64;
+                      sizeof(int) * 8 + sizeof(float2) * TTS_MAX_N + sizeof(float2) * 2 * fft_cols * (Nx + 1) + 64;
   cudaError_t e = cudaFuncSetAttribute(sampler_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return TTS_ECUDA;
   sampler_kernel<<<1, SAMPLER_THREADS, smem, st>>>(A, Nx, Ny, R, p_in, p_out, policy, vd_alpha, k_lines, central,
                                                    (unsigned long long)seed, (unsigned long long)ctr,
-                                                   with_replacement, Wx, mask_out, fft_cols);
+                                                   with_replacement, Wx, mask_out, mask_out2, fft_cols);
   return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
 }
 
@@ -376,7 +382,7 @@ int launch_fft2d(const float2* in, float2* out, int batch, int Nx, int Ny, int i
                                                           1.0f / sqrtf((float)Ny));
   if (cudaGetLastError() != cudaSuccess) return TTS_ECUDA;
   const int cols_per_cta = max(1, min(Ny, 4096 / Nx));
-  const size_t smem_c = sizeof(float2) * (Nx + 2 * (size_t)cols_per_cta * Nx);
+  const size_t smem_c = sizeof(float2) * (Nx + 2 * (size_t)cols_per_cta * (Nx + 1));
   e = cudaFuncSetAttribute(fft_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c);
   if (e != cudaSuccess) return TTS_ECUDA;
   const long grid_c = (long)batch * ((Ny + cols_per_cta - 1) / cols_per_cta);
