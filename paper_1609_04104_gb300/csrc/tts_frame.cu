@@ -116,34 +116,47 @@ __device__ __forceinline__ void ff_add_ff(float& hi, float& lo, float h2, float 
 // Ridge solve (S1): (G_hi + G_lo) gamma = h_hi + h_lo. FP32 Gauss-Jordan inverse of G_hi
 // (pivots on the diagonal; G is Hermitian positive definite), then `iters` refinement
 // sweeps gamma += Ginv (h - G gamma) with the residual in float-float arithmetic and
-// gamma held as a float-float pair (gam + glo). G_hi in sm.Gf, h_hi in sm.h.
+// gamma held as a float-float pair (gam + glo); the sweeps stop once every correction is
+// below sqrt(tol2) relative. G_hi in sm.Gf, h_hi in sm.h.
 // ---------------------------------------------------------------------------------
-__device__ void ridge_solve(SM& sm, int R, const float2* Glo, const float2* hlo, int iters) {
+template <int OWN>
+__device__ void ridge_solve(SM& sm, int R, const float2* Glo, const float2* hlo, int iters, float tol2) {
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
   const int RR = R * R;
+  int oi[OWN], oj[OWN];
+#pragma unroll
+  for (int o = 0; o < OWN; ++o) {
+    const int e = tid + o * nth;
+    oi[o] = e / R;
+    oj[o] = e - oi[o] * R;
+  }
   for (int e = tid; e < RR; e += nth) sm.GJa[e] = sm.Gf[e];
   __syncthreads();
   float2* M = sm.GJa;
   float2* N = sm.GJb;
   for (int k = 0; k < R; ++k) {
     const float2 d = M[k * R + k];
-    const float den = d.x * d.x + d.y * d.y;
-    const float2 piv = make_float2(d.x / den, -d.y / den);
-    for (int e = tid; e < RR; e += nth) {
-      const int i = e / R, j = e - (e / R) * R;
-      float2 v;
-      if (i == k && j == k) {
-        v = piv;
-      } else if (i == k) {
-        v = cmul(M[e], piv);
-      } else if (j == k) {
-        const float2 t = cmul(M[e], piv);
-        v = make_float2(-t.x, -t.y);
-      } else {
-        const float2 rk = cmul(M[k * R + j], piv);
-        v = csub(M[e], cmul(M[i * R + k], rk));
+    const float inv = __frcp_rn(d.x * d.x + d.y * d.y);
+    const float2 piv = make_float2(d.x * inv, -d.y * inv);
+#pragma unroll
+    for (int o = 0; o < OWN; ++o) {
+      const int e = tid + o * nth;
+      if (e < RR) {
+        const int i = oi[o], j = oj[o];
+        float2 v;
+        if (i == k && j == k) {
+          v = piv;
+        } else if (i == k) {
+          v = cmul(M[e], piv);
+        } else if (j == k) {
+          const float2 t = cmul(M[e], piv);
+          v = make_float2(-t.x, -t.y);
+        } else {
+          const float2 rk = cmul(M[k * R + j], piv);
+          v = csub(M[e], cmul(M[i * R + k], rk));
+        }
+        N[e] = v;
       }
-      N[e] = v;
     }
     __syncthreads();
     float2* t = M;
@@ -165,7 +178,9 @@ __device__ void ridge_solve(SM& sm, int R, const float2* Glo, const float2* hlo,
     }
   }
   __syncthreads();
+  int* flag = (int*)(sm.tmpv);
   for (int it = 0; it < iters; ++it) {
+    if (tid == 0) *flag = 0;
     // r = h - G gamma in float-float (warp per row)
     for (int i = warp; i < R; i += nwarp) {
       float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
@@ -215,6 +230,7 @@ __device__ void ridge_solve(SM& sm, int R, const float2* Glo, const float2* hlo,
       }
       if (lane == 0) {
         float2 g = sm.gam[i], gl = sm.glo[i];
+        if (cabs2(acc) > tol2 * cabs2(g)) *flag = 1;   // correction above sqrt(tol2) relative
         ff_add_ff(g.x, gl.x, acc.x, 0.f);
         ff_add_ff(g.y, gl.y, acc.y, 0.f);
         sm.gam[i] = g;
@@ -222,6 +238,7 @@ __device__ void ridge_solve(SM& sm, int R, const float2* Glo, const float2* hlo,
       }
     }
     __syncthreads();
+    if (*flag == 0) break;
   }
 }
 
@@ -269,46 +286,91 @@ __device__ void step_ingest(const FrameParams& p, SM& sm, int cta) {
   const Slice as = slice_of(Nx, C, cta), bs = slice_of(Ny, C, cta);
   for (int e = as.lo * R + tid; e < as.hi * R; e += nth) p.A0[e] = p.A[e];
   for (int e = bs.lo * R + tid; e < bs.hi * R; e += nth) p.B0[e] = p.B[e];
-  // one list of outputs, one per thread and pass: P[m][r] and Ahat_S[m][r] for m in this
-  // CTA's slice of S, (B^H B)[q][r] for q in its slice of [0, R), ||a_r||^2 (last CTA)
+  // outputs of this CTA: P[m][r] and Ahat_S[m][r] for m in its slice of S, (B^H B)[q][r]
+  // for q in its slice of [0, R), and ||a_r||^2 (last CTA). Rows of A and B stream
+  // through shared memory in chunks; each thread owns up to two outputs per pass and
+  // keeps two accumulators per output.
   const Slice qs = slice_of(R, C, cta);
   const int nm = ms.hi - ms.lo, nq = qs.hi - qs.lo;
   const int nP = nm * R, nAh = nm * R, nMB = nq * R, nNA = (cta == C - 1) ? R : 0;
   const int total = nP + nAh + nMB + nNA;
   float2* AhS = p.AhS[0];
-  for (int o = tid; o < total; o += nth) {
-    if (o < nP) {
-      const int m = ms.lo + o / R, r = o % R;
-      const float2* yt = p.Yt + (size_t)m * Ny;
-      float2 acc = make_float2(0.f, 0.f);
-#pragma unroll 4
-      for (int j = 0; j < Ny; ++j) cfma(acc, yt[j], cconj(p.B[j * R + r]));
-      p.P[m * R + r] = acc;
-    } else if (o < nP + nAh) {
-      const int q = o - nP;
-      const int m = ms.lo + q / R, r = q % R;
-      const int i = sm.rows[m];
-      float2 acc = make_float2(0.f, 0.f);
-      int idx = 0;
-#pragma unroll 4
-      for (int n = 0; n < Nx; ++n) {
-        cfma(acc, sm.Wx[idx], p.A[n * R + r]);
-        idx += i;
-        if (idx >= Nx) idx -= Nx;
+  const int NR = max(Nx, Ny);
+  const int nch = max(1, min(NR, p.lay.chunk_f2 / (2 * R)));
+  float2* As = sm.chunk;            // nch x R rows of A
+  float2* Bs = sm.chunk + nch * R;  // nch x R rows of B
+  __syncthreads();
+  for (int o0 = 0; o0 < total; o0 += 2 * nth) {
+    int kind[2], row[2], col[2];
+    float2 a0[2], a1[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int o = o0 + tid + u * nth;
+      a0[u] = a1[u] = make_float2(0.f, 0.f);
+      if (o < nP) {
+        kind[u] = 0; row[u] = ms.lo + o / R; col[u] = o % R;
+      } else if (o < nP + nAh) {
+        kind[u] = 1; row[u] = ms.lo + (o - nP) / R; col[u] = (o - nP) % R;
+      } else if (o < nP + nAh + nMB) {
+        kind[u] = 2; row[u] = qs.lo + (o - nP - nAh) / R; col[u] = (o - nP - nAh) % R;
+      } else if (o < total) {
+        kind[u] = 3; row[u] = 0; col[u] = o - nP - nAh - nMB;
+      } else {
+        kind[u] = 4; row[u] = 0; col[u] = 0;
       }
-      AhS[m * R + r] = cscale(acc, p.isx);
-    } else if (o < nP + nAh + nMB) {
-      const int q2 = o - nP - nAh;
-      const int q = qs.lo + q2 / R, r = q2 % R;
-      float2 acc = make_float2(0.f, 0.f);
-#pragma unroll 4
-      for (int j = 0; j < Ny; ++j) cfmac(acc, p.B[j * R + q], p.B[j * R + r]);
-      p.MB[q * R + r] = acc;
-    } else {
-      const int r = o - nP - nAh - nMB;
-      float acc = 0.f;
-      for (int n = 0; n < Nx; ++n) acc += cabs2(p.A[n * R + r]);
-      p.nA[0][r] = acc;
+    }
+    for (int j0 = 0; j0 < NR; j0 += nch) {
+      const int nc = min(nch, NR - j0);
+      __syncthreads();
+      for (int e = tid; e < nc * R; e += nth) {
+        const int jj = e / R;
+        As[e] = j0 + jj < Nx ? p.A[j0 * R + e] : make_float2(0.f, 0.f);
+        Bs[e] = j0 + jj < Ny ? p.B[j0 * R + e] : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int r = col[u];
+        if (kind[u] == 0) {
+          const float2* yt = p.Yt + (size_t)row[u] * Ny + j0;
+          const int lim = min(nc, Ny - j0);
+          int jj = 0;
+          for (; jj + 1 < lim; jj += 2) {
+            cfma(a0[u], yt[jj], cconj(Bs[jj * R + r]));
+            cfma(a1[u], yt[jj + 1], cconj(Bs[(jj + 1) * R + r]));
+          }
+          if (jj < lim) cfma(a0[u], yt[jj], cconj(Bs[jj * R + r]));
+        } else if (kind[u] == 1) {
+          const int i = sm.rows[row[u]];
+          const int lim = min(nc, Nx - j0);
+          int idx = (int)(((long long)i * j0) % Nx);
+          for (int jj = 0; jj < lim; ++jj) {
+            if (jj & 1) cfma(a1[u], sm.Wx[idx], As[jj * R + r]);
+            else cfma(a0[u], sm.Wx[idx], As[jj * R + r]);
+            idx += i;
+            if (idx >= Nx) idx -= Nx;
+          }
+        } else if (kind[u] == 2) {
+          const int q = row[u];
+          int jj = 0;
+          for (; jj + 1 < nc; jj += 2) {
+            cfmac(a0[u], Bs[jj * R + q], Bs[jj * R + r]);
+            cfmac(a1[u], Bs[(jj + 1) * R + q], Bs[(jj + 1) * R + r]);
+          }
+          if (jj < nc) cfmac(a0[u], Bs[jj * R + q], Bs[jj * R + r]);
+        } else if (kind[u] == 3) {
+          for (int jj = 0; jj < nc; ++jj) a0[u].x += cabs2(As[jj * R + r]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const float2 v = cadd(a0[u], a1[u]);
+      const int r = col[u];
+      if (kind[u] == 0) p.P[row[u] * R + r] = v;
+      else if (kind[u] == 1) AhS[row[u] * R + r] = cscale(v, p.isx);
+      else if (kind[u] == 2) p.MB[row[u] * R + r] = v;
+      else if (kind[u] == 3) p.nA[0][r] = v.x;
     }
   }
   __syncthreads();
@@ -327,8 +389,33 @@ __device__ void step_ingest(const FrameParams& p, SM& sm, int cta) {
 
 // ---------------------------------------------------------------------------------
 // step A: ridge solve for gamma (S1), majorized A step (S2) on this CTA's rows, then the
-// partial sums of Ahat'_S and ||a'_r||^2 over those rows
+// partial sums of Ahat'_S and ||a'_r||^2 over those rows. OWN = outputs per thread.
 // ---------------------------------------------------------------------------------
+// warp 0: alpha = sum_r |gamma_r|^2 w_r + rho and the MM step coefficients
+// c0 = lf abar / den, c1 = alpha / den, c2 = 1 / den (den = lf abar + alpha) into sm.fs,
+// alpha into sm.ds[0]
+__device__ __forceinline__ void step_coefficients(const FrameParams& p, SM& sm, const float* wr, int wstride,
+                                                  double rho, double abar) {
+  const int tid = threadIdx.x;
+  if (tid < 32) {
+    float acc = 0.f;
+    for (int r = tid; r < p.R; r += 32) acc += cabs2(sm.gam[r]) * wr[r * wstride];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (tid == 0) {
+      const double alpha = rho + (double)acc;
+      const float den = (float)(p.lf * abar + alpha);
+      const float inv = 1.0f / den;
+      sm.ds[0] = alpha;
+      sm.ds[1] = abar;
+      sm.fs[0] = (float)(p.lf * abar) * inv;
+      sm.fs[1] = (float)alpha * inv;
+      sm.fs[2] = inv;
+      sm.fs[3] = (float)rho;
+    }
+  }
+}
+
+template <int OWN>
 __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int Nx = p.Nx, R = p.R, C = p.C, MC = p.MC;
@@ -341,10 +428,18 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
   float2* QC = PC + MC * R;              // MC x R
   float2* TW = QC + MC * R;              // MC x na
   const int RR = R * R;
-  // Gram of the masked rank-one DFTs (all R x R entries) and the right-hand side
-  float2 g[TTS_MAX_OWN], hacc = make_float2(0.f, 0.f);
+  int orow[OWN], ocol[OWN];
 #pragma unroll
-  for (int o = 0; o < TTS_MAX_OWN; ++o) g[o] = make_float2(0.f, 0.f);
+  for (int o = 0; o < OWN; ++o) {
+    const int e = tid + o * nth;
+    orow[o] = e / R;
+    ocol[o] = e - orow[o] * R;
+  }
+  // Gram of the masked rank-one DFTs (all R x R entries) and the right-hand side;
+  // two accumulators per output (even / odd m)
+  float2 g0[OWN], g1[OWN], h0 = make_float2(0.f, 0.f), h1 = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int o = 0; o < OWN; ++o) g0[o] = g1[o] = make_float2(0.f, 0.f);
   for (int m0 = 0; m0 < s; m0 += MC) {
     const int mc = min(MC, s - m0);
     for (int e = tid; e < mc * R; e += nth) {
@@ -352,52 +447,47 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
       PC[e] = p.P[m0 * R + e];
     }
     __syncthreads();
+    int ir[OWN], ic[OWN];
 #pragma unroll
-    for (int o = 0; o < TTS_MAX_OWN; ++o) {
-      const int e = tid + o * nth;
-      if (e < RR) {
-        const int i = e / R, j = e - (e / R) * R;
-        float2 acc = g[o];
-        for (int mm = 0; mm < mc; ++mm) cfmac(acc, AH[mm * R + i], AH[mm * R + j]);
-        g[o] = acc;
+    for (int o = 0; o < OWN; ++o) {
+      const bool v = tid + o * nth < RR;
+      ir[o] = v ? orow[o] : 0;
+      ic[o] = v ? ocol[o] : 0;
+    }
+    int mm = 0;
+    for (; mm + 1 < mc; mm += 2) {
+#pragma unroll
+      for (int o = 0; o < OWN; ++o) {
+        cfmac(g0[o], AH[mm * R + ir[o]], AH[mm * R + ic[o]]);
+        cfmac(g1[o], AH[(mm + 1) * R + ir[o]], AH[(mm + 1) * R + ic[o]]);
+      }
+      if (tid < R) {
+        cfmac(h0, AH[mm * R + tid], PC[mm * R + tid]);
+        cfmac(h1, AH[(mm + 1) * R + tid], PC[(mm + 1) * R + tid]);
       }
     }
-    if (tid < R)
-      for (int mm = 0; mm < mc; ++mm) cfmac(hacc, AH[mm * R + tid], PC[mm * R + tid]);
+    if (mm < mc) {
+#pragma unroll
+      for (int o = 0; o < OWN; ++o) cfmac(g0[o], AH[mm * R + ir[o]], AH[mm * R + ic[o]]);
+      if (tid < R) cfmac(h0, AH[mm * R + tid], PC[mm * R + tid]);
+    }
     __syncthreads();
   }
   const float fmu = (float)p.mu;
 #pragma unroll
-  for (int o = 0; o < TTS_MAX_OWN; ++o) {
+  for (int o = 0; o < OWN; ++o) {
     const int e = tid + o * nth;
     if (e < RR) {
-      const int i = e / R, j = e - (e / R) * R;
-      float2 v = cmul(g[o], p.MB[e]);
-      if (i == j) v = make_float2(v.x + fmu, 0.f);
+      float2 v = cmul(cadd(g0[o], g1[o]), p.MB[e]);
+      if (orow[o] == ocol[o]) v = make_float2(v.x + fmu, 0.f);
       sm.Gf[e] = v;
     }
   }
-  if (tid < R) sm.h[tid] = hacc;
+  if (tid < R) sm.h[tid] = cadd(h0, h1);
   __syncthreads();
-  ridge_solve(sm, R, nullptr, nullptr, p.refine);
-  // alpha_A = sum |gamma_r|^2 ||b_r||^2 + rho and the step coefficients (one thread:
-  // FP64 is scarce on this part)
-  if (tid == 0) {
-    const double rho = p.sf[SF_RHO], abar = p.sf[SF_ABAR_A];
-    double alpha = rho;
-    for (int r = 0; r < R; ++r) {
-      const double gx = (double)sm.gam[r].x + (double)sm.glo[r].x;
-      const double gy = (double)sm.gam[r].y + (double)sm.glo[r].y;
-      alpha += (gx * gx + gy * gy) * (double)p.MB[r * R + r].x;
-    }
-    const double den = p.lf * abar + alpha;
-    sm.ds[0] = alpha;
-    sm.fs[0] = (float)(p.lf * abar / den);
-    sm.fs[1] = (float)(alpha / den);
-    sm.fs[2] = (float)(1.0 / den);
-    sm.fs[3] = (float)rho;
-    if (cta == 0) p.sf[SF_ALPHA_A] = alpha;
-  }
+  ridge_solve<OWN>(sm, R, nullptr, nullptr, p.refine, 1e-20f);
+  // alpha_A = sum |gamma_r|^2 ||b_r||^2 + rho (||b_r||^2 = (B^H B)[r][r])
+  step_coefficients(p, sm, (const float*)p.MB, 2 * (R + 1), p.sf[SF_RHO], p.sf[SF_ABAR_A]);
   if (cta == 0)
     for (int r = tid; r < R; r += nth) {
       p.gamma[r] = sm.gam[r];
@@ -411,11 +501,12 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
     gM[e] = cmul(sm.gam[q], p.MB[r * R + q]);
   }
   __syncthreads();
+  if (cta == 0 && tid == 0) p.sf[SF_ALPHA_A] = sm.ds[0];
   // Theta conj(B) on this CTA's rows: T[n][r] = sum_m conj(F[S_m, n]) Q[m][r],
   // Q = P - Ahat_S diag(gamma) (B^H B)^T, accumulated over chunks of m
-  float2 t[TTS_MAX_OWN];
+  float2 t0[OWN], t1[OWN];
 #pragma unroll
-  for (int o = 0; o < TTS_MAX_OWN; ++o) t[o] = make_float2(0.f, 0.f);
+  for (int o = 0; o < OWN; ++o) t0[o] = t1[o] = make_float2(0.f, 0.f);
   const int NO = na * R;
   for (int m0 = 0; m0 < s; m0 += MC) {
     const int mc = min(MC, s - m0);
@@ -427,33 +518,46 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
     __syncthreads();
     for (int e = tid; e < mc * R; e += nth) {
       const int mm = e / R, r = e - mm * R;
-      float2 acc = PC[e];
-      for (int q = 0; q < R; ++q) acc = csub(acc, cmul(AH[mm * R + q], gM[q * R + r]));
-      QC[e] = acc;
+      float2 a0 = PC[e], a1 = make_float2(0.f, 0.f);
+      int q = 0;
+      for (; q + 1 < R; q += 2) {
+        a0 = csub(a0, cmul(AH[mm * R + q], gM[q * R + r]));
+        a1 = csub(a1, cmul(AH[mm * R + q + 1], gM[(q + 1) * R + r]));
+      }
+      if (q < R) a0 = csub(a0, cmul(AH[mm * R + q], gM[q * R + r]));
+      QC[e] = cadd(a0, a1);
     }
     __syncthreads();
+    int ir[OWN], ic[OWN];
 #pragma unroll
-    for (int o = 0; o < TTS_MAX_OWN; ++o) {
-      const int e = tid + o * nth;
-      if (e < NO) {
-        const int nl = e / R, r = e - (e / R) * R;
-        float2 acc = t[o];
-        for (int mm = 0; mm < mc; ++mm) cfmac(acc, TW[mm * na + nl], QC[mm * R + r]);
-        t[o] = acc;
+    for (int o = 0; o < OWN; ++o) {
+      const bool v = tid + o * nth < NO;
+      ir[o] = v ? orow[o] : 0;
+      ic[o] = v ? ocol[o] : 0;
+    }
+    int mm = 0;
+    for (; mm + 1 < mc; mm += 2) {
+#pragma unroll
+      for (int o = 0; o < OWN; ++o) {
+        cfmac(t0[o], TW[mm * na + ir[o]], QC[mm * R + ic[o]]);
+        cfmac(t1[o], TW[(mm + 1) * na + ir[o]], QC[(mm + 1) * R + ic[o]]);
       }
+    }
+    if (mm < mc) {
+#pragma unroll
+      for (int o = 0; o < OWN; ++o) cfmac(t0[o], TW[mm * na + ir[o]], QC[mm * R + ic[o]]);
     }
     __syncthreads();
   }
   // A step: grad = rho A - T diag(conj gamma); A <- c0 A0 + c1 A - c2 grad
   const float c0 = sm.fs[0], c1 = sm.fs[1], c2 = sm.fs[2], frho = sm.fs[3];
 #pragma unroll
-  for (int o = 0; o < TTS_MAX_OWN; ++o) {
+  for (int o = 0; o < OWN; ++o) {
     const int e = tid + o * nth;
     if (e < NO) {
-      const int r = e - (e / R) * R;
       const float2 a = sm.A[e], a0 = sm.A0[e];
-      const float2 tt = cscale(t[o], p.isx);
-      const float2 grad = csub(cscale(a, frho), cmul(tt, cconj(sm.gam[r])));
+      const float2 tt = cscale(cadd(t0[o], t1[o]), p.isx);
+      const float2 grad = csub(cscale(a, frho), cmul(tt, cconj(sm.gam[ocol[o]])));
       float2 an;
       an.x = c0 * a0.x + c1 * a.x - c2 * grad.x;
       an.y = c0 * a0.y + c1 * a.y - c2 * grad.y;
@@ -470,9 +574,14 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
     __syncthreads();
     for (int e = tid; e < mc * R; e += nth) {
       const int mm = e / R, r = e - mm * R;
-      float2 acc = make_float2(0.f, 0.f);
-      for (int nl = 0; nl < na; ++nl) cfma(acc, TW[mm * na + nl], sm.A[nl * R + r]);
-      part[(m0 + mm) * R + r] = cscale(acc, p.isx);
+      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+      int nl = 0;
+      for (; nl + 1 < na; nl += 2) {
+        cfma(a0, TW[mm * na + nl], sm.A[nl * R + r]);
+        cfma(a1, TW[mm * na + nl + 1], sm.A[(nl + 1) * R + r]);
+      }
+      if (nl < na) cfma(a0, TW[mm * na + nl], sm.A[nl * R + r]);
+      part[(m0 + mm) * R + r] = cscale(cadd(a0, a1), p.isx);
     }
     __syncthreads();
   }
@@ -481,6 +590,18 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
     for (int nl = 0; nl < na; ++nl) acc += cabs2(sm.A[nl * R + r]);
     p.partNA[cta * R + r] = acc;
   }
+}
+
+// sum of C per-CTA partials stride apart, loads issued four at a time
+__device__ __forceinline__ float2 sum_partials(const float2* src, size_t stride, int C) {
+  float2 acc = make_float2(0.f, 0.f);
+  for (int c = 0; c < C; c += 4) {
+    float2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = c + u < C ? src[(c + u) * stride] : make_float2(0.f, 0.f);
+    acc = cadd(acc, cadd(cadd(v[0], v[1]), cadd(v[2], v[3])));
+  }
+  return acc;
 }
 
 // reduce the per-CTA partials of Ahat'_S and ||a'||^2 (this CTA's slice of the entries)
@@ -493,13 +614,16 @@ __device__ void step_reduce_A(const FrameParams& p, SM& sm, int cta, int k) {
   float* nout = p.nA[(k + 1) & 1];
   for (int e = es.lo + threadIdx.x; e < es.hi; e += blockDim.x) {
     if (e < s * R) {
-      float2 acc = make_float2(0.f, 0.f);
-      for (int c = 0; c < C; ++c) acc = cadd(acc, p.partA[(size_t)c * Nx * R + e]);
-      out[e] = acc;
+      out[e] = sum_partials(p.partA + e, (size_t)Nx * R, C);
     } else {
       const int r = e - s * R;
       float acc = 0.f;
-      for (int c = 0; c < C; ++c) acc += p.partNA[c * R + r];
+      for (int c = 0; c < C; c += 4) {
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = c + u < C ? p.partNA[(c + u) * R + r] : 0.f;
+        acc += (v[0] + v[1]) + (v[2] + v[3]);
+      }
       nout[r] = acc;
     }
   }
@@ -508,6 +632,7 @@ __device__ void step_reduce_A(const FrameParams& p, SM& sm, int cta, int k) {
 // ---------------------------------------------------------------------------------
 // step B: majorized B step (S2) on this CTA's rows, then partials of B^H B and P
 // ---------------------------------------------------------------------------------
+template <int OWN>
 __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int Nx = p.Nx, Ny = p.Ny, R = p.R, C = p.C, MC = p.MC;
@@ -520,14 +645,18 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) 
   float2* AH = sm.chunk;                 // MC x R
   float2* YB = AH + MC * R;              // MC x nb
   const int RR = R * R;
+  int orow[OWN], ocol[OWN];
+#pragma unroll
+  for (int o = 0; o < OWN; ++o) {
+    const int e = tid + o * nth;
+    orow[o] = e / R;
+    ocol[o] = e - orow[o] * R;
+  }
   for (int r = tid; r < R; r += nth) sm.gam[r] = p.gamma[r];
   // MA = Ahat^H Ahat (thread-owned entries) and U[j][r] = sum_m Yt[m][j] conj(Ahat[m][r])
-  float2 ma[TTS_MAX_OWN], u[TTS_MAX_OWN];
+  float2 ma[OWN], u[OWN];
 #pragma unroll
-  for (int o = 0; o < TTS_MAX_OWN; ++o) {
-    ma[o] = make_float2(0.f, 0.f);
-    u[o] = make_float2(0.f, 0.f);
-  }
+  for (int o = 0; o < OWN; ++o) ma[o] = u[o] = make_float2(0.f, 0.f);
   const int NO = nb * R;
   for (int m0 = 0; m0 < s; m0 += MC) {
     const int mc = min(MC, s - m0);
@@ -537,20 +666,20 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) 
       YB[e] = p.Yt[(size_t)(m0 + mm) * Ny + bs.lo + jl];
     }
     __syncthreads();
+    int mr[OWN], mq[OWN], uj[OWN], ur[OWN];
 #pragma unroll
-    for (int o = 0; o < TTS_MAX_OWN; ++o) {
-      const int e = tid + o * nth;
-      if (e < RR) {
-        const int r = e / R, q = e - (e / R) * R;
-        float2 acc = ma[o];
-        for (int mm = 0; mm < mc; ++mm) cfmac(acc, AH[mm * R + r], AH[mm * R + q]);
-        ma[o] = acc;
-      }
-      if (e < NO) {
-        const int jl = e / R, r = e - (e / R) * R;
-        float2 acc = u[o];
-        for (int mm = 0; mm < mc; ++mm) cfmac(acc, AH[mm * R + r], YB[mm * nb + jl]);
-        u[o] = acc;
+    for (int o = 0; o < OWN; ++o) {
+      const bool vm = tid + o * nth < RR, vu = tid + o * nth < NO;
+      mr[o] = vm ? orow[o] : 0;
+      mq[o] = vm ? ocol[o] : 0;
+      uj[o] = vu ? orow[o] : 0;
+      ur[o] = vu ? ocol[o] : 0;
+    }
+    for (int mm = 0; mm < mc; ++mm) {
+#pragma unroll
+      for (int o = 0; o < OWN; ++o) {
+        cfmac(ma[o], AH[mm * R + mr[o]], AH[mm * R + mq[o]]);
+        cfmac(u[o], AH[mm * R + ur[o]], YB[mm * nb + uj[o]]);
       }
     }
     __syncthreads();
@@ -558,39 +687,29 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) 
   // gMA[q][r] = gamma_q MA[r][q]
   float2* gMA = sm.GJa;
 #pragma unroll
-  for (int o = 0; o < TTS_MAX_OWN; ++o) {
+  for (int o = 0; o < OWN; ++o) {
     const int e = tid + o * nth;
-    if (e < RR) {
-      const int r = e / R, q = e - (e / R) * R;
-      gMA[q * R + r] = cmul(sm.gam[q], ma[o]);
-    }
+    if (e < RR) gMA[ocol[o] * R + orow[o]] = cmul(sm.gam[ocol[o]], ma[o]);
   }
-  if (tid == 0) {
-    const double rho = p.sf[SF_RHO], abar = p.sf[SF_ABAR_B];
-    double alpha = rho;
-    for (int r = 0; r < R; ++r) {
-      const double gx = p.gamma_d[r].x, gy = p.gamma_d[r].y;
-      alpha += (gx * gx + gy * gy) * (double)nA[r];
-    }
-    const double den = p.lf * abar + alpha;
-    sm.ds[0] = alpha;
-    sm.ds[1] = abar;
-    sm.fs[0] = (float)(p.lf * abar / den);
-    sm.fs[1] = (float)(alpha / den);
-    sm.fs[2] = (float)(1.0 / den);
-    sm.fs[3] = (float)rho;
-  }
+  // alpha_B = sum |gamma_r|^2 ||a_r||^2 + rho
+  step_coefficients(p, sm, nA, 1, p.sf[SF_RHO], p.sf[SF_ABAR_B]);
   __syncthreads();
   const float c0 = sm.fs[0], c1 = sm.fs[1], c2 = sm.fs[2], frho = sm.fs[3];
   // B step: T_B = U - B diag(gamma) MA^T, grad = rho B - T_B diag(conj gamma)
-  float2 nbv[TTS_MAX_OWN];
+  float2 nbv[OWN];
 #pragma unroll
-  for (int o = 0; o < TTS_MAX_OWN; ++o) {
+  for (int o = 0; o < OWN; ++o) {
     const int e = tid + o * nth;
     if (e < NO) {
-      const int jl = e / R, r = e - (e / R) * R;
-      float2 tb = u[o];
-      for (int q = 0; q < R; ++q) tb = csub(tb, cmul(sm.B[jl * R + q], gMA[q * R + r]));
+      const int jl = orow[o], r = ocol[o];
+      float2 tb0 = u[o], tb1 = make_float2(0.f, 0.f);
+      int q = 0;
+      for (; q + 1 < R; q += 2) {
+        tb0 = csub(tb0, cmul(sm.B[jl * R + q], gMA[q * R + r]));
+        tb1 = csub(tb1, cmul(sm.B[jl * R + q + 1], gMA[(q + 1) * R + r]));
+      }
+      if (q < R) tb0 = csub(tb0, cmul(sm.B[jl * R + q], gMA[q * R + r]));
+      const float2 tb = cadd(tb0, tb1);
       const float2 b = sm.B[e], b0 = sm.B0[e];
       const float2 grad = csub(cscale(b, frho), cmul(tb, cconj(sm.gam[r])));
       nbv[o].x = c0 * b0.x + c1 * b.x - c2 * grad.x;
@@ -599,7 +718,7 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) 
   }
   __syncthreads();
 #pragma unroll
-  for (int o = 0; o < TTS_MAX_OWN; ++o) {
+  for (int o = 0; o < OWN; ++o) {
     const int e = tid + o * nth;
     if (e < NO) {
       sm.B[e] = nbv[o];
@@ -619,11 +738,19 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) 
   __syncthreads();
   // partials over this CTA's rows: B'^H B' and Yt conj(B')
   float2* pmb = p.partMB + (size_t)cta * RR;
-  for (int e = tid; e < RR; e += nth) {
-    const int q = e / R, r = e - q * R;
-    float2 acc = make_float2(0.f, 0.f);
-    for (int jl = 0; jl < nb; ++jl) cfmac(acc, sm.B[jl * R + q], sm.B[jl * R + r]);
-    pmb[e] = acc;
+#pragma unroll
+  for (int o = 0; o < OWN; ++o) {
+    const int e = tid + o * nth;
+    if (e < RR) {
+      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+      int jl = 0;
+      for (; jl + 1 < nb; jl += 2) {
+        cfmac(a0, sm.B[jl * R + orow[o]], sm.B[jl * R + ocol[o]]);
+        cfmac(a1, sm.B[(jl + 1) * R + orow[o]], sm.B[(jl + 1) * R + ocol[o]]);
+      }
+      if (jl < nb) cfmac(a0, sm.B[jl * R + orow[o]], sm.B[jl * R + ocol[o]]);
+      pmb[e] = cadd(a0, a1);
+    }
   }
   float2* pp = p.partP + (size_t)cta * Nx * R;
   for (int m0 = 0; m0 < s; m0 += MC) {
@@ -635,9 +762,14 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) 
     __syncthreads();
     for (int e = tid; e < mc * R; e += nth) {
       const int mm = e / R, r = e - mm * R;
-      float2 acc = make_float2(0.f, 0.f);
-      for (int jl = 0; jl < nb; ++jl) cfma(acc, YB[mm * nb + jl], cconj(sm.B[jl * R + r]));
-      pp[(m0 + mm) * R + r] = acc;
+      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+      int jl = 0;
+      for (; jl + 1 < nb; jl += 2) {
+        cfma(a0, YB[mm * nb + jl], cconj(sm.B[jl * R + r]));
+        cfma(a1, YB[mm * nb + jl + 1], cconj(sm.B[(jl + 1) * R + r]));
+      }
+      if (jl < nb) cfma(a0, YB[mm * nb + jl], cconj(sm.B[jl * R + r]));
+      pp[(m0 + mm) * R + r] = cadd(a0, a1);
     }
     __syncthreads();
   }
@@ -650,18 +782,16 @@ __device__ void step_reduce_B(const FrameParams& p, SM& sm, int cta) {
   const int E = R * R + s * R;
   const Slice es = slice_of(E, C, cta);
   for (int e = es.lo + threadIdx.x; e < es.hi; e += blockDim.x) {
-    float2 acc = make_float2(0.f, 0.f);
-    if (e < R * R) {
-      for (int c = 0; c < C; ++c) acc = cadd(acc, p.partMB[(size_t)c * R * R + e]);
-      p.MB[e] = acc;
-    } else {
-      const int f = e - R * R;
-      for (int c = 0; c < C; ++c) acc = cadd(acc, p.partP[(size_t)c * Nx * R + f]);
-      p.P[f] = acc;
-    }
+    const bool mb = e < R * R;
+    const float2* src = mb ? p.partMB + e : p.partP + (e - R * R);
+    const size_t stride = mb ? (size_t)R * R : (size_t)Nx * R;
+    const float2 acc = sum_partials(src, stride, C);
+    if (mb) p.MB[e] = acc;
+    else p.P[e - R * R] = acc;
   }
 }
 
+template <int OWN>
 __global__ void __launch_bounds__(TTS_THREADS, 1) frame_kernel(FrameParams p, int step_begin, int step_end,
                                                                int fused) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -724,9 +854,9 @@ __global__ void __launch_bounds__(TTS_THREADS, 1) frame_kernel(FrameParams p, in
       continue;
     }
     const int k = (step - 1) / 4, sub = (step - 1) % 4;
-    if (sub == 0) step_solve_A(p, sm, cta, k);
+    if (sub == 0) step_solve_A<OWN>(p, sm, cta, k);
     else if (sub == 1) step_reduce_A(p, sm, cta, k);
-    else if (sub == 2) step_B(p, sm, cta, k, k == p.K - 1);
+    else if (sub == 2) step_B<OWN>(p, sm, cta, k, k == p.K - 1);
     else step_reduce_B(p, sm, cta);
     __syncthreads();
   }
@@ -763,7 +893,7 @@ __global__ void __launch_bounds__(TTS_THREADS, 1) ridge_kernel(const double2* G,
     hlo[e] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
   }
   __syncthreads();
-  ridge_solve(sm, R, Glo, hlo, iters);
+  ridge_solve<TTS_MAX_OWN>(sm, R, Glo, hlo, iters, 1e-28f);
   for (int e = threadIdx.x; e < R; e += blockDim.x)
     gamma[e] = make_double2((double)sm.gam[e].x + (double)sm.glo[e].x, (double)sm.gam[e].y + (double)sm.glo[e].y);
 }
@@ -807,13 +937,14 @@ int frame_configure(FrameParams& p, int requested_C) {
   return TTS_EINVAL;
 }
 
-int launch_frame(const FrameParams& p, int launch_mode, cudaStream_t st) {
+template <int OWN>
+static int launch_frame_t(const FrameParams& p, int launch_mode, cudaStream_t st) {
   static bool attrs = false;
   cudaError_t e;
   if (!attrs) {
-    e = cudaFuncSetAttribute(frame_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    e = cudaFuncSetAttribute(frame_kernel<OWN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return TTS_ECUDA;
-    e = cudaFuncSetAttribute(frame_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(frame_kernel<OWN>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return TTS_ECUDA;
     attrs = true;
   }
@@ -832,13 +963,30 @@ int launch_frame(const FrameParams& p, int launch_mode, cudaStream_t st) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, frame_kernel, p, 0, nsteps, 1);
+    e = cudaLaunchKernelEx(&cfg, frame_kernel<OWN>, p, 0, nsteps, 1);
     if (e != cudaSuccess) return TTS_ECUDA;
   } else {
     for (int s = 0; s < nsteps; ++s) {
-      frame_kernel<<<p.C, TTS_THREADS, smem, st>>>(p, s, s + 1, 0);
+      frame_kernel<OWN><<<p.C, TTS_THREADS, smem, st>>>(p, s, s + 1, 0);
       if (cudaGetLastError() != cudaSuccess) return TTS_ECUDA;
     }
   }
   return TTS_OK;
+}
+
+// outputs each thread owns: R x R entries of the Gram and Gauss-Jordan updates, and the
+// (row, r) entries of this CTA's rows of A and B
+int frame_own(const FrameParams& p) {
+  const int n = std::max(p.R * p.R, std::max(p.rA, p.rB) * p.R);
+  const int own = (n + TTS_THREADS - 1) / TTS_THREADS;
+  return own <= 1 ? 1 : own <= 2 ? 2 : own <= 4 ? 4 : 8;
+}
+
+int launch_frame(const FrameParams& p, int launch_mode, cudaStream_t st) {
+  switch (frame_own(p)) {
+    case 1: return launch_frame_t<1>(p, launch_mode, st);
+    case 2: return launch_frame_t<2>(p, launch_mode, st);
+    case 4: return launch_frame_t<4>(p, launch_mode, st);
+    default: return launch_frame_t<8>(p, launch_mode, st);
+  }
 }
