@@ -880,6 +880,7 @@ __global__ void __launch_bounds__(TTS_THREADS, 1) ridge_kernel(const double2* G,
   sm.h = sm.gam + 2 * R;
   sm.rr = sm.gam + 3 * R;
   float2* hlo = sm.gam + 4 * R;
+  sm.tmpv = sm.gam + 5 * R;   // refinement convergence flag
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
     const double2 g = G[e];
     const float hx = (float)g.x, hy = (float)g.y;
@@ -901,7 +902,7 @@ __global__ void __launch_bounds__(TTS_THREADS, 1) ridge_kernel(const double2* G,
 }  // namespace
 
 int launch_ridge(const double2* G, const double2* h, int R, double2* gamma, cudaStream_t st) {
-  const int smem = (int)(sizeof(float2) * (4 * R * R + 5 * R));
+  const int smem = (int)(sizeof(float2) * (4 * R * R + 6 * R));
   if (cudaFuncSetAttribute(ridge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return TTS_ECUDA;
   ridge_kernel<<<1, TTS_THREADS, smem, st>>>(G, h, R, 12, gamma);
