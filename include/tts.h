@@ -197,6 +197,48 @@ int tts_ridge_solve(const double* G, const double* h, int R, double* gamma);
  * in {2, 3, 5}. Asynchronous. */
 int tts_fft2d(const tts_c64* in, tts_c64* out, int batch, int Nx, int Ny, int inverse, void* cuda_stream);
 
+/* ---- Frame update without allocation ------------------------------------------------
+ * The paper has no counterpart of this call; it serves callers that cannot allocate
+ * device memory while they run: code whose device memory is handed out by an allocator
+ * it does not control, real-time loops that were sized once and must not grow, and code
+ * that cannot afford the implicit device synchronisation of cudaMalloc / cudaFree.
+ *
+ * It runs the same frame update as tts_push_frame on state the caller holds in device
+ * memory. Every temporary lives in one fixed array of TTS_NOALLOC_SCRATCH_BYTES in
+ * device memory that the library declares at file scope; every GPU that loads the
+ * library holds that array until the process exits. The call allocates nothing
+ * (no cudaMalloc, no cudaFree, no allocating library routine). Limits: Nx, Ny <= 256
+ * with prime factors in {2,3,5}, R <= 32; larger problems return TTS_EINVAL.
+ *
+ * All calls on a device share the one array and it keeps the last call's contents; the
+ * call re-initialises what must start at zero. Calls whose work overlaps on the GPU
+ * (several host threads, or several streams) race on the array and give wrong results:
+ * serialise them. The first call on a device looks up the array's device address (with
+ * that device current); make that first call before any stream capture. The call is
+ * asynchronous on cuda_stream (NULL = default stream) and does not report non-finite
+ * input samples: such a frame is skipped on the device. */
+#define TTS_NOALLOC_MAX_N 256
+#define TTS_NOALLOC_MAX_R 32
+#define TTS_NOALLOC_SCRATCH_BYTES (2u << 20)
+
+typedef struct {
+  int Nx, Ny, R;
+  double lambda_forget, mu;
+  int mm_iters;
+  int update;               /* TTS_UPDATE_* */
+  tts_c64* A;               /* device, Nx x R row-major, updated in place */
+  tts_c64* B;               /* device, Ny x R row-major, updated in place */
+  double* stats;            /* device, 4 doubles updated in place: w, abar_A, abar_B, frames
+                               processed; all zero before the first frame */
+  tts_c64* gamma;           /* device, R values written: gamma_t of this frame */
+  const tts_c64* y_rows;    /* device: acquired rows (|S| x Ny), or the whole Nx x Ny
+                               frame with TTS_FULL_FRAME */
+  const uint8_t* line_mask; /* device, Nx bytes */
+  int flags;                /* 0 or TTS_FULL_FRAME */
+} tts_frame_args;
+
+int tts_push_frame_noalloc(const tts_frame_args* args, void* cuda_stream);
+
 const char* tts_last_error(void);
 
 #ifdef __cplusplus

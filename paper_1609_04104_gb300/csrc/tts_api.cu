@@ -54,6 +54,8 @@ size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
+void tts_internal_set_error(const char* msg) { g_err = msg ? msg : ""; }
+
 struct tts_handle {
   tts_config cfg;
   int dev = 0;

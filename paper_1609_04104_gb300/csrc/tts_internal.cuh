@@ -284,6 +284,7 @@ int launch_image(const float2* A, const float2* B, const float2* gamma, float2* 
 int launch_sampler(const float2* A, int Nx, int Ny, int R, const double* p_in, double* p_out, int policy,
                    double vd_alpha, int k_lines, int central, uint64_t seed, uint64_t ctr, int with_replacement,
                    const float2* Wx, uint8_t* mask_out, uint8_t* mask_out2, cudaStream_t st);
+void tts_internal_set_error(const char* msg);   // message returned by tts_last_error
 int launch_fft2d(const float2* in, float2* out, int batch, int Nx, int Ny, int inverse, const float2* Wx,
                  const float2* Wy, float2* scratch, cudaStream_t st);
 int launch_ridge(const double2* G, const double2* h, int R, double2* gamma, cudaStream_t st);

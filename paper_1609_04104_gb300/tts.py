@@ -27,7 +27,7 @@ EXPORTS = [
     "tts_config_init", "tts_create", "tts_create_ex", "tts_destroy", "tts_set_factors", "tts_get_factors",
     "tts_get_stats", "tts_set_stats", "tts_get_gamma", "tts_push_frame", "tts_image", "tts_next_mask",
     "tts_line_probs", "tts_sample_lines_from_probs", "tts_save", "tts_load", "tts_synchronize",
-    "tts_launches_per_frame", "tts_ridge_solve", "tts_fft2d", "tts_last_error",
+    "tts_launches_per_frame", "tts_ridge_solve", "tts_fft2d", "tts_push_frame_noalloc", "tts_last_error",
 ]
 
 
@@ -45,6 +45,16 @@ class tts_config(ctypes.Structure):
         ("vd_alpha", ctypes.c_double), ("with_replacement", ctypes.c_int), ("update", ctypes.c_int),
         ("launch", ctypes.c_int), ("cluster_ctas", ctypes.c_int), ("init_seed", ctypes.c_uint64),
         ("stream_id", ctypes.c_uint32), ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class tts_frame_args(ctypes.Structure):
+    _fields_ = [
+        ("Nx", ctypes.c_int), ("Ny", ctypes.c_int), ("R", ctypes.c_int),
+        ("lambda_forget", ctypes.c_double), ("mu", ctypes.c_double),
+        ("mm_iters", ctypes.c_int), ("update", ctypes.c_int),
+        ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("stats", ctypes.c_void_p), ("gamma", ctypes.c_void_p),
+        ("y_rows", ctypes.c_void_p), ("line_mask", ctypes.c_void_p), ("flags", ctypes.c_int),
     ]
 
 
@@ -85,6 +95,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "tts_launches_per_frame": (I, [H]),
         "tts_ridge_solve": (I, [P, P, I, P]),
         "tts_fft2d": (I, [P, P, I, I, I, I, P]),
+        "tts_push_frame_noalloc": (I, [ctypes.POINTER(tts_frame_args), P]),
         "tts_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -259,6 +270,21 @@ def tts_fft2d(x, out, inverse=False, stream=None) -> None:
         batch, Nx, Ny = x.shape
     s = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(load().tts_fft2d(x.data_ptr(), out.data_ptr(), batch, Nx, Ny, int(inverse), s))
+
+
+def tts_push_frame_noalloc(A, B, stats, gamma, y_rows, line_mask, lambda_forget, mu, mm_iters=1,
+                           update=TTS_UPDATE_GAUSS_SEIDEL, full_frame=False, stream=None) -> None:
+    """Frame update on caller-held device state (torch CUDA tensors) that allocates
+    nothing: A (Nx x R), B (Ny x R), gamma (R) complex64; stats (4) float64 holding
+    w, abar_A, abar_B, frames; y_rows and line_mask as for tts_push_frame."""
+    for t in (A, B, stats, gamma, y_rows, line_mask):
+        if not _is_torch(t) or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("tts_push_frame_noalloc takes contiguous CUDA tensors")
+    args = tts_frame_args(A.shape[0], B.shape[0], A.shape[1], lambda_forget, mu, mm_iters, update,
+                          A.data_ptr(), B.data_ptr(), stats.data_ptr(), gamma.data_ptr(), y_rows.data_ptr(),
+                          line_mask.data_ptr(), TTS_FULL_FRAME if full_frame else 0)
+    s = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(load().tts_push_frame_noalloc(ctypes.byref(args), s))
 
 
 class Tracker:
