@@ -193,7 +193,7 @@ int tts_create_ex(const tts_config* cfg, tts_handle** out) {
     off += align_up(pc.bytes);
   }
   p.K = cfg->mm_iters;
-  p.refine = 6;
+  p.refine = 4;
   p.jacobi = cfg->update == TTS_UPDATE_JACOBI;
   p.lf = cfg->lambda_forget;
   p.mu = cfg->mu;

@@ -47,10 +47,14 @@ struct SM {
   int* misc;  // [0] |S|, [1] non-finite flag
   float* red;
   float2 *A, *A0, *B, *B0;  // this CTA's rows (rA x R, rB x R)
-  float2 *Gf, *GJa, *GJb;   // R x R
+  float2 *Gf;               // R x R
+  float2 *GJa, *GJb;        // Rp x Rp (R padded to a multiple of 16)
+  float2 *Pk, *Tk;          // 16 x 16 block inverse, 16 x Rp block row
   float2 *gam, *glo, *h, *rr, *tmpv;  // R each
   double* ds;               // 8 doubles
   float* fs;                // 8 floats
+  float2* yb;               // Yt[m][j] for this CTA's B rows j (|S| <= MC)
+  bool yb_ready;
   float2* chunk;
 };
 
@@ -69,6 +73,8 @@ __device__ SM carve(const FrameParams& p, unsigned char* base) {
   s.Gf = (float2*)(base + L.Gf);
   s.GJa = (float2*)(base + L.GJa);
   s.GJb = (float2*)(base + L.GJb);
+  s.Pk = (float2*)(base + L.gjx);
+  s.Tk = s.Pk + 256;
   float2* v = (float2*)(base + L.vec);
   const int R = p.R;
   s.gam = v;
@@ -78,6 +84,8 @@ __device__ SM carve(const FrameParams& p, unsigned char* base) {
   s.tmpv = v + 4 * R;
   s.ds = (double*)(v + 6 * R);   // vec region holds 8R float2: 6R for vectors, then 8 doubles + 8 floats
   s.fs = (float*)(s.ds + 8);
+  s.yb = (float2*)(base + L.yb);
+  s.yb_ready = false;
   s.chunk = (float2*)(base + L.chunk);
   return s;
 }
@@ -119,41 +127,111 @@ __device__ __forceinline__ void ff_add_ff(float& hi, float& lo, float h2, float 
 // gamma held as a float-float pair (gam + glo); the sweeps stop once every correction is
 // below sqrt(tol2) relative. G_hi in sm.Gf, h_hi in sm.h.
 // ---------------------------------------------------------------------------------
+// Inverse of the 16 x 16 diagonal block at [kb, kb+16) of M (row stride ld), by one warp:
+// Gauss-Jordan in registers, lane = column (lane & 15) of rows 8 (lane >> 4) + 0..7;
+// rows and columns of the pivot are exchanged with shuffles. Result into P (16 x 16).
+__device__ __forceinline__ void warp_inverse16(const float2* M, int ld, int kb, float2* P) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, c = lane & 15, h = lane >> 4;
+  float2 m[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) m[e] = M[(kb + 8 * h + e) * ld + kb + c];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int qe = q & 7, qh = q >> 3;
+    float2 d, rq, cq[8];
+    d.x = __shfl_sync(FULL, m[qe].x, q + 16 * qh);
+    d.y = __shfl_sync(FULL, m[qe].y, q + 16 * qh);
+    rq.x = __shfl_sync(FULL, m[qe].x, c + 16 * qh);
+    rq.y = __shfl_sync(FULL, m[qe].y, c + 16 * qh);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      cq[e].x = __shfl_sync(FULL, m[e].x, q + 16 * h);
+      cq[e].y = __shfl_sync(FULL, m[e].y, q + 16 * h);
+    }
+    const float inv = __frcp_rn(d.x * d.x + d.y * d.y);
+    const float2 piv = make_float2(d.x * inv, -d.y * inv);
+    const float2 rqp = cmul(rq, piv);
+    // branch-free update (the row and column of the pivot are lane dependent)
+    const bool colq = (c == q);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const bool rowq = (h == qh) && (e == qe);
+      const float2 gen = csub(m[e], cmul(cq[e], rqp));
+      const float2 t = cmul(cq[e], piv);
+      const float2 colv = make_float2(-t.x, -t.y);
+      const float2 rv = colq ? piv : rqp;
+      const float2 ov = colq ? colv : gen;
+      m[e] = rowq ? rv : ov;
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 8; ++e) P[(8 * h + e) * 16 + c] = m[e];
+}
+
 template <int OWN>
 __device__ void ridge_solve(SM& sm, int R, const float2* Glo, const float2* hlo, int iters, float tol2) {
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
-  const int RR = R * R;
+  const int Rp = (R + 15) & ~15;
+  const int RP2 = Rp * Rp;
   int oi[OWN], oj[OWN];
 #pragma unroll
   for (int o = 0; o < OWN; ++o) {
     const int e = tid + o * nth;
-    oi[o] = e / R;
-    oj[o] = e - oi[o] * R;
+    oi[o] = e / Rp;
+    oj[o] = e - oi[o] * Rp;
   }
-  for (int e = tid; e < RR; e += nth) sm.GJa[e] = sm.Gf[e];
+  // G padded with the identity to Rp x Rp
+#pragma unroll
+  for (int o = 0; o < OWN; ++o) {
+    const int e = tid + o * nth;
+    if (e < RP2) {
+      const int i = oi[o], j = oj[o];
+      sm.GJa[e] = (i < R && j < R) ? sm.Gf[i * R + j] : make_float2(i == j ? 1.f : 0.f, 0.f);
+    }
+  }
   __syncthreads();
+  // blocked Gauss-Jordan inverse with 16 x 16 pivot blocks (Hermitian positive definite:
+  // every pivot block is a Schur complement and invertible)
   float2* M = sm.GJa;
   float2* N = sm.GJb;
-  for (int k = 0; k < R; ++k) {
-    const float2 d = M[k * R + k];
-    const float inv = __frcp_rn(d.x * d.x + d.y * d.y);
-    const float2 piv = make_float2(d.x * inv, -d.y * inv);
+  for (int kb = 0; kb < Rp; kb += 16) {
+    if (warp == 0) warp_inverse16(M, Rp, kb, sm.Pk);
+    __syncthreads();
+    // block row k of the update: T = P M[kb:kb+16, :]
+    for (int e = tid; e < 16 * Rp; e += nth) {
+      const int t = e / Rp, cc = e - t * Rp;
+      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 16; u += 2) {
+        cfma(a0, sm.Pk[t * 16 + u], M[(kb + u) * Rp + cc]);
+        cfma(a1, sm.Pk[t * 16 + u + 1], M[(kb + u + 1) * Rp + cc]);
+      }
+      sm.Tk[e] = cadd(a0, a1);
+    }
+    __syncthreads();
 #pragma unroll
     for (int o = 0; o < OWN; ++o) {
       const int e = tid + o * nth;
-      if (e < RR) {
-        const int i = oi[o], j = oj[o];
+      if (e < RP2) {
+        const int i = oi[o], cc = oj[o];
+        const bool bi = (i >= kb) && (i < kb + 16), bc = (cc >= kb) && (cc < kb + 16);
         float2 v;
-        if (i == k && j == k) {
-          v = piv;
-        } else if (i == k) {
-          v = cmul(M[e], piv);
-        } else if (j == k) {
-          const float2 t = cmul(M[e], piv);
-          v = make_float2(-t.x, -t.y);
+        if (bi) {
+          v = bc ? sm.Pk[(i - kb) * 16 + (cc - kb)] : sm.Tk[(i - kb) * Rp + cc];
         } else {
-          const float2 rk = cmul(M[k * R + j], piv);
-          v = csub(M[e], cmul(M[i * R + k], rk));
+          // column source: the block inverse for pivot-block columns, else T (no divergence)
+          const float2* src = bc ? sm.Pk + (cc - kb) : sm.Tk + cc;
+          const int ld = bc ? 16 : Rp;
+          float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int u = 0; u < 16; u += 2) {
+            cfma(a0, M[i * Rp + kb + u], src[u * ld]);
+            cfma(a1, M[i * Rp + kb + u + 1], src[(u + 1) * ld]);
+          }
+          const float2 a = cadd(a0, a1);
+          const float2 base = bc ? make_float2(0.f, 0.f) : M[e];
+          v = csub(base, a);
         }
         N[e] = v;
       }
@@ -163,11 +241,11 @@ __device__ void ridge_solve(SM& sm, int R, const float2* Glo, const float2* hlo,
     M = N;
     N = t;
   }
-  const float2* Gi = M;
+  const float2* Gi = M;   // inverse, row stride Rp
   // gamma_0 = Ginv h (one warp per row)
   for (int i = warp; i < R; i += nwarp) {
     float2 acc = make_float2(0.f, 0.f);
-    for (int j = lane; j < R; j += 32) cfma(acc, Gi[i * R + j], sm.h[j]);
+    for (int j = lane; j < R; j += 32) cfma(acc, Gi[i * Rp + j], sm.h[j]);
     for (int o = 16; o > 0; o >>= 1) {
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
@@ -178,9 +256,15 @@ __device__ void ridge_solve(SM& sm, int R, const float2* Glo, const float2* hlo,
     }
   }
   __syncthreads();
-  int* flag = (int*)(sm.tmpv);
+  // convergence: max_i |delta_i|^2 <= tol2 max_i |gamma_i|^2 (float bits of non-negative
+  // floats order like unsigned integers)
+  unsigned* dmax = (unsigned*)(sm.tmpv);
+  unsigned* gmax = dmax + 1;
   for (int it = 0; it < iters; ++it) {
-    if (tid == 0) *flag = 0;
+    if (tid == 0) {
+      *dmax = 0u;
+      *gmax = 0u;
+    }
     // r = h - G gamma in float-float (warp per row)
     for (int i = warp; i < R; i += nwarp) {
       float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
@@ -223,14 +307,15 @@ __device__ void ridge_solve(SM& sm, int R, const float2* Glo, const float2* hlo,
     // gamma += Ginv r
     for (int i = warp; i < R; i += nwarp) {
       float2 acc = make_float2(0.f, 0.f);
-      for (int j = lane; j < R; j += 32) cfma(acc, Gi[i * R + j], sm.rr[j]);
+      for (int j = lane; j < R; j += 32) cfma(acc, Gi[i * Rp + j], sm.rr[j]);
       for (int o = 16; o > 0; o >>= 1) {
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
         acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
       }
       if (lane == 0) {
         float2 g = sm.gam[i], gl = sm.glo[i];
-        if (cabs2(acc) > tol2 * cabs2(g)) *flag = 1;   // correction above sqrt(tol2) relative
+        atomicMax(dmax, __float_as_uint(cabs2(acc)));
+        atomicMax(gmax, __float_as_uint(cabs2(g)));
         ff_add_ff(g.x, gl.x, acc.x, 0.f);
         ff_add_ff(g.y, gl.y, acc.y, 0.f);
         sm.gam[i] = g;
@@ -238,7 +323,8 @@ __device__ void ridge_solve(SM& sm, int R, const float2* Glo, const float2* hlo,
       }
     }
     __syncthreads();
-    if (*flag == 0) break;
+    if (__uint_as_float(*dmax) <= tol2 * __uint_as_float(*gmax)) break;
+    __syncthreads();
   }
 }
 
@@ -253,26 +339,147 @@ __device__ __forceinline__ void fill_twiddles(const FrameParams& p, SM& sm, floa
 }
 
 // ---------------------------------------------------------------------------------
-// step 0: ingest the frame, form Ahat_S, ||a_r||^2, B^H B and P of the first iteration
+// partial sums over this CTA's rows (shared by the ingest and the MM steps)
 // ---------------------------------------------------------------------------------
+// Ahat_S[m][r] = sum over this CTA's rows n of F[S_m, n] A[n][r] / sqrt(Nx), and ||a_r||^2;
+// TW is chunk scratch of MC x (rows of A). With tw_ready the twiddles of a single chunk
+// are already in TW.
+__device__ void partials_A(const FrameParams& p, SM& sm, int cta, float2* TW, bool tw_ready) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int Nx = p.Nx, R = p.R, MC = p.MC;
+  const int s = sm.misc[0];
+  const Slice as = slice_of(Nx, p.C, cta);
+  const int na = as.hi - as.lo;
+  float2* part = p.partA + (size_t)cta * Nx * R;
+  for (int m0 = 0; m0 < s; m0 += MC) {
+    const int mc = min(MC, s - m0);
+    if (!(tw_ready && s <= MC)) fill_twiddles(p, sm, TW, m0, mc, as.lo, na);
+    __syncthreads();
+    for (int e = tid; e < mc * R; e += nth) {
+      const int mm = e / R, r = e - mm * R;
+      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+      int nl = 0;
+      for (; nl + 1 < na; nl += 2) {
+        cfma(a0, TW[mm * na + nl], sm.A[nl * R + r]);
+        cfma(a1, TW[mm * na + nl + 1], sm.A[(nl + 1) * R + r]);
+      }
+      if (nl < na) cfma(a0, TW[mm * na + nl], sm.A[nl * R + r]);
+      part[(m0 + mm) * R + r] = cscale(cadd(a0, a1), p.isx);
+    }
+    __syncthreads();
+  }
+  for (int r = tid; r < R; r += nth) {
+    float acc = 0.f;
+    for (int nl = 0; nl < na; ++nl) acc += cabs2(sm.A[nl * R + r]);
+    p.partNA[cta * R + r] = acc;
+  }
+}
+
+// Yt[m][j] for m in [m0, m0 + mc) and this CTA's B rows j, into YB (mc x nb)
+__device__ __forceinline__ void load_yb(const FrameParams& p, float2* YB, int m0, int mc, int lo, int nb) {
+  const int n = mc * nb, nth = blockDim.x;
+  for (int base = threadIdx.x; base < n; base += 4 * nth) {
+    float2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = base + u * nth;
+      if (e < n) {
+        const int mm = e / nb, jl = e - mm * nb;
+        v[u] = p.Yt[(size_t)(m0 + mm) * p.Ny + lo + jl];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = base + u * nth;
+      if (e < n) YB[e] = v[u];
+    }
+  }
+}
+
+// (B^H B)[q][r] and P[m][r] = sum over this CTA's rows j of Yt[m][j] conj(B[j][r])
+template <int OWN>
+__device__ void partials_B(const FrameParams& p, SM& sm, int cta, bool do_mb, bool do_p) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int Nx = p.Nx, R = p.R, MC = p.MC, RR = R * R;
+  const int s = sm.misc[0];
+  const Slice bs = slice_of(p.Ny, p.C, cta);
+  const int nb = bs.hi - bs.lo;
+  if (do_mb) {
+    float2* pmb = p.partMB + (size_t)cta * RR;
+#pragma unroll
+    for (int o = 0; o < OWN; ++o) {
+      const int e = tid + o * nth;
+      if (e < RR) {
+        const int q = e / R, r = e - q * R;
+        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+        int jl = 0;
+        for (; jl + 1 < nb; jl += 2) {
+          cfmac(a0, sm.B[jl * R + q], sm.B[jl * R + r]);
+          cfmac(a1, sm.B[(jl + 1) * R + q], sm.B[(jl + 1) * R + r]);
+        }
+        if (jl < nb) cfmac(a0, sm.B[jl * R + q], sm.B[jl * R + r]);
+        pmb[e] = cadd(a0, a1);
+      }
+    }
+  }
+  if (!do_p) return;
+  float2* pp = p.partP + (size_t)cta * Nx * R;
+  float2* YB = s <= MC ? sm.yb : sm.chunk;
+  for (int m0 = 0; m0 < s; m0 += MC) {
+    const int mc = min(MC, s - m0);
+    if (s > MC || !sm.yb_ready) load_yb(p, YB, m0, mc, bs.lo, nb);
+    __syncthreads();
+    if (s <= MC) sm.yb_ready = true;
+    for (int e = tid; e < mc * R; e += nth) {
+      const int mm = e / R, r = e - mm * R;
+      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+      int jl = 0;
+      for (; jl + 1 < nb; jl += 2) {
+        cfma(a0, YB[mm * nb + jl], cconj(sm.B[jl * R + r]));
+        cfma(a1, YB[mm * nb + jl + 1], cconj(sm.B[(jl + 1) * R + r]));
+      }
+      if (jl < nb) cfma(a0, YB[mm * nb + jl], cconj(sm.B[jl * R + r]));
+      pp[(m0 + mm) * R + r] = cadd(a0, a1);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// step 0: ingest the frame: inverse row transforms of this CTA's slice of S (Yt), the
+// anchors A[t-1], B[t-1], and partial sums of Ahat_S, ||a||^2 and B^H B over this CTA's rows
+// ---------------------------------------------------------------------------------
+template <int OWN>
 __device__ void step_ingest(const FrameParams& p, SM& sm, int cta) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int Nx = p.Nx, Ny = p.Ny, R = p.R, C = p.C;
   const int s = sm.misc[0];
   const Slice ms = slice_of(s, C, cta);
-  // acquired rows times conj(F_Ny) for this CTA's slice of S (inverse row transforms)
   const int fft_rows = max(1, p.lay.chunk_f2 / (2 * Ny));
   int bad = 0;
   for (int m0 = ms.lo; m0 < ms.hi; m0 += fft_rows) {
     const int nr = min(fft_rows, ms.hi - m0);
     float2* buf = sm.chunk;
     float2* tmp = sm.chunk + fft_rows * Ny;
-    for (int e = tid; e < nr * Ny; e += nth) {
-      const int mr = e / Ny;
-      const size_t src = p.full_frame ? (size_t)sm.rows[m0 + mr] * Ny + (e - mr * Ny) : (size_t)m0 * Ny + e;
-      const float2 v = p.yrows[src];
-      if (!isfinite(v.x) || !isfinite(v.y)) bad = 1;
-      buf[e] = v;
+    for (int base = tid; base < nr * Ny; base += 4 * nth) {
+      float2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = base + u * nth;
+        if (e < nr * Ny) {
+          const int mr = e / Ny;
+          const size_t src = p.full_frame ? (size_t)sm.rows[m0 + mr] * Ny + (e - mr * Ny) : (size_t)m0 * Ny + e;
+          v[u] = p.yrows[src];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = base + u * nth;
+        if (e < nr * Ny) {
+          if (!isfinite(v[u].x) || !isfinite(v[u].y)) bad = 1;
+          buf[e] = v[u];
+        }
+      }
     }
     __syncthreads();
     float2* res = fft_smem(buf, tmp, p.plan_y, nr, Ny, sm.Wy, +1, tid, nth);
@@ -286,93 +493,8 @@ __device__ void step_ingest(const FrameParams& p, SM& sm, int cta) {
   const Slice as = slice_of(Nx, C, cta), bs = slice_of(Ny, C, cta);
   for (int e = as.lo * R + tid; e < as.hi * R; e += nth) p.A0[e] = p.A[e];
   for (int e = bs.lo * R + tid; e < bs.hi * R; e += nth) p.B0[e] = p.B[e];
-  // outputs of this CTA: P[m][r] and Ahat_S[m][r] for m in its slice of S, (B^H B)[q][r]
-  // for q in its slice of [0, R), and ||a_r||^2 (last CTA). Rows of A and B stream
-  // through shared memory in chunks; each thread owns up to two outputs per pass and
-  // keeps two accumulators per output.
-  const Slice qs = slice_of(R, C, cta);
-  const int nm = ms.hi - ms.lo, nq = qs.hi - qs.lo;
-  const int nP = nm * R, nAh = nm * R, nMB = nq * R, nNA = (cta == C - 1) ? R : 0;
-  const int total = nP + nAh + nMB + nNA;
-  float2* AhS = p.AhS[0];
-  const int NR = max(Nx, Ny);
-  const int nch = max(1, min(NR, p.lay.chunk_f2 / (2 * R)));
-  float2* As = sm.chunk;            // nch x R rows of A
-  float2* Bs = sm.chunk + nch * R;  // nch x R rows of B
-  __syncthreads();
-  for (int o0 = 0; o0 < total; o0 += 2 * nth) {
-    int kind[2], row[2], col[2];
-    float2 a0[2], a1[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int o = o0 + tid + u * nth;
-      a0[u] = a1[u] = make_float2(0.f, 0.f);
-      if (o < nP) {
-        kind[u] = 0; row[u] = ms.lo + o / R; col[u] = o % R;
-      } else if (o < nP + nAh) {
-        kind[u] = 1; row[u] = ms.lo + (o - nP) / R; col[u] = (o - nP) % R;
-      } else if (o < nP + nAh + nMB) {
-        kind[u] = 2; row[u] = qs.lo + (o - nP - nAh) / R; col[u] = (o - nP - nAh) % R;
-      } else if (o < total) {
-        kind[u] = 3; row[u] = 0; col[u] = o - nP - nAh - nMB;
-      } else {
-        kind[u] = 4; row[u] = 0; col[u] = 0;
-      }
-    }
-    for (int j0 = 0; j0 < NR; j0 += nch) {
-      const int nc = min(nch, NR - j0);
-      __syncthreads();
-      for (int e = tid; e < nc * R; e += nth) {
-        const int jj = e / R;
-        As[e] = j0 + jj < Nx ? p.A[j0 * R + e] : make_float2(0.f, 0.f);
-        Bs[e] = j0 + jj < Ny ? p.B[j0 * R + e] : make_float2(0.f, 0.f);
-      }
-      __syncthreads();
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int r = col[u];
-        if (kind[u] == 0) {
-          const float2* yt = p.Yt + (size_t)row[u] * Ny + j0;
-          const int lim = min(nc, Ny - j0);
-          int jj = 0;
-          for (; jj + 1 < lim; jj += 2) {
-            cfma(a0[u], yt[jj], cconj(Bs[jj * R + r]));
-            cfma(a1[u], yt[jj + 1], cconj(Bs[(jj + 1) * R + r]));
-          }
-          if (jj < lim) cfma(a0[u], yt[jj], cconj(Bs[jj * R + r]));
-        } else if (kind[u] == 1) {
-          const int i = sm.rows[row[u]];
-          const int lim = min(nc, Nx - j0);
-          int idx = (int)(((long long)i * j0) % Nx);
-          for (int jj = 0; jj < lim; ++jj) {
-            if (jj & 1) cfma(a1[u], sm.Wx[idx], As[jj * R + r]);
-            else cfma(a0[u], sm.Wx[idx], As[jj * R + r]);
-            idx += i;
-            if (idx >= Nx) idx -= Nx;
-          }
-        } else if (kind[u] == 2) {
-          const int q = row[u];
-          int jj = 0;
-          for (; jj + 1 < nc; jj += 2) {
-            cfmac(a0[u], Bs[jj * R + q], Bs[jj * R + r]);
-            cfmac(a1[u], Bs[(jj + 1) * R + q], Bs[(jj + 1) * R + r]);
-          }
-          if (jj < nc) cfmac(a0[u], Bs[jj * R + q], Bs[jj * R + r]);
-        } else if (kind[u] == 3) {
-          for (int jj = 0; jj < nc; ++jj) a0[u].x += cabs2(As[jj * R + r]);
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const float2 v = cadd(a0[u], a1[u]);
-      const int r = col[u];
-      if (kind[u] == 0) p.P[row[u] * R + r] = v;
-      else if (kind[u] == 1) AhS[row[u] * R + r] = cscale(v, p.isx);
-      else if (kind[u] == 2) p.MB[row[u] * R + r] = v;
-      else if (kind[u] == 3) p.nA[0][r] = v.x;
-    }
-  }
+  partials_A(p, sm, cta, sm.chunk, false);
+  partials_B<OWN>(p, sm, cta, true, false);
   __syncthreads();
   if (tid == 0) p.status[1 + cta] = sm.misc[1];
   if (cta == 0 && tid == 0) {
@@ -440,6 +562,8 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
   float2 g0[OWN], g1[OWN], h0 = make_float2(0.f, 0.f), h1 = make_float2(0.f, 0.f);
 #pragma unroll
   for (int o = 0; o < OWN; ++o) g0[o] = g1[o] = make_float2(0.f, 0.f);
+  float2* MBs = sm.GJb;   // B^H B staged for the Gram (GJb is free until the solve)
+  for (int e = tid; e < RR; e += nth) MBs[e] = p.MB[e];
   for (int m0 = 0; m0 < s; m0 += MC) {
     const int mc = min(MC, s - m0);
     for (int e = tid; e < mc * R; e += nth) {
@@ -478,7 +602,7 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
   for (int o = 0; o < OWN; ++o) {
     const int e = tid + o * nth;
     if (e < RR) {
-      float2 v = cmul(cadd(g0[o], g1[o]), p.MB[e]);
+      float2 v = cmul(cadd(g0[o], g1[o]), MBs[e]);
       if (orow[o] == ocol[o]) v = make_float2(v.x + fmu, 0.f);
       sm.Gf[e] = v;
     }
@@ -486,8 +610,12 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
   if (tid < R) sm.h[tid] = cadd(h0, h1);
   __syncthreads();
   ridge_solve<OWN>(sm, R, nullptr, nullptr, p.refine, 1e-20f);
+  // B^H B again in shared memory (the solve overwrote GJb)
+  float2* MBt = sm.GJb;
+  for (int e = tid; e < RR; e += nth) MBt[e] = p.MB[e];
+  __syncthreads();
   // alpha_A = sum |gamma_r|^2 ||b_r||^2 + rho (||b_r||^2 = (B^H B)[r][r])
-  step_coefficients(p, sm, (const float*)p.MB, 2 * (R + 1), p.sf[SF_RHO], p.sf[SF_ABAR_A]);
+  step_coefficients(p, sm, (const float*)MBt, 2 * (R + 1), p.sf[SF_RHO], p.sf[SF_ABAR_A]);
   if (cta == 0)
     for (int r = tid; r < R; r += nth) {
       p.gamma[r] = sm.gam[r];
@@ -498,7 +626,7 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
   float2* gM = sm.GJa;
   for (int e = tid; e < RR; e += nth) {
     const int q = e / R, r = e - q * R;
-    gM[e] = cmul(sm.gam[q], p.MB[r * R + q]);
+    gM[e] = cmul(sm.gam[q], MBt[r * R + q]);
   }
   __syncthreads();
   if (cta == 0 && tid == 0) p.sf[SF_ALPHA_A] = sm.ds[0];
@@ -508,12 +636,14 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
 #pragma unroll
   for (int o = 0; o < OWN; ++o) t0[o] = t1[o] = make_float2(0.f, 0.f);
   const int NO = na * R;
+  const bool one_chunk = s <= MC;   // AH and PC still hold the whole of Ahat_S and P
   for (int m0 = 0; m0 < s; m0 += MC) {
     const int mc = min(MC, s - m0);
-    for (int e = tid; e < mc * R; e += nth) {
-      AH[e] = AhS[m0 * R + e];
-      PC[e] = p.P[m0 * R + e];
-    }
+    if (!one_chunk)
+      for (int e = tid; e < mc * R; e += nth) {
+        AH[e] = AhS[m0 * R + e];
+        PC[e] = p.P[m0 * R + e];
+      }
     fill_twiddles(p, sm, TW, m0, mc, as.lo, na);
     __syncthreads();
     for (int e = tid; e < mc * R; e += nth) {
@@ -567,29 +697,7 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
   }
   __syncthreads();
   // partial sums over this CTA's rows: Ahat'_S[m][r] and ||a'_r||^2
-  float2* part = p.partA + (size_t)cta * Nx * R;
-  for (int m0 = 0; m0 < s; m0 += MC) {
-    const int mc = min(MC, s - m0);
-    fill_twiddles(p, sm, TW, m0, mc, as.lo, na);
-    __syncthreads();
-    for (int e = tid; e < mc * R; e += nth) {
-      const int mm = e / R, r = e - mm * R;
-      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-      int nl = 0;
-      for (; nl + 1 < na; nl += 2) {
-        cfma(a0, TW[mm * na + nl], sm.A[nl * R + r]);
-        cfma(a1, TW[mm * na + nl + 1], sm.A[(nl + 1) * R + r]);
-      }
-      if (nl < na) cfma(a0, TW[mm * na + nl], sm.A[nl * R + r]);
-      part[(m0 + mm) * R + r] = cscale(cadd(a0, a1), p.isx);
-    }
-    __syncthreads();
-  }
-  for (int r = tid; r < R; r += nth) {
-    float acc = 0.f;
-    for (int nl = 0; nl < na; ++nl) acc += cabs2(sm.A[nl * R + r]);
-    p.partNA[cta * R + r] = acc;
-  }
+  partials_A(p, sm, cta, TW, one_chunk);
 }
 
 // sum of C per-CTA partials stride apart, loads issued four at a time
@@ -643,7 +751,7 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) 
   const Slice bs = slice_of(Ny, C, cta);
   const int nb = bs.hi - bs.lo;
   float2* AH = sm.chunk;                 // MC x R
-  float2* YB = AH + MC * R;              // MC x nb
+  float2* YB = s <= MC ? sm.yb : AH + MC * R;   // MC x nb
   const int RR = R * R;
   int orow[OWN], ocol[OWN];
 #pragma unroll
@@ -652,7 +760,11 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) 
     orow[o] = e / R;
     ocol[o] = e - orow[o] * R;
   }
-  for (int r = tid; r < R; r += nth) sm.gam[r] = p.gamma[r];
+  float* nAs = (float*)sm.tmpv;   // ||a_r||^2 in shared memory
+  for (int r = tid; r < R; r += nth) {
+    sm.gam[r] = p.gamma[r];
+    nAs[r] = nA[r];
+  }
   // MA = Ahat^H Ahat (thread-owned entries) and U[j][r] = sum_m Yt[m][j] conj(Ahat[m][r])
   float2 ma[OWN], u[OWN];
 #pragma unroll
@@ -661,11 +773,9 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) 
   for (int m0 = 0; m0 < s; m0 += MC) {
     const int mc = min(MC, s - m0);
     for (int e = tid; e < mc * R; e += nth) AH[e] = Ah[m0 * R + e];
-    for (int e = tid; e < mc * nb; e += nth) {
-      const int mm = e / nb, jl = e - mm * nb;
-      YB[e] = p.Yt[(size_t)(m0 + mm) * Ny + bs.lo + jl];
-    }
+    if (s > MC || !sm.yb_ready) load_yb(p, YB, m0, mc, bs.lo, nb);
     __syncthreads();
+    if (s <= MC) sm.yb_ready = true;
     int mr[OWN], mq[OWN], uj[OWN], ur[OWN];
 #pragma unroll
     for (int o = 0; o < OWN; ++o) {
@@ -692,7 +802,7 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) 
     if (e < RR) gMA[ocol[o] * R + orow[o]] = cmul(sm.gam[ocol[o]], ma[o]);
   }
   // alpha_B = sum |gamma_r|^2 ||a_r||^2 + rho
-  step_coefficients(p, sm, nA, 1, p.sf[SF_RHO], p.sf[SF_ABAR_B]);
+  step_coefficients(p, sm, nAs, 1, p.sf[SF_RHO], p.sf[SF_ABAR_B]);
   __syncthreads();
   const float c0 = sm.fs[0], c1 = sm.fs[1], c2 = sm.fs[2], frho = sm.fs[3];
   // B step: T_B = U - B diag(gamma) MA^T, grad = rho B - T_B diag(conj gamma)
@@ -737,41 +847,28 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) 
   }
   __syncthreads();
   // partials over this CTA's rows: B'^H B' and Yt conj(B')
-  float2* pmb = p.partMB + (size_t)cta * RR;
-#pragma unroll
-  for (int o = 0; o < OWN; ++o) {
-    const int e = tid + o * nth;
-    if (e < RR) {
-      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-      int jl = 0;
-      for (; jl + 1 < nb; jl += 2) {
-        cfmac(a0, sm.B[jl * R + orow[o]], sm.B[jl * R + ocol[o]]);
-        cfmac(a1, sm.B[(jl + 1) * R + orow[o]], sm.B[(jl + 1) * R + ocol[o]]);
-      }
-      if (jl < nb) cfmac(a0, sm.B[jl * R + orow[o]], sm.B[jl * R + ocol[o]]);
-      pmb[e] = cadd(a0, a1);
+  partials_B<OWN>(p, sm, cta, true, true);
+}
+
+// reduce every partial of the ingest: Ahat_S, ||a||^2, B^H B, P
+__device__ void step_reduce_all(const FrameParams& p, SM& sm, int cta) {
+  const int R = p.R, C = p.C, Nx = p.Nx;
+  const int s = sm.misc[0];
+  const int E1 = s * R, E2 = E1 + R, E3 = E2 + R * R, E = E3 + s * R;
+  const Slice es = slice_of(E, C, cta);
+  for (int e = es.lo + threadIdx.x; e < es.hi; e += blockDim.x) {
+    if (e < E1) {
+      p.AhS[0][e] = sum_partials(p.partA + e, (size_t)Nx * R, C);
+    } else if (e < E2) {
+      const int r = e - E1;
+      float acc = 0.f;
+      for (int c = 0; c < C; ++c) acc += p.partNA[c * R + r];
+      p.nA[0][r] = acc;
+    } else if (e < E3) {
+      p.MB[e - E2] = sum_partials(p.partMB + (e - E2), (size_t)R * R, C);
+    } else {
+      p.P[e - E3] = sum_partials(p.partP + (e - E3), (size_t)Nx * R, C);
     }
-  }
-  float2* pp = p.partP + (size_t)cta * Nx * R;
-  for (int m0 = 0; m0 < s; m0 += MC) {
-    const int mc = min(MC, s - m0);
-    for (int e = tid; e < mc * nb; e += nth) {
-      const int mm = e / nb, jl = e - mm * nb;
-      YB[e] = p.Yt[(size_t)(m0 + mm) * Ny + bs.lo + jl];
-    }
-    __syncthreads();
-    for (int e = tid; e < mc * R; e += nth) {
-      const int mm = e / R, r = e - mm * R;
-      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-      int jl = 0;
-      for (; jl + 1 < nb; jl += 2) {
-        cfma(a0, YB[mm * nb + jl], cconj(sm.B[jl * R + r]));
-        cfma(a1, YB[mm * nb + jl + 1], cconj(sm.B[(jl + 1) * R + r]));
-      }
-      if (jl < nb) cfma(a0, YB[mm * nb + jl], cconj(sm.B[jl * R + r]));
-      pp[(m0 + mm) * R + r] = cadd(a0, a1);
-    }
-    __syncthreads();
   }
 }
 
@@ -804,13 +901,11 @@ __global__ void __launch_bounds__(TTS_THREADS, 1) frame_kernel(FrameParams p, in
   if (tid < 8) sm.misc[tid] = 0;
   // this CTA's rows of the factors (and of the anchors after the ingest step)
   const Slice as = slice_of(p.Nx, p.C, cta), bs = slice_of(p.Ny, p.C, cta);
-  for (int e = tid; e < (as.hi - as.lo) * R; e += nth) {
-    sm.A[e] = p.A[as.lo * R + e];
-    if (step_begin > 0) sm.A0[e] = p.A0[as.lo * R + e];
-  }
-  for (int e = tid; e < (bs.hi - bs.lo) * R; e += nth) {
-    sm.B[e] = p.B[bs.lo * R + e];
-    if (step_begin > 0) sm.B0[e] = p.B0[bs.lo * R + e];
+  block_copy(sm.A, p.A + as.lo * R, (as.hi - as.lo) * R);
+  block_copy(sm.B, p.B + bs.lo * R, (bs.hi - bs.lo) * R);
+  if (step_begin > 0) {
+    block_copy(sm.A0, p.A0 + as.lo * R, (as.hi - as.lo) * R);
+    block_copy(sm.B0, p.B0 + bs.lo * R, (bs.hi - bs.lo) * R);
   }
   __syncthreads();
   if (step_begin == 0) {
@@ -849,11 +944,21 @@ __global__ void __launch_bounds__(TTS_THREADS, 1) frame_kernel(FrameParams p, in
       }
     }
     if (step == 0) {
-      step_ingest(p, sm, cta);
+      step_ingest<OWN>(p, sm, cta);
       __syncthreads();
       continue;
     }
-    const int k = (step - 1) / 4, sub = (step - 1) % 4;
+    if (step == 1) {
+      partials_B<OWN>(p, sm, cta, false, true);
+      __syncthreads();
+      continue;
+    }
+    if (step == 2) {
+      step_reduce_all(p, sm, cta);
+      __syncthreads();
+      continue;
+    }
+    const int k = (step - 3) / 4, sub = (step - 3) % 4;
     if (sub == 0) step_solve_A<OWN>(p, sm, cta, k);
     else if (sub == 1) step_reduce_A(p, sm, cta, k);
     else if (sub == 2) step_B<OWN>(p, sm, cta, k, k == p.K - 1);
@@ -871,11 +976,14 @@ __global__ void __launch_bounds__(TTS_THREADS, 1) ridge_kernel(const double2* G,
   SM sm;
   float2* base = (float2*)smem_raw;
   const int RR = R * R;
+  const int Rp = (R + 15) & ~15;
   sm.Gf = base;
-  sm.GJa = base + RR;
-  sm.GJb = base + 2 * RR;
-  float2* Glo = base + 3 * RR;
-  sm.gam = base + 4 * RR;
+  float2* Glo = base + RR;
+  sm.GJa = base + 2 * RR;
+  sm.GJb = sm.GJa + Rp * Rp;
+  sm.Pk = sm.GJb + Rp * Rp;
+  sm.Tk = sm.Pk + 256;
+  sm.gam = sm.Tk + 16 * Rp;
   sm.glo = sm.gam + R;
   sm.h = sm.gam + 2 * R;
   sm.rr = sm.gam + 3 * R;
@@ -902,7 +1010,8 @@ __global__ void __launch_bounds__(TTS_THREADS, 1) ridge_kernel(const double2* G,
 }  // namespace
 
 int launch_ridge(const double2* G, const double2* h, int R, double2* gamma, cudaStream_t st) {
-  const int smem = (int)(sizeof(float2) * (4 * R * R + 6 * R));
+  const int Rp = (R + 15) & ~15;
+  const int smem = (int)(sizeof(float2) * (2 * R * R + 2 * Rp * Rp + 256 + 16 * Rp + 6 * R));
   if (cudaFuncSetAttribute(ridge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return TTS_ECUDA;
   ridge_kernel<<<1, TTS_THREADS, smem, st>>>(G, h, R, 12, gamma);
@@ -922,7 +1031,7 @@ int frame_configure(FrameParams& p, int requested_C) {
     for (int MC : {32, 16, 8}) {
       const int rA = (p.Nx + C - 1) / C, rB = (p.Ny + C - 1) / C;
       if (rA * p.R > TTS_MAX_OWN * TTS_THREADS || rB * p.R > TTS_MAX_OWN * TTS_THREADS) continue;
-      if (p.R * p.R > TTS_MAX_OWN * TTS_THREADS) continue;
+      if (((p.R + 15) & ~15) * ((p.R + 15) & ~15) > TTS_MAX_OWN * TTS_THREADS) continue;
       const FrameLayout L = frame_layout(p.Nx, p.Ny, p.R, rA, rB, MC);
       if (L.bytes <= maxsm) {
         p.C = C;
@@ -978,7 +1087,8 @@ static int launch_frame_t(const FrameParams& p, int launch_mode, cudaStream_t st
 // outputs each thread owns: R x R entries of the Gram and Gauss-Jordan updates, and the
 // (row, r) entries of this CTA's rows of A and B
 int frame_own(const FrameParams& p) {
-  const int n = std::max(p.R * p.R, std::max(p.rA, p.rB) * p.R);
+  const int Rp = (p.R + 15) & ~15;
+  const int n = std::max(Rp * Rp, std::max(p.rA, p.rB) * p.R);
   const int own = (n + TTS_THREADS - 1) / TTS_THREADS;
   return own <= 1 ? 1 : own <= 2 ? 2 : own <= 4 ? 4 : 8;
 }

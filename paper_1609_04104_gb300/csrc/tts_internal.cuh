@@ -51,6 +51,28 @@ __host__ __device__ __forceinline__ double2 zmulc(double2 a, double2 b) {  // co
 __host__ __device__ __forceinline__ double2 zsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 
 // ------------------------------------------------------------------------------------
+// Block-wide copy of n elements with U loads in flight per thread before the stores, so
+// that global-memory latency is paid once per U elements rather than per element.
+// ------------------------------------------------------------------------------------
+template <typename T, int U = 4>
+__device__ __forceinline__ void block_copy(T* __restrict__ dst, const T* __restrict__ src, int n) {
+  const int nth = blockDim.x;
+  for (int base = threadIdx.x; base < n; base += U * nth) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = base + u * nth;
+      if (e < n) v[u] = src[e];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = base + u * nth;
+      if (e < n) dst[e] = v[u];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
 // Mixed-radix Stockham autosort FFT in shared memory.
 //
 // Unnormalised DFT  y_k = sum_n x_n w^{nk},  w = exp(sign * 2 pi i / N),
@@ -91,24 +113,32 @@ __device__ __forceinline__ float2 tw(const float2* W, int idx, int sign) {
   return sign < 0 ? w : make_float2(w.x, -w.y);
 }
 
+// n / d for 0 <= n < 2^32 / d with a precomputed multiplier m = floor((2^32 - 1) / d) + 1
+// (exact in that range: n m / 2^32 lies in [n/d, n/d + n/2^32) and frac(n/d) <= 1 - 1/d).
+// For d = 1 the multiplier wraps to 0, which stands for "divide by one".
+__device__ __forceinline__ unsigned fast_div(unsigned n, unsigned m) { return m ? __umulhi(n, m) : n; }
+__host__ __device__ __forceinline__ unsigned div_magic(unsigned d) { return 0xFFFFFFFFu / d + 1u; }
+
 template <int P>
 __device__ __forceinline__ void fft_stage(const float2* x, float2* y, int N, int Ns, int batch, int bstride,
                                           const float2* W, int sign, int tid, int nthreads) {
   const int Np = N / P;
   const int step = N / (Ns * P);
   const int items = batch * Np;
+  const unsigned mNp = div_magic((unsigned)Np), mNs = div_magic((unsigned)Ns);
   for (int it = tid; it < items; it += nthreads) {
-    const int b = it / Np;
+    const int b = (int)fast_div((unsigned)it, mNp);
     const int j = it - b * Np;
     const float2* xb = x + b * bstride;
     float2* yb = y + b * bstride;
-    const int k = j % Ns;
+    const int jd = (int)fast_div((unsigned)j, mNs);
+    const int k = j - jd * Ns;
     float2 v[P];
 #pragma unroll
     for (int q = 0; q < P; ++q) v[q] = xb[j + q * Np];
 #pragma unroll
-    for (int q = 1; q < P; ++q) v[q] = cmul(v[q], tw(W, k * q * step, sign));
-    const int base = (j / Ns) * Ns * P + k;
+    for (int q = 1; q < P; ++q) v[q] = cmul(v[q], tw(W, k * q * step, sign));   // k q step < N
+    const int base = jd * Ns * P + k;
     if (P == 2) {
       yb[base] = cadd(v[0], v[1]);
       yb[base + Ns] = csub(v[0], v[1]);
@@ -198,7 +228,7 @@ enum { SF_W = 0, SF_RHO = 1, SF_ABAR_A = 2, SF_ABAR_B = 3, SF_ALPHA_A = 4, SF_AL
 // Shared-memory layout of the frame kernel (bytes offsets), computed identically on the
 // host (launch size) and the device (carving).
 struct FrameLayout {
-  int Wx, Wy, rows, misc, red, myA, myA0, myB, myB0, Gf, GJa, GJb, vec, chunk;
+  int Wx, Wy, rows, misc, red, myA, myA0, myB, myB0, Gf, GJa, GJb, gjx, vec, yb, chunk;
   int chunk_f2;   // capacity of the chunk region in float2
   int bytes;
 };
@@ -222,10 +252,13 @@ __host__ __device__ inline FrameLayout frame_layout(int Nx, int Ny, int R, int r
   L.myA0 = take(f2 * rA * R);
   L.myB = take(f2 * rB * R);
   L.myB0 = take(f2 * rB * R);
+  const int Rp = (R + 15) & ~15;   // ridge system padded to 16 x 16 blocks
   L.Gf = take(f2 * R * R);
-  L.GJa = take(f2 * R * R);
-  L.GJb = take(f2 * R * R);
+  L.GJa = take(f2 * Rp * Rp);
+  L.GJb = take(f2 * Rp * Rp);
+  L.gjx = take(f2 * (256 + 16 * Rp));
   L.vec = take(f2 * (6 * R + 16));
+  L.yb = take(f2 * MC * rB);       // Yt block of this CTA's B rows, kept when |S| <= MC
   const int rmax = rA > rB ? rA : rB;
   int cf = MC * (rmax + rB + 3 * R);
   if (cf < 2 * Ny) cf = 2 * Ny;     // at least one row transform (ping-pong)
@@ -271,10 +304,11 @@ struct FrameParams {
   const float2* Wy;               // exp(-2 pi i k / Ny)
 };
 
-// Steps of one frame: 0 = ingest; then per MM iteration k: 1 + 4k + {0: ridge solve and
-// A step, 1: reduce the A partials, 2: B step, 3: reduce the B partials}; the last
-// iteration has no step 3.
-__host__ __device__ inline int frame_num_steps(int K) { return 4 * K; }
+// Steps of one frame: 0 = ingest (row transforms, anchors, partial sums over the rows of
+// A and of B), 1 = partial sums of P, 2 = reduce all partials; then per MM iteration k:
+// 3 + 4k + {0: ridge solve and A step, 1: reduce the A partials, 2: B step, 3: reduce the
+// B partials}; the last iteration has no step 3.
+__host__ __device__ inline int frame_num_steps(int K) { return 4 * K + 2; }
 
 // host-side launchers (tts_kernels.cu)
 int launch_frame(const FrameParams& p, int launch_mode, cudaStream_t st);

@@ -16,11 +16,28 @@ __global__ void __launch_bounds__(256) image_kernel(const float2* __restrict__ A
   float2* sB = sA + 32 * (R + 1);     // 32 x (R+1)
   const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
   const int tid = threadIdx.x;
-  for (int e = tid; e < 32 * R; e += blockDim.x) {
-    const int ii = e / R, r = e - ii * R;
-    const int i = i0 + ii, j = j0 + ii;
-    sA[ii * (R + 1) + r] = i < Nx ? cmul(A[i * R + r], gamma[r]) : make_float2(0.f, 0.f);
-    sB[ii * (R + 1) + r] = j < Ny ? B[j * R + r] : make_float2(0.f, 0.f);
+  for (int base = tid; base < 32 * R; base += 4 * blockDim.x) {
+    float2 va[4], vb[4], vg[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = base + u * blockDim.x;
+      if (e < 32 * R) {
+        const int ii = e / R, r = e - ii * R;
+        const int i = i0 + ii, j = j0 + ii;
+        va[u] = i < Nx ? A[i * R + r] : make_float2(0.f, 0.f);
+        vb[u] = j < Ny ? B[j * R + r] : make_float2(0.f, 0.f);
+        vg[u] = gamma[r];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = base + u * blockDim.x;
+      if (e < 32 * R) {
+        const int ii = e / R, r = e - ii * R;
+        sA[ii * (R + 1) + r] = cmul(va[u], vg[u]);
+        sB[ii * (R + 1) + r] = vb[u];
+      }
+    }
   }
   __syncthreads();
   const int jj = tid & 31, ib = tid >> 5;  // each thread: column jj, rows ib, ib+8, ib+16, ib+24
@@ -89,9 +106,24 @@ __global__ void __launch_bounds__(SAMPLER_THREADS) sampler_kernel(
     for (int r0 = 0; r0 < R; r0 += fft_cols) {
       const int nc = min(fft_cols, R - r0);
       // coalesced along the rows of A, transposed into columns
-      for (int e = tid; e < nc * Nx; e += blockDim.x) {
-        const int n = e / nc, c = e - n * nc;
-        buf[c * ld + n] = A[n * R + r0 + c];
+      for (int base = tid; base < nc * Nx; base += 8 * blockDim.x) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = base + u * blockDim.x;
+          if (e < nc * Nx) {
+            const int n = e / nc, c = e - n * nc;
+            v[u] = A[n * R + r0 + c];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = base + u * blockDim.x;
+          if (e < nc * Nx) {
+            const int n = e / nc, c = e - n * nc;
+            buf[c * ld + n] = v[u];
+          }
+        }
       }
       __syncthreads();
       float2* res = fft_smem(buf, buf + fft_cols * ld, plan, nc, ld, W, -1, tid, blockDim.x);
@@ -109,7 +141,11 @@ __global__ void __launch_bounds__(SAMPLER_THREADS) sampler_kernel(
       }
       __syncthreads();
     }
-    const double inv = 1.0 / ((double)R * (double)(Nx + Ny));
+    // one FP64 division for the block (FP64 is slow on this part), then FMAs
+    double* dinv = (double*)(misc + 4);
+    if (tid == 0) *dinv = 1.0 / ((double)R * (double)(Nx + Ny));
+    __syncthreads();
+    const double inv = *dinv;
     for (int i = tid; i < Nx; i += blockDim.x) p[i] = ((double)Ny * (double)rowacc[i] + (double)R) * inv;
   } else {
     // uniform or variable density: weights then a fixed-order tree normalisation
@@ -135,7 +171,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS) sampler_kernel(
     }
     const double total = tsum[0];
     __syncthreads();
-    for (int i = tid; i < Nx; i += blockDim.x) p[i] = p[i] / total;
+    for (int i = tid; i < Nx; i += blockDim.x) p[i] = p[i] / total;   // exact division: fixed policies only
   }
   __syncthreads();
   if (p_out != nullptr)

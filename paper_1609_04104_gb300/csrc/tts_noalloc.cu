@@ -102,7 +102,7 @@ extern "C" int tts_push_frame_noalloc(const tts_frame_args* a, void* cuda_stream
   if (scratch_bytes(Nx, Ny, R, p.C) > sizeof(g_noalloc_scratch))
     return na_fail(TTS_EINVAL, "tts_push_frame_noalloc: problem exceeds the fixed scratch");
   p.K = a->mm_iters;
-  p.refine = 6;
+  p.refine = 4;
   p.jacobi = a->update == TTS_UPDATE_JACOBI;
   p.lf = a->lambda_forget;
   p.mu = a->mu;
