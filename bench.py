@@ -31,6 +31,22 @@ sys.path.insert(0, ROOT)
 METRIC = "frames/s and p50/p99 frame latency at image NRMSE<=1e-4 vs plain per-frame path"
 UNIT = "frames/s"
 
+# DRAM traffic of one fused frame_kernel launch on an informative cine-256 frame (|S| = 32),
+# dram__bytes_read.sum + dram__bytes_write.sum from the ncu capture summarised in
+# profiles/frame_kernel_cine256.md, valid only for the kernel source with this hash.
+FRAME_TRAFFIC_BYTES = 410624
+FRAME_TRAFFIC_SRC_SHA = "73b3d8a927cb1c42"
+
+
+def frame_traffic():
+    import hashlib
+    src = os.path.join(ROOT, "paper_1609_04104_gb300", "csrc", "tts_frame.cu")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return FRAME_TRAFFIC_BYTES if h == FRAME_TRAFFIC_SRC_SHA else None
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -45,6 +61,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--cpu-sample-frames", type=int, default=8)
+    ap.add_argument("--fft2d", action="store_true", help="time the batched unitary 2D DFT kernel instead")
+    ap.add_argument("--fft-n", type=int, default=256)
+    ap.add_argument("--fft-batch", type=int, default=512)
     return ap.parse_args()
 
 
@@ -263,7 +282,8 @@ def run_tts(args, rank, world):
     bytes_per_launch = float(np.mean([(Nx if t < nfull else S) * Ny * 8 + Nx + 2 * K * (Nx + Ny) * R * 8
                                       for t in range(T)]))
     roof = {"bound": "alu", "kernel": "frame_kernel", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved / peak_tflops, "traffic": None,
+            "frac": achieved / peak_tflops, "traffic": frame_traffic(),
+            "traffic_note": "DRAM bytes per fused launch on an informative frame (|S|=32), ncu",
             "flops_per_launch": flops_per_launch, "algorithmic_bytes_per_launch": bytes_per_launch,
             "achieved_gbs": bytes_per_launch / kmean / 1e9, "avg_launch_us": kmean * 1e6,
             "peak_note": "FP32 SIMT peak 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived, not measured)"}
@@ -362,8 +382,49 @@ def run_reference(args, rank, world):
     }
 
 
+def run_fft2d(args):
+    """Batched unitary 2D DFT (tts_fft2d) on a batch larger than L2: algorithmic bytes are
+    one read and one write of every image (16 N^2 bytes per image)."""
+    import torch
+
+    from paper_1609_04104_gb300 import tts
+    tts.load()
+    n, b = args.fft_n, args.fft_batch
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn((b, n, n), dtype=torch.complex64, device="cuda", generator=g)
+    y = torch.empty_like(x)
+    st = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        tts.tts_fft2d(x, y, stream=st)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(args.steps):
+        e0.record(st)
+        tts.tts_fft2d(x, y, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+    t = float(np.median(times))
+    algo = 2.0 * b * n * n * 8
+    peak = 6704.5
+    try:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        pass
+    achieved = algo / t / 1e9
+    return {"metric": "batched unitary 2D DFT throughput", "value": b / t, "unit": "images/s",
+            "config": {"workload": f"fft2d_{n}x{n}_batch{b}", "bytes_per_call": algo, "l2": "working set > L2"},
+            "ms_per_call": t * 1e3, "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                                                 "unit": "GB/s", "frac": achieved / peak,
+                                                 "note": "algorithmic bytes 16 N^2 per image; two passes move 32 N^2"}}
+
+
 def main():
     args = parse()
+    if args.fft2d:
+        print(json.dumps(run_fft2d(args)))
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
