@@ -455,12 +455,13 @@ __device__ void step_ingest(const FrameParams& p, SM& sm, int cta) {
   const int Nx = p.Nx, Ny = p.Ny, R = p.R, C = p.C;
   const int s = sm.misc[0];
   const Slice ms = slice_of(s, C, cta);
-  const int fft_rows = max(1, p.lay.chunk_f2 / (2 * Ny));
+  const int bsy = fsz(Ny);   // padded row stride of the transform buffers
+  const int fft_rows = max(1, p.lay.chunk_f2 / (2 * bsy));
   int bad = 0;
   for (int m0 = ms.lo; m0 < ms.hi; m0 += fft_rows) {
     const int nr = min(fft_rows, ms.hi - m0);
     float2* buf = sm.chunk;
-    float2* tmp = sm.chunk + fft_rows * Ny;
+    float2* tmp = sm.chunk + fft_rows * bsy;
     for (int base = tid; base < nr * Ny; base += 4 * nth) {
       float2 v[4];
 #pragma unroll
@@ -477,13 +478,17 @@ __device__ void step_ingest(const FrameParams& p, SM& sm, int cta) {
         const int e = base + u * nth;
         if (e < nr * Ny) {
           if (!isfinite(v[u].x) || !isfinite(v[u].y)) bad = 1;
-          buf[e] = v[u];
+          const int mr = e / Ny;
+          buf[mr * bsy + fpad(e - mr * Ny)] = v[u];
         }
       }
     }
     __syncthreads();
-    float2* res = fft_smem(buf, tmp, p.plan_y, nr, Ny, sm.Wy, +1, tid, nth);
-    for (int e = tid; e < nr * Ny; e += nth) p.Yt[(size_t)m0 * Ny + e] = cscale(res[e], p.isy);
+    float2* res = fft_smem(buf, tmp, p.plan_y, nr, bsy, sm.Wy, +1, tid, nth);
+    for (int e = tid; e < nr * Ny; e += nth) {
+      const int mr = e / Ny;
+      p.Yt[(size_t)m0 * Ny + e] = cscale(res[mr * bsy + fpad(e - mr * Ny)], p.isy);
+    }
     __syncthreads();
   }
   if (bad) atomicOr(&sm.misc[1], 1);
@@ -897,7 +902,7 @@ __global__ void __launch_bounds__(TTS_THREADS, 1) frame_kernel(FrameParams p, in
   const int cta = blockIdx.x;
   const int R = p.R;
   for (int e = tid; e < p.Nx; e += nth) sm.Wx[e] = p.Wx[e];
-  for (int e = tid; e < p.Ny; e += nth) sm.Wy[e] = p.Wy[e];
+  for (int e = tid; e < p.Ny; e += nth) sm.Wy[fpad(e)] = p.Wy[e];
   if (tid < 8) sm.misc[tid] = 0;
   // this CTA's rows of the factors (and of the anchors after the ingest step)
   const Slice as = slice_of(p.Nx, p.C, cta), bs = slice_of(p.Ny, p.C, cta);

@@ -76,7 +76,8 @@ __device__ __forceinline__ void block_copy(T* __restrict__ dst, const T* __restr
 // Mixed-radix Stockham autosort FFT in shared memory.
 //
 // Unnormalised DFT  y_k = sum_n x_n w^{nk},  w = exp(sign * 2 pi i / N),
-// N = 4^a 2^b 3^c 5^d (radices taken in the order 4, 2, 3, 5). Stage with radix p and
+// N = 16^a 8^b 4^c 2^d 3^e 5^f (radices in that order; 16 and 8 are computed in registers
+// as radix-4 x radix-4 and radix-2 x radix-4). Stage with radix p and
 // Ns points already combined: work item j in [0, N/p) reads x[j + q N/p], q < p,
 // twiddles element q by w_{Ns p}^{(j mod Ns) q}, takes a p-point DFT and writes
 // y[(j / Ns) Ns p + (j mod Ns) + q Ns]. The result is in natural order.
@@ -97,8 +98,8 @@ __host__ __device__ inline FftPlan fft_plan(int N) {
   p.n = N;
   p.nrad = 0;
   int n = N;
-  const int order[4] = {4, 2, 3, 5};
-  for (int o = 0; o < 4; ++o) {
+  const int order[6] = {16, 8, 4, 2, 3, 5};
+  for (int o = 0; o < 6; ++o) {
     while (n % order[o] == 0 && p.nrad < 12) {
       p.rad[p.nrad++] = order[o];
       n /= order[o];
@@ -108,8 +109,14 @@ __host__ __device__ inline FftPlan fft_plan(int N) {
   return p;
 }
 
+// Shared-memory layout of FFT data and FFT twiddle tables: one pad slot per 16 elements,
+// so that the strided Stockham stores y[j P + u] and twiddle reads W[k q] hit distinct banks.
+__host__ __device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
+__host__ __device__ __forceinline__ int fsz(int n) { return n > 0 ? fpad(n - 1) + 1 : 0; }
+
+// twiddle idx of a padded table of exp(-2 pi i k / N)
 __device__ __forceinline__ float2 tw(const float2* W, int idx, int sign) {
-  float2 w = W[idx];
+  float2 w = W[fpad(idx)];
   return sign < 0 ? w : make_float2(w.x, -w.y);
 }
 
@@ -118,6 +125,51 @@ __device__ __forceinline__ float2 tw(const float2* W, int idx, int sign) {
 // For d = 1 the multiplier wraps to 0, which stands for "divide by one".
 __device__ __forceinline__ unsigned fast_div(unsigned n, unsigned m) { return m ? __umulhi(n, m) : n; }
 __host__ __device__ __forceinline__ unsigned div_magic(unsigned d) { return 0xFFFFFFFFu / d + 1u; }
+
+// radix-4 butterfly: out_k = sum_n a_n w_4^{nk} (w_4 = -i forward, +i inverse)
+__device__ __forceinline__ void bfly4(float2 a0, float2 a1, float2 a2, float2 a3, int sign, float2& o0, float2& o1,
+                                      float2& o2, float2& o3) {
+  const float2 s0 = cadd(a0, a2), d0 = csub(a0, a2);
+  const float2 s1 = cadd(a1, a3), d1 = csub(a1, a3);
+  const float2 d1w = sign < 0 ? make_float2(d1.y, -d1.x) : make_float2(-d1.y, d1.x);
+  o0 = cadd(s0, s1);
+  o1 = cadd(d0, d1w);
+  o2 = csub(s0, s1);
+  o3 = csub(d0, d1w);
+}
+
+// 16-point DFT in registers: n = 4 n1 + n2, k = k1 + 4 k2; inner twiddles w_16^{n2 k1}
+// taken from the length-N table (16 divides N)
+__device__ __forceinline__ void dft16(float2* v, const float2* W, int N, int sign) {
+  const int s16 = N / 16;
+  float2 t[16];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    float2 r0, r1, r2, r3;
+    bfly4(v[n2], v[4 + n2], v[8 + n2], v[12 + n2], sign, r0, r1, r2, r3);
+    t[n2 * 4 + 0] = r0;
+    t[n2 * 4 + 1] = n2 == 0 ? r1 : cmul(r1, tw(W, n2 * 1 * s16, sign));
+    t[n2 * 4 + 2] = n2 == 0 ? r2 : cmul(r2, tw(W, n2 * 2 * s16, sign));
+    t[n2 * 4 + 3] = n2 == 0 ? r3 : cmul(r3, tw(W, n2 * 3 * s16, sign));
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+    bfly4(t[0 * 4 + k1], t[1 * 4 + k1], t[2 * 4 + k1], t[3 * 4 + k1], sign, v[k1], v[k1 + 4], v[k1 + 8], v[k1 + 12]);
+}
+
+// 8-point DFT in registers: n = 4 n1 + n2 (n1 < 2), k = k1 + 2 k2; inner twiddles w_8^{n2 k1}
+__device__ __forceinline__ void dft8(float2* v, const float2* W, int N, int sign) {
+  const int s8 = N / 8;
+  float2 t0[4], t1[4];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    t0[n2] = cadd(v[n2], v[4 + n2]);
+    const float2 d = csub(v[n2], v[4 + n2]);
+    t1[n2] = n2 == 0 ? d : cmul(d, tw(W, n2 * s8, sign));
+  }
+  bfly4(t0[0], t0[1], t0[2], t0[3], sign, v[0], v[2], v[4], v[6]);
+  bfly4(t1[0], t1[1], t1[2], t1[3], sign, v[1], v[3], v[5], v[7]);
+}
 
 template <int P>
 __device__ __forceinline__ void fft_stage(const float2* x, float2* y, int N, int Ns, int batch, int bstride,
@@ -135,22 +187,27 @@ __device__ __forceinline__ void fft_stage(const float2* x, float2* y, int N, int
     const int k = j - jd * Ns;
     float2 v[P];
 #pragma unroll
-    for (int q = 0; q < P; ++q) v[q] = xb[j + q * Np];
+    for (int q = 0; q < P; ++q) v[q] = xb[fpad(j + q * Np)];
 #pragma unroll
     for (int q = 1; q < P; ++q) v[q] = cmul(v[q], tw(W, k * q * step, sign));   // k q step < N
     const int base = jd * Ns * P + k;
-    if (P == 2) {
-      yb[base] = cadd(v[0], v[1]);
-      yb[base + Ns] = csub(v[0], v[1]);
+    if (P == 16 || P == 8) {
+      if (P == 16) dft16(v, W, N, sign);
+      else dft8(v, W, N, sign);
+#pragma unroll
+      for (int u = 0; u < P; ++u) yb[fpad(base + u * Ns)] = v[u];
+    } else if (P == 2) {
+      yb[fpad(base)] = cadd(v[0], v[1]);
+      yb[fpad(base + Ns)] = csub(v[0], v[1]);
     } else if (P == 4) {
       const float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
       const float2 b0 = cadd(v[1], v[3]), b1 = csub(v[1], v[3]);
       // b1 times w_4: forward (-i) -> (b1.y, -b1.x); inverse (+i) -> (-b1.y, b1.x)
       const float2 b1w = sign < 0 ? make_float2(b1.y, -b1.x) : make_float2(-b1.y, b1.x);
-      yb[base] = cadd(a0, b0);
-      yb[base + Ns] = cadd(a1, b1w);
-      yb[base + 2 * Ns] = csub(a0, b0);
-      yb[base + 3 * Ns] = csub(a1, b1w);
+      yb[fpad(base)] = cadd(a0, b0);
+      yb[fpad(base + Ns)] = cadd(a1, b1w);
+      yb[fpad(base + 2 * Ns)] = csub(a0, b0);
+      yb[fpad(base + 3 * Ns)] = csub(a1, b1w);
     } else {
       // p-point DFT with the table: w_p^{qu} = W[((q u) mod p) N/p]
 #pragma unroll
@@ -158,14 +215,16 @@ __device__ __forceinline__ void fft_stage(const float2* x, float2* y, int N, int
         float2 acc = v[0];
 #pragma unroll
         for (int q = 1; q < P; ++q) cfma(acc, v[q], tw(W, ((q * u) % P) * Np, sign));
-        yb[base + u * Ns] = acc;
+        yb[fpad(base + u * Ns)] = acc;
       }
     }
   }
 }
 
-// Transforms `batch` sequences of length plan.n stored bstride apart in buf; tmp is the
-// ping-pong buffer of the same shape. Every thread of the block must call it.
+// Transforms `batch` sequences of length plan.n stored bstride apart in buf (element i of a
+// sequence at fpad(i); bstride >= fsz(n)); W is the padded twiddle table (element k at
+// fpad(k)); tmp is the ping-pong buffer of the same shape. Every thread of the block must
+// call it.
 __device__ inline float2* fft_smem(float2* buf, float2* tmp, const FftPlan& plan, int batch, int bstride,
                                    const float2* W, int sign, int tid, int nthreads) {
   const int N = plan.n;
@@ -174,7 +233,9 @@ __device__ inline float2* fft_smem(float2* buf, float2* tmp, const FftPlan& plan
   int Ns = 1;
   for (int st = 0; st < plan.nrad; ++st) {
     const int p = plan.rad[st];
-    if (p == 4) fft_stage<4>(x, y, N, Ns, batch, bstride, W, sign, tid, nthreads);
+    if (p == 16) fft_stage<16>(x, y, N, Ns, batch, bstride, W, sign, tid, nthreads);
+    else if (p == 8) fft_stage<8>(x, y, N, Ns, batch, bstride, W, sign, tid, nthreads);
+    else if (p == 4) fft_stage<4>(x, y, N, Ns, batch, bstride, W, sign, tid, nthreads);
     else if (p == 2) fft_stage<2>(x, y, N, Ns, batch, bstride, W, sign, tid, nthreads);
     else if (p == 3) fft_stage<3>(x, y, N, Ns, batch, bstride, W, sign, tid, nthreads);
     else fft_stage<5>(x, y, N, Ns, batch, bstride, W, sign, tid, nthreads);
@@ -244,7 +305,7 @@ __host__ __device__ inline FrameLayout frame_layout(int Nx, int Ny, int R, int r
   };
   const int f2 = 8;
   L.Wx = take(f2 * Nx);
-  L.Wy = take(f2 * Ny);
+  L.Wy = take(f2 * fsz(Ny));       // padded FFT twiddle table
   L.rows = take(4 * Nx);
   L.misc = take(4 * 8);
   L.red = take(4 * 2 * TTS_THREADS);
@@ -261,7 +322,7 @@ __host__ __device__ inline FrameLayout frame_layout(int Nx, int Ny, int R, int r
   L.yb = take(f2 * MC * rB);       // Yt block of this CTA's B rows, kept when |S| <= MC
   const int rmax = rA > rB ? rA : rB;
   int cf = MC * (rmax + rB + 3 * R);
-  if (cf < 2 * Ny) cf = 2 * Ny;     // at least one row transform (ping-pong)
+  if (cf < 2 * fsz(Ny)) cf = 2 * fsz(Ny);     // at least one row transform (ping-pong)
   L.chunk_f2 = cf;
   L.chunk = take(f2 * cf);
   L.bytes = off + 16;

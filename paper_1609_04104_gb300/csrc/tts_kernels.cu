@@ -1,5 +1,7 @@
 // Image formation, line sampler (S0 of Alg. 5), factor initialisation and the
 // batched unitary 2D DFT.
+#include <algorithm>
+
 #include "tts_internal.cuh"
 
 namespace {
@@ -88,8 +90,8 @@ __global__ void __launch_bounds__(SAMPLER_THREADS) sampler_kernel(
   int* cand = (int*)(nrm + 64);                                     // Nx
   uint8_t* mask = (uint8_t*)(cand + TTS_MAX_N);                     // Nx
   int* misc = (int*)(mask + TTS_MAX_N);                             // 8
-  float2* W = (float2*)(misc + 8);                                  // Nx
-  float2* buf = W + TTS_MAX_N;                                      // 2 x fft_cols x Nx
+  float2* W = (float2*)(misc + 8);                                  // fsz(Nx), padded
+  float2* buf = W + fsz(TTS_MAX_N);                                 // 2 x fft_cols x ld
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
 
   // (1) probabilities
@@ -97,12 +99,12 @@ __global__ void __launch_bounds__(SAMPLER_THREADS) sampler_kernel(
     for (int i = tid; i < Nx; i += blockDim.x) p[i] = p_in[i];
   } else if (policy == TTS_POLICY_INFORMATIVE) {
     for (int i = tid; i < Nx; i += blockDim.x) {
-      W[i] = Wx[i];
+      W[fpad(i)] = Wx[i];
       rowacc[i] = 0.f;
     }
     __syncthreads();
     const FftPlan plan = fft_plan(Nx);
-    const int ld = Nx + 1;   // padded column stride in shared memory
+    const int ld = fsz(Nx) | 1;   // padded column stride (odd) in shared memory
     for (int r0 = 0; r0 < R; r0 += fft_cols) {
       const int nc = min(fft_cols, R - r0);
       // coalesced along the rows of A, transposed into columns
@@ -121,7 +123,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS) sampler_kernel(
           const int e = base + u * blockDim.x;
           if (e < nc * Nx) {
             const int n = e / nc, c = e - n * nc;
-            buf[c * ld + n] = v[u];
+            buf[c * ld + fpad(n)] = v[u];
           }
         }
       }
@@ -129,14 +131,14 @@ __global__ void __launch_bounds__(SAMPLER_THREADS) sampler_kernel(
       float2* res = fft_smem(buf, buf + fft_cols * ld, plan, nc, ld, W, -1, tid, blockDim.x);
       for (int c = warp; c < nc; c += nwarp) {
         float acc = 0.f;
-        for (int n = lane; n < Nx; n += 32) acc += cabs2(res[c * ld + n]);
+        for (int n = lane; n < Nx; n += 32) acc += cabs2(res[c * ld + fpad(n)]);
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) nrm[c] = acc > 0.f ? 1.f / acc : 0.f;
       }
       __syncthreads();
       for (int i = tid; i < Nx; i += blockDim.x) {
         float acc = rowacc[i];
-        for (int c = 0; c < nc; ++c) acc += nrm[c] > 0.f ? cabs2(res[c * ld + i]) * nrm[c] : 1.f / (float)Nx;
+        for (int c = 0; c < nc; ++c) acc += nrm[c] > 0.f ? cabs2(res[c * ld + fpad(i)]) * nrm[c] : 1.f / (float)Nx;
         rowacc[i] = acc;
       }
       __syncthreads();
@@ -313,35 +315,46 @@ __global__ void __launch_bounds__(256) fft_rows_kernel(const float2* __restrict_
                                                        long nrows, int Ny, int rows_per_cta, int sign,
                                                        const float2* __restrict__ Wy, float scale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ld = fsz(Ny);   // padded row stride in shared memory
   float2* W = (float2*)smem_raw;
-  float2* buf = W + Ny;
-  float2* tmp = buf + rows_per_cta * Ny;
+  float2* buf = W + fsz(Ny);
+  float2* tmp = buf + rows_per_cta * ld;
   const int tid = threadIdx.x;
-  for (int e = tid; e < Ny; e += blockDim.x) W[e] = Wy[e];
+  for (int e = tid; e < Ny; e += blockDim.x) W[fpad(e)] = Wy[e];
   const long r0 = (long)blockIdx.x * rows_per_cta;
   const int nr = (int)min((long)rows_per_cta, nrows - r0);
   if (nr <= 0) return;
-  const float4* src = (const float4*)(in + r0 * Ny);
-  float4* b4 = (float4*)buf;
   const int n2 = nr * Ny;
   if ((Ny & 1) == 0) {
-    for (int e = tid; e < n2 / 2; e += blockDim.x) b4[e] = src[e];
+    // float4 global loads: two elements of one row (a pair never straddles a pad slot)
+    const float4* src = (const float4*)(in + r0 * Ny);
+    for (int e = tid; e < n2 / 2; e += blockDim.x) {
+      const float4 v = src[e];
+      const int i0 = 2 * e, r = i0 / Ny, c = i0 - r * Ny;
+      buf[r * ld + fpad(c)] = make_float2(v.x, v.y);
+      buf[r * ld + fpad(c + 1)] = make_float2(v.z, v.w);
+    }
   } else {
-    for (int e = tid; e < n2; e += blockDim.x) buf[e] = in[r0 * Ny + e];
+    for (int e = tid; e < n2; e += blockDim.x) {
+      const int r = e / Ny, c = e - r * Ny;
+      buf[r * ld + fpad(c)] = in[r0 * Ny + e];
+    }
   }
   __syncthreads();
   const FftPlan plan = fft_plan(Ny);
-  float2* res = fft_smem(buf, tmp, plan, nr, Ny, W, sign, tid, blockDim.x);
+  float2* res = fft_smem(buf, tmp, plan, nr, ld, W, sign, tid, blockDim.x);
   if ((Ny & 1) == 0) {
     float4* dst = (float4*)(out + r0 * Ny);
-    const float4* r4 = (const float4*)res;
     for (int e = tid; e < n2 / 2; e += blockDim.x) {
-      float4 v = r4[e];
-      v.x *= scale; v.y *= scale; v.z *= scale; v.w *= scale;
-      dst[e] = v;
+      const int i0 = 2 * e, r = i0 / Ny, c = i0 - r * Ny;
+      const float2 x0 = res[r * ld + fpad(c)], x1 = res[r * ld + fpad(c + 1)];
+      dst[e] = make_float4(x0.x * scale, x0.y * scale, x1.x * scale, x1.y * scale);
     }
   } else {
-    for (int e = tid; e < n2; e += blockDim.x) out[r0 * Ny + e] = cscale(res[e], scale);
+    for (int e = tid; e < n2; e += blockDim.x) {
+      const int r = e / Ny, c = e - r * Ny;
+      out[r0 * Ny + e] = cscale(res[r * ld + fpad(c)], scale);
+    }
   }
 }
 
@@ -349,27 +362,27 @@ __global__ void __launch_bounds__(256) fft_cols_kernel(float2* data, int Nx, int
                                                        const float2* __restrict__ Wx, float scale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* W = (float2*)smem_raw;
-  const int ld = Nx + 1;   // padded column stride in shared memory
-  float2* buf = W + Nx;
+  const int ld = fsz(Nx) | 1;   // padded column stride (odd) in shared memory
+  float2* buf = W + fsz(Nx);
   float2* tmp = buf + cols_per_cta * ld;
   const int tid = threadIdx.x;
-  for (int e = tid; e < Nx; e += blockDim.x) W[e] = Wx[e];
+  for (int e = tid; e < Nx; e += blockDim.x) W[fpad(e)] = Wx[e];
   const int nblk = (Ny + cols_per_cta - 1) / cols_per_cta;
   const long img = blockIdx.x / nblk;
   const int j0 = (blockIdx.x % nblk) * cols_per_cta;
   const int nc = min(cols_per_cta, Ny - j0);
   float2* base = data + img * (long)Nx * Ny;
-  // stage column block transposed: buf[c * Nx + i] = X[i][j0 + c]
+  // stage column block transposed: column c of the block at c * ld, element i at fpad(i)
   for (int e = tid; e < Nx * nc; e += blockDim.x) {
     const int i = e / nc, c = e - i * nc;
-    buf[c * ld + i] = base[(long)i * Ny + j0 + c];
+    buf[c * ld + fpad(i)] = base[(long)i * Ny + j0 + c];
   }
   __syncthreads();
   const FftPlan plan = fft_plan(Nx);
   float2* res = fft_smem(buf, tmp, plan, nc, ld, W, sign, tid, blockDim.x);
   for (int e = tid; e < Nx * nc; e += blockDim.x) {
     const int i = e / nc, c = e - i * nc;
-    base[(long)i * Ny + j0 + c] = cscale(res[c * ld + i], scale);
+    base[(long)i * Ny + j0 + c] = cscale(res[c * ld + fpad(i)], scale);
   }
 }
 
@@ -389,7 +402,8 @@ int launch_sampler(const float2* A, int Nx, int Ny, int R, const double* p_in, d
   const int fft_cols = max(1, min(min(R, 64), 8192 / max(Nx, 1)));
   const size_t smem = sizeof(double) * TTS_MAX_N + sizeof(unsigned long long) * TTS_MAX_N +
                       sizeof(float) * TTS_MAX_N + sizeof(float) * 64 + sizeof(int) * TTS_MAX_N + TTS_MAX_N +
-                      sizeof(int) * 8 + sizeof(float2) * TTS_MAX_N + sizeof(float2) * 2 * fft_cols * (Nx + 1) + 64;
+                      sizeof(int) * 8 + sizeof(float2) * fsz(TTS_MAX_N) +
+                      sizeof(float2) * 2 * fft_cols * (fsz(Nx) | 1) + 64;
   cudaError_t e = cudaFuncSetAttribute(sampler_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return TTS_ECUDA;
   sampler_kernel<<<1, SAMPLER_THREADS, smem, st>>>(A, Nx, Ny, R, p_in, p_out, policy, vd_alpha, k_lines, central,
@@ -408,20 +422,30 @@ int launch_fft2d(const float2* in, float2* out, int batch, int Nx, int Ny, int i
                  const float2* Wy, float2* scratch, cudaStream_t st) {
   (void)scratch;
   const int sign = inverse ? +1 : -1;
-  const long nrows = (long)batch * Nx;
   const int rows_per_cta = max(1, 4096 / Ny);
-  const size_t smem_r = sizeof(float2) * (Ny + 2 * (size_t)rows_per_cta * Ny);
+  const size_t smem_r = sizeof(float2) * (fsz(Ny) + 2 * (size_t)rows_per_cta * fsz(Ny));
   cudaError_t e = cudaFuncSetAttribute(fft_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
   if (e != cudaSuccess) return TTS_ECUDA;
-  const long grid_r = (nrows + rows_per_cta - 1) / rows_per_cta;
-  fft_rows_kernel<<<(unsigned)grid_r, 256, smem_r, st>>>(in, out, nrows, Ny, rows_per_cta, sign, Wy,
-                                                          1.0f / sqrtf((float)Ny));
-  if (cudaGetLastError() != cudaSuccess) return TTS_ECUDA;
   const int cols_per_cta = max(1, min(Ny, 4096 / Nx));
-  const size_t smem_c = sizeof(float2) * (Nx + 2 * (size_t)cols_per_cta * (Nx + 1));
+  const size_t smem_c = sizeof(float2) * (fsz(Nx) + 2 * (size_t)cols_per_cta * (fsz(Nx) | 1));
   e = cudaFuncSetAttribute(fft_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c);
   if (e != cudaSuccess) return TTS_ECUDA;
-  const long grid_c = (long)batch * ((Ny + cols_per_cta - 1) / cols_per_cta);
-  fft_cols_kernel<<<(unsigned)grid_c, 256, smem_c, st>>>(out, Nx, Ny, cols_per_cta, sign, Wx, 1.0f / sqrtf((float)Nx));
-  return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
+  // Images go in groups whose row-pass result (written to out) stays in L2 until the
+  // column pass reads it back: DRAM then sees about one read of in and one write of out.
+  const size_t img = (size_t)Nx * Ny * sizeof(float2);
+  const size_t l2_budget = 32u << 20;
+  const int group = (int)std::max<size_t>(1, std::min<size_t>((size_t)batch, l2_budget / img));
+  for (int g0 = 0; g0 < batch; g0 += group) {
+    const int gb = std::min(group, batch - g0);
+    const long nrows = (long)gb * Nx;
+    const long grid_r = (nrows + rows_per_cta - 1) / rows_per_cta;
+    fft_rows_kernel<<<(unsigned)grid_r, 256, smem_r, st>>>(in + (size_t)g0 * Nx * Ny, out + (size_t)g0 * Nx * Ny, nrows,
+                                                            Ny, rows_per_cta, sign, Wy, 1.0f / sqrtf((float)Ny));
+    if (cudaGetLastError() != cudaSuccess) return TTS_ECUDA;
+    const long grid_c = (long)gb * ((Ny + cols_per_cta - 1) / cols_per_cta);
+    fft_cols_kernel<<<(unsigned)grid_c, 256, smem_c, st>>>(out + (size_t)g0 * Nx * Ny, Nx, Ny, cols_per_cta, sign, Wx,
+                                                            1.0f / sqrtf((float)Nx));
+    if (cudaGetLastError() != cudaSuccess) return TTS_ECUDA;
+  }
+  return TTS_OK;
 }
