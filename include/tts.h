@@ -53,7 +53,8 @@ enum {
   TTS_ERANGE = -4,      /* frame index that is not the most recent frame */
   TTS_ENONFINITE = -5,  /* NaN/Inf in an input frame; the frame was not applied */
   TTS_ETIMEOUT = -6,    /* a bounded device wait ran out */
-  TTS_ESTATE = -7       /* call out of order (e.g. NULL mask before any tts_next_mask) */
+  TTS_ESTATE = -7,      /* call out of order (e.g. NULL mask before any tts_next_mask) */
+  TTS_EBUSY = -8        /* engine admission refused: no free slot or no arena room */
 };
 
 #define TTS_DEVICE_PTRS 1
@@ -184,9 +185,10 @@ int tts_synchronize(tts_handle* h);
 /* Kernel launches one tts_push_frame enqueues with the handle's settings. */
 int tts_launches_per_frame(tts_handle* h);
 
-/* The ridge step of (S1) on a given system: solves G gamma = h in FP64 by the LDL^H
- * factorisation the frame kernel uses (§III-A: gamma = (Phi^H Phi + mu I)^{-1} Phi^H y,
- * here with G = Phi^H Phi + mu I supplied). G is R x R complex128 (interleaved re, im),
+/* The ridge step of (S1) on a given system: solves G gamma = h to FP64 accuracy with the
+ * solver the frame kernel uses (§III-A: gamma = (Phi^H Phi + mu I)^{-1} Phi^H y, here
+ * with G = Phi^H Phi + mu I supplied): an FP32 Gauss-Jordan inverse followed by
+ * iterative refinement whose residuals are formed in float-float arithmetic. G is R x R complex128 (interleaved re, im),
  * row-major, Hermitian positive definite; only its lower triangle is read. h and gamma
  * hold R complex128 values. Host pointers; runs on the current device, synchronously. */
 int tts_ridge_solve(const double* G, const double* h, int R, double* gamma);
@@ -238,6 +240,87 @@ typedef struct {
 } tts_frame_args;
 
 int tts_push_frame_noalloc(const tts_frame_args* args, void* cuda_stream);
+
+/* ---- Many streams on one GPU: the batching and serving engine ------------------------
+ * The paper tracks one cine stream at a time (Alg. 3, Alg. 5); it has no counterpart of
+ * this part. An engine keeps many independent trackers (streams of any Nx, Ny, R, K,
+ * lambda_forget, mu, policy and rate) resident on one GPU and advances any subset of
+ * them by one frame per call, with all their work in three kernel launches (see
+ * tts_engine_step). Each stream's results equal those of a handle with the same
+ * tts_config and cluster_ctas run alone: the batch changes where a frame runs, not what
+ * it computes.
+ *
+ * Memory: tts_engine_create reserves one device arena of arena_bytes; each admitted
+ * stream takes tts_stream_footprint bytes of it until released. The engine owns the
+ * arena, the slots' handles, a device parameter block and two pinned host copies of it.
+ * All engine work is ordered on the engine's stream; calls returning host data wait
+ * for it. An engine is not thread-safe: serialise calls on one engine. */
+#define TTS_ENGINE_GRAPH 1          /* tts_engine_create: replay each step as a CUDA graph */
+#define TTS_ENGINE_MAX_SLOTS 4096
+
+typedef struct tts_engine tts_engine;
+
+typedef struct {
+  size_t arena_bytes;         /* size of the device arena */
+  size_t arena_used;          /* bytes held by admitted streams */
+  size_t arena_largest_free;  /* largest stream footprint that admission can place now */
+  int active;                 /* admitted streams */
+  int max_slots;
+  int cluster_ctas;           /* CTAs per frame (one cluster) */
+  int resident_clusters;      /* clusters the persistent frame launch keeps on the GPU */
+  int owned_outputs;          /* per-thread outputs of the persistent frame kernel */
+  int64_t steps;              /* tts_engine_step calls that launched work */
+} tts_engine_stats;
+
+/* Device bytes a stream with this configuration holds in an engine arena (the same
+ * workspace a handle allocates); cfg->cluster_ctas 0 means 8, the engine default. */
+int tts_stream_footprint(const tts_config* cfg, size_t* bytes);
+
+/* Create an engine on the current device. arena_bytes >= 4096; max_slots in
+ * 1..TTS_ENGINE_MAX_SLOTS (at most that many streams at once); cluster_ctas in
+ * {0 (= 8), 1, 2, 4, 8, 16}: CTAs of the cluster that runs one frame, the same for every
+ * stream; flags 0 or TTS_ENGINE_GRAPH; cuda_stream NULL = a stream the engine creates.
+ * TTS_ENOMEM if the arena or the parameter block cannot be allocated. */
+int tts_engine_create(size_t arena_bytes, int max_slots, int cluster_ctas, int flags, void* cuda_stream,
+                      tts_engine** out);
+/* Waits for the engine's work, then frees everything it owns, admitted streams included. */
+void tts_engine_destroy(tts_engine* e);
+
+/* Admission: create a tracker for cfg in a free slot whose footprint fits in the arena
+ * (first fit). cfg->cluster_ctas, cfg->launch and cfg->cuda_stream are replaced by the
+ * engine's. On success *slot is the stream's slot (0..max_slots-1). TTS_EBUSY when every
+ * slot is taken or no free arena block is large enough; TTS_EINVAL for a bad cfg. Does
+ * not wait for steps in flight. */
+int tts_engine_admit(tts_engine* e, const tts_config* cfg, int* slot);
+/* Waits for the engine's work, then frees the slot and returns its arena block. */
+int tts_engine_release(tts_engine* e, int slot);
+/* The tracker of a slot (owned by the engine, valid until release): tts_get_factors,
+ * tts_get_stats, tts_set_factors, tts_save, tts_load ... apply to it on the engine's stream. */
+int tts_engine_handle(tts_engine* e, int slot, tts_handle** h);
+
+/* One frame for each of n distinct slots (0 <= n <= max_slots), then the image and the
+ * next frame's lines of each:
+ *   y_rows[k]     frame of slots[k], as for tts_push_frame (|S| x Ny acquired rows, or
+ *                 Nx x Ny with TTS_FULL_FRAME), host or device per TTS_DEVICE_PTRS;
+ *   line_masks    NULL, or n masks (each NULL = the mask the engine drew for the slot);
+ *   rates[k]      rate in (0, 1] of the draw for the slot's next frame;
+ *   seeds[k]      key of that draw.
+ * For every listed slot this equals tts_push_frame, tts_image (into the engine's image
+ * buffer of the slot) and tts_next_mask(rate, seed) on the slot's handle. Host frames
+ * are checked and copied as tts_push_frame does, except a full host frame with a NULL
+ * mask, which is copied whole and checked on the device. If any frame is refused
+ * (TTS_EINVAL, TTS_ESTATE, TTS_ENONFINITE) no slot is advanced. Asynchronous; it waits
+ * only for the step before last, whose host parameter copy it reuses. */
+int tts_engine_step(tts_engine* e, int n, const int* slots, const tts_c64* const* y_rows,
+                    const uint8_t* const* line_masks, const double* rates, const uint64_t* seeds, int flags);
+/* The image (Nx x Ny) the last step computed for the slot; TTS_ERANGE before its first
+ * frame. Host out waits for the engine's stream; device out is an async copy. */
+int tts_engine_image(tts_engine* e, int slot, tts_c64* out, int flags);
+/* The mask (Nx bytes) the last step drew for the slot's next frame; TTS_ESTATE if none. */
+int tts_engine_mask(tts_engine* e, int slot, uint8_t* out, int flags);
+/* Waits for the engine's stream; TTS_ENONFINITE (once) if any slot skipped a frame. */
+int tts_engine_synchronize(tts_engine* e);
+int tts_engine_info(tts_engine* e, tts_engine_stats* stats);
 
 const char* tts_last_error(void);
 

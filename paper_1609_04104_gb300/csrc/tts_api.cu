@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "tts_internal.cuh"
+#include "tts_handle.cuh"
 
 namespace {
 
@@ -52,55 +52,40 @@ std::vector<float2> twiddles(int N) {
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
+struct Piece {
+  void** ptr;
+  size_t bytes;
+};
+
+// The device workspace of a tracker, in allocation order.
+std::vector<Piece> handle_pieces(tts_handle* h, int Nx, int Ny, int R, int C) {
+  FrameParams& p = h->fp;
+  return {
+      {(void**)&p.A, sizeof(float2) * Nx * R},          {(void**)&p.B, sizeof(float2) * Ny * R},
+      {(void**)&p.A0, sizeof(float2) * Nx * R},         {(void**)&p.B0, sizeof(float2) * Ny * R},
+      {(void**)&h->ystage, sizeof(float2) * Nx * Ny},   {(void**)&p.Yt, sizeof(float2) * Nx * Ny},
+      {(void**)&p.rows, sizeof(int) * Nx},              {(void**)&p.nrows, sizeof(int) * 4},
+      {(void**)&p.AhS[0], sizeof(float2) * Nx * R},     {(void**)&p.AhS[1], sizeof(float2) * Nx * R},
+      {(void**)&p.nA[0], sizeof(float) * R},            {(void**)&p.nA[1], sizeof(float) * R},
+      {(void**)&p.MB, sizeof(float2) * R * R},          {(void**)&p.P, sizeof(float2) * Nx * R},
+      {(void**)&p.partA, sizeof(float2) * C * Nx * R},  {(void**)&p.partNA, sizeof(float) * C * R},
+      {(void**)&p.partMB, sizeof(float2) * C * R * R},  {(void**)&p.partP, sizeof(float2) * C * Nx * R},
+      {(void**)&p.sc, sizeof(double) * SC_COUNT},
+      {(void**)&p.sf, sizeof(double) * SF_COUNT},       {(void**)&p.gamma, sizeof(float2) * R},
+      {(void**)&p.gamma_d, sizeof(double2) * R},        {(void**)&p.status, sizeof(int) * (1 + TTS_MAX_CLUSTER)},
+      {(void**)&p.Wx, sizeof(float2) * Nx},             {(void**)&p.Wy, sizeof(float2) * Ny},
+      {(void**)&h->X, sizeof(float2) * Nx * Ny},        {(void**)&h->dmask_push, (size_t)Nx},
+      {(void**)&h->dmask_next, (size_t)Nx},             {(void**)&h->dp, sizeof(double) * Nx},
+  };
+}
+
 }  // namespace
 
 void tts_internal_set_error(const char* msg) { g_err = msg ? msg : ""; }
+int tts_fail(int code, const char* fmt, const char* detail) { return fail(code, fmt, detail); }
+int tts_cuda_fail(cudaError_t e, const char* where) { return cuda_fail(e, where); }
 
-struct tts_handle {
-  tts_config cfg;
-  int dev = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  void* dmem = nullptr;
-  size_t dbytes = 0;
-  FrameParams fp;
-  float2* X = nullptr;          // image
-  float2* ystage = nullptr;     // acquired rows from host pushes
-  uint8_t* dmask_push = nullptr;
-  uint8_t* dmask_next = nullptr;
-  double* dp = nullptr;
-  int64_t t = 0;                // frames processed
-  bool have_next = false;
-  bool next_on_host = false;
-  std::vector<uint8_t> next_host;
-};
-
-extern "C" {
-
-const char* tts_last_error(void) { return g_err.c_str(); }
-
-void tts_config_init(tts_config* c, int Nx, int Ny, int R, double lambda_forget, double mu) {
-  if (!c) return;
-  memset(c, 0, sizeof(*c));
-  c->Nx = Nx;
-  c->Ny = Ny;
-  c->R = R;
-  c->lambda_forget = lambda_forget;
-  c->mu = mu;
-  c->mm_iters = 1;
-  c->central_lines = 8;
-  c->policy = TTS_POLICY_INFORMATIVE;
-  c->vd_alpha = -1.0;
-  c->with_replacement = 0;
-  c->update = TTS_UPDATE_GAUSS_SEIDEL;
-  c->launch = TTS_LAUNCH_FUSED;
-  c->cluster_ctas = 0;
-  c->init_seed = 0;
-  c->stream_id = 0;
-  c->cuda_stream = nullptr;
-}
-
-static int check_config(const tts_config* c) {
+int handle_check_config(const tts_config* c) {
   if (!c) return fail(TTS_EINVAL, "config is NULL%s");
   if (c->Nx < 1 || c->Nx > TTS_MAX_N || !smooth235(c->Nx)) return fail(TTS_EINVAL, "Nx must be 1..512 with prime factors in {2,3,5}%s");
   if (c->Ny < 1 || c->Ny > TTS_MAX_N || !smooth235(c->Ny)) return fail(TTS_EINVAL, "Ny must be 1..512 with prime factors in {2,3,5}%s");
@@ -117,16 +102,22 @@ static int check_config(const tts_config* c) {
   return TTS_OK;
 }
 
-int tts_create(int Nx, int Ny, int R, double lambda_forget, double mu, tts_handle** out) {
-  tts_config c;
-  tts_config_init(&c, Nx, Ny, R, lambda_forget, mu);
-  return tts_create_ex(&c, out);
+size_t handle_footprint(const tts_config& cfg) {
+  tts_handle tmp;
+  memset(&tmp.fp, 0, sizeof(tmp.fp));
+  tmp.fp.Nx = cfg.Nx;
+  tmp.fp.Ny = cfg.Ny;
+  tmp.fp.R = cfg.R;
+  if (frame_configure(tmp.fp, cfg.cluster_ctas) != TTS_OK) return 0;
+  size_t total = 0;
+  for (auto& pc : handle_pieces(&tmp, cfg.Nx, cfg.Ny, cfg.R, tmp.fp.C)) total += align_up(pc.bytes);
+  return total;
 }
 
-int tts_create_ex(const tts_config* cfg, tts_handle** out) {
+int handle_create(const tts_config* cfg, void* mem, tts_handle** out) {
   if (!out) return fail(TTS_EINVAL, "out is NULL%s");
   *out = nullptr;
-  int rc = check_config(cfg);
+  int rc = handle_check_config(cfg);
   if (rc) return rc;
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -156,35 +147,19 @@ int tts_create_ex(const tts_config* cfg, tts_handle** out) {
     }
     h->own_stream = true;
   }
-  // device workspace layout
-  struct Piece {
-    void** ptr;
-    size_t bytes;
-  };
-  std::vector<Piece> pieces = {
-      {(void**)&p.A, sizeof(float2) * Nx * R},          {(void**)&p.B, sizeof(float2) * Ny * R},
-      {(void**)&p.A0, sizeof(float2) * Nx * R},         {(void**)&p.B0, sizeof(float2) * Ny * R},
-      {(void**)&h->ystage, sizeof(float2) * Nx * Ny},   {(void**)&p.Yt, sizeof(float2) * Nx * Ny},
-      {(void**)&p.rows, sizeof(int) * Nx},              {(void**)&p.nrows, sizeof(int) * 4},
-      {(void**)&p.AhS[0], sizeof(float2) * Nx * R},     {(void**)&p.AhS[1], sizeof(float2) * Nx * R},
-      {(void**)&p.nA[0], sizeof(float) * R},            {(void**)&p.nA[1], sizeof(float) * R},
-      {(void**)&p.MB, sizeof(float2) * R * R},          {(void**)&p.P, sizeof(float2) * Nx * R},
-      {(void**)&p.partA, sizeof(float2) * C * Nx * R},  {(void**)&p.partNA, sizeof(float) * C * R},
-      {(void**)&p.partMB, sizeof(float2) * C * R * R},  {(void**)&p.partP, sizeof(float2) * C * Nx * R},
-      {(void**)&p.sc, sizeof(double) * SC_COUNT},
-      {(void**)&p.sf, sizeof(double) * SF_COUNT},       {(void**)&p.gamma, sizeof(float2) * R},
-      {(void**)&p.gamma_d, sizeof(double2) * R},        {(void**)&p.status, sizeof(int) * (1 + TTS_MAX_CLUSTER)},
-      {(void**)&p.Wx, sizeof(float2) * Nx},             {(void**)&p.Wy, sizeof(float2) * Ny},
-      {(void**)&h->X, sizeof(float2) * Nx * Ny},        {(void**)&h->dmask_push, (size_t)Nx},
-      {(void**)&h->dmask_next, (size_t)Nx},             {(void**)&h->dp, sizeof(double) * Nx},
-  };
+  std::vector<Piece> pieces = handle_pieces(h, Nx, Ny, R, C);
   size_t total = 0;
   for (auto& pc : pieces) total += align_up(pc.bytes);
-  e = cudaMalloc(&h->dmem, total);
-  if (e != cudaSuccess) {
-    if (h->own_stream) cudaStreamDestroy(h->stream);
-    delete h;
-    return fail(TTS_ENOMEM, "device allocation of the tracker workspace failed%s");
+  if (mem) {
+    h->dmem = mem;
+    h->own_mem = false;
+  } else {
+    e = cudaMalloc(&h->dmem, total);
+    if (e != cudaSuccess) {
+      if (h->own_stream) cudaStreamDestroy(h->stream);
+      delete h;
+      return fail(TTS_ENOMEM, "device allocation of the tracker workspace failed%s");
+    }
   }
   h->dbytes = total;
   size_t off = 0;
@@ -213,7 +188,7 @@ int tts_create_ex(const tts_config* cfg, tts_handle** out) {
   if (rc == TTS_OK) ck(cudaStreamSynchronize(h->stream), "create");
   if (rc != TTS_OK) {
     if (g_err.empty()) g_err = "kernel launch failed during create";
-    cudaFree(h->dmem);
+    if (h->own_mem) cudaFree(h->dmem);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
     return rc;
@@ -223,10 +198,90 @@ int tts_create_ex(const tts_config* cfg, tts_handle** out) {
   return TTS_OK;
 }
 
+int handle_stage_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line_mask, int flags, FrameParams* pout) {
+  const int Nx = h->cfg.Nx, Ny = h->cfg.Ny;
+  FrameParams p = h->fp;
+  p.full_frame = (flags & TTS_FULL_FRAME) ? 1 : 0;
+  if (flags & TTS_DEVICE_PTRS) {
+    if (!line_mask && !h->have_next) return fail(TTS_ESTATE, "no mask given and none drawn yet%s");
+    p.mask = line_mask ? line_mask : h->dmask_next;
+    p.yrows = (const float2*)y_rows;
+  } else {
+    const uint8_t* m = line_mask;
+    if (!m) {
+      if (!h->have_next) return fail(TTS_ESTATE, "no mask given and none drawn yet%s");
+      if (!h->next_on_host) {
+        CK(cudaMemcpyAsync(h->next_host.data(), h->dmask_next, Nx, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        h->next_on_host = true;
+      }
+      m = h->next_host.data();
+    }
+    int s = 0;
+    for (int i = 0; i < Nx; ++i) s += m[i] != 0;
+    if (s == 0) return fail(TTS_EINVAL, "the line mask selects no line%s");
+    const size_t nrows_in = (flags & TTS_FULL_FRAME) ? (size_t)Nx : (size_t)s;
+    const float* f = (const float*)y_rows;
+    for (int i = 0, m_ = 0; i < Nx; ++i) {
+      if (!m[i]) continue;
+      const float* row = f + 2 * (size_t)Ny * ((flags & TTS_FULL_FRAME) ? (size_t)i : (size_t)m_++);
+      for (int e = 0; e < 2 * Ny; ++e)
+        if (!isfinite(row[e])) return fail(TTS_ENONFINITE, "frame holds NaN or Inf; not applied%s");
+    }
+    CK(cudaMemcpyAsync(h->dmask_push, m, Nx, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->ystage, y_rows, sizeof(float2) * nrows_in * Ny, cudaMemcpyHostToDevice, h->stream));
+    p.mask = h->dmask_push;
+    p.yrows = h->ystage;
+  }
+  *pout = p;
+  return TTS_OK;
+}
+
+uint64_t handle_draw_counter(const tts_handle* h) {
+  return ((uint64_t)(h->cfg.stream_id & 0xFFFFFFu) << 40) | ((uint64_t)h->t & ((1ull << 40) - 1));
+}
+
+int handle_k_lines(const tts_handle* h, double rate) {
+  return std::max(h->cfg.central_lines, (int)floor(rate * h->cfg.Nx + 0.5));
+}
+
+extern "C" {
+
+const char* tts_last_error(void) { return g_err.c_str(); }
+
+void tts_config_init(tts_config* c, int Nx, int Ny, int R, double lambda_forget, double mu) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->Nx = Nx;
+  c->Ny = Ny;
+  c->R = R;
+  c->lambda_forget = lambda_forget;
+  c->mu = mu;
+  c->mm_iters = 1;
+  c->central_lines = 8;
+  c->policy = TTS_POLICY_INFORMATIVE;
+  c->vd_alpha = -1.0;
+  c->with_replacement = 0;
+  c->update = TTS_UPDATE_GAUSS_SEIDEL;
+  c->launch = TTS_LAUNCH_FUSED;
+  c->cluster_ctas = 0;
+  c->init_seed = 0;
+  c->stream_id = 0;
+  c->cuda_stream = nullptr;
+}
+
+int tts_create(int Nx, int Ny, int R, double lambda_forget, double mu, tts_handle** out) {
+  tts_config c;
+  tts_config_init(&c, Nx, Ny, R, lambda_forget, mu);
+  return tts_create_ex(&c, out);
+}
+
+int tts_create_ex(const tts_config* cfg, tts_handle** out) { return handle_create(cfg, nullptr, out); }
+
 void tts_destroy(tts_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
-  cudaFree(h->dmem);
+  if (h->own_mem) cudaFree(h->dmem);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -284,40 +339,9 @@ int tts_get_gamma(tts_handle* h, tts_c64* gamma) {
 
 int tts_push_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line_mask, int flags) {
   if (!h || !y_rows) return fail(TTS_EINVAL, "NULL argument%s");
-  const int Nx = h->cfg.Nx, Ny = h->cfg.Ny;
-  FrameParams p = h->fp;
-  p.full_frame = (flags & TTS_FULL_FRAME) ? 1 : 0;
-  if (flags & TTS_DEVICE_PTRS) {
-    if (!line_mask && !h->have_next) return fail(TTS_ESTATE, "no mask given and none drawn yet%s");
-    p.mask = line_mask ? line_mask : h->dmask_next;
-    p.yrows = (const float2*)y_rows;
-  } else {
-    const uint8_t* m = line_mask;
-    if (!m) {
-      if (!h->have_next) return fail(TTS_ESTATE, "no mask given and none drawn yet%s");
-      if (!h->next_on_host) {
-        CK(cudaMemcpyAsync(h->next_host.data(), h->dmask_next, Nx, cudaMemcpyDeviceToHost, h->stream));
-        CK(cudaStreamSynchronize(h->stream));
-        h->next_on_host = true;
-      }
-      m = h->next_host.data();
-    }
-    int s = 0;
-    for (int i = 0; i < Nx; ++i) s += m[i] != 0;
-    if (s == 0) return fail(TTS_EINVAL, "the line mask selects no line%s");
-    const size_t nrows_in = (flags & TTS_FULL_FRAME) ? (size_t)Nx : (size_t)s;
-    const float* f = (const float*)y_rows;
-    for (int i = 0, m_ = 0; i < Nx; ++i) {
-      if (!m[i]) continue;
-      const float* row = f + 2 * (size_t)Ny * ((flags & TTS_FULL_FRAME) ? (size_t)i : (size_t)m_++);
-      for (int e = 0; e < 2 * Ny; ++e)
-        if (!isfinite(row[e])) return fail(TTS_ENONFINITE, "frame holds NaN or Inf; not applied%s");
-    }
-    CK(cudaMemcpyAsync(h->dmask_push, m, Nx, cudaMemcpyHostToDevice, h->stream));
-    CK(cudaMemcpyAsync(h->ystage, y_rows, sizeof(float2) * nrows_in * Ny, cudaMemcpyHostToDevice, h->stream));
-    p.mask = h->dmask_push;
-    p.yrows = h->ystage;
-  }
+  FrameParams p;
+  const int rs = handle_stage_frame(h, y_rows, line_mask, flags, &p);
+  if (rs != TTS_OK) return rs;
   const int rc = launch_frame(p, h->cfg.launch, h->stream);
   if (rc != TTS_OK) return fail(rc, "frame kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
   h->t += 1;
@@ -338,18 +362,14 @@ int tts_image(tts_handle* h, int64_t t, tts_c64* out, int flags) {
   return TTS_OK;
 }
 
-static uint64_t draw_counter(const tts_handle* h) {
-  return ((uint64_t)(h->cfg.stream_id & 0xFFFFFFu) << 40) | ((uint64_t)h->t & ((1ull << 40) - 1));
-}
-
 int tts_next_mask(tts_handle* h, double rate, uint64_t seed, uint8_t* line_mask_out, int flags) {
   if (!h || !line_mask_out) return fail(TTS_EINVAL, "NULL argument%s");
   if (!(rate > 0.0 && rate <= 1.0)) return fail(TTS_EINVAL, "rate must lie in (0, 1]%s");
   const int Nx = h->cfg.Nx;
-  const int k_lines = std::max(h->cfg.central_lines, (int)floor(rate * Nx + 0.5));
+  const int k_lines = handle_k_lines(h, rate);
   uint8_t* out2 = (flags & TTS_DEVICE_PTRS) ? line_mask_out : nullptr;
   int rc = launch_sampler(h->fp.A, Nx, h->cfg.Ny, h->cfg.R, nullptr, h->dp, h->cfg.policy, h->cfg.vd_alpha, k_lines,
-                          h->cfg.central_lines, seed, draw_counter(h), h->cfg.with_replacement, h->fp.Wx,
+                          h->cfg.central_lines, seed, handle_draw_counter(h), h->cfg.with_replacement, h->fp.Wx,
                           h->dmask_next, out2, h->stream);
   if (rc != TTS_OK) return fail(rc, "sampler kernel launch failed%s");
   h->have_next = true;

@@ -149,7 +149,7 @@ __device__ __forceinline__ void warp_inverse16(const float2* M, int ld, int kb, 
       cq[e].x = __shfl_sync(FULL, m[e].x, q + 16 * h);
       cq[e].y = __shfl_sync(FULL, m[e].y, q + 16 * h);
     }
-    const float inv = __frcp_rn(d.x * d.x + d.y * d.y);
+    const float inv = __frcp_rn(cabs2(d));
     const float2 piv = make_float2(d.x * inv, -d.y * inv);
     const float2 rqp = cmul(rq, piv);
     // branch-free update (the row and column of the pivot are lane dependent)
@@ -157,7 +157,8 @@ __device__ __forceinline__ void warp_inverse16(const float2* M, int ld, int kb, 
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const bool rowq = (h == qh) && (e == qe);
-      const float2 gen = csub(m[e], cmul(cq[e], rqp));
+      float2 gen = m[e];
+      cfms(gen, cq[e], rqp);
       const float2 t = cmul(cq[e], piv);
       const float2 colv = make_float2(-t.x, -t.y);
       const float2 rv = colq ? piv : rqp;
@@ -280,12 +281,9 @@ __device__ void ridge_solve(SM& sm, int R, const float2* Glo, const float2* hlo,
         ff_add_ff(ih, il, pp, e);
         two_prod(g.y, x.x, pp, e);
         ff_add_ff(ih, il, pp, e);
-        float cr = g.x * xl.x - g.y * xl.y, ci = g.x * xl.y + g.y * xl.x;
-        if (Glo) {
-          const float2 gl = Glo[i * R + j];
-          cr += gl.x * x.x - gl.y * x.y;
-          ci += gl.x * x.y + gl.y * x.x;
-        }
+        float2 cc = cmul(g, xl);
+        if (Glo) cfma(cc, Glo[i * R + j], x);
+        const float cr = cc.x, ci = cc.y;
         ff_add_f(rh, rl, cr);
         ff_add_f(ih, il, ci);
       }
@@ -370,7 +368,10 @@ __device__ void partials_A(const FrameParams& p, SM& sm, int cta, float2* TW, bo
   }
   for (int r = tid; r < R; r += nth) {
     float acc = 0.f;
-    for (int nl = 0; nl < na; ++nl) acc += cabs2(sm.A[nl * R + r]);
+    for (int nl = 0; nl < na; ++nl) {
+      const float2 v = sm.A[nl * R + r];
+      acc = fmaf(v.x, v.x, fmaf(v.y, v.y, acc));
+    }
     p.partNA[cta * R + r] = acc;
   }
 }
@@ -526,7 +527,7 @@ __device__ __forceinline__ void step_coefficients(const FrameParams& p, SM& sm, 
   const int tid = threadIdx.x;
   if (tid < 32) {
     float acc = 0.f;
-    for (int r = tid; r < p.R; r += 32) acc += cabs2(sm.gam[r]) * wr[r * wstride];
+    for (int r = tid; r < p.R; r += 32) acc = fmaf(cabs2(sm.gam[r]), wr[r * wstride], acc);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (tid == 0) {
       const double alpha = rho + (double)acc;
@@ -656,10 +657,10 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
       float2 a0 = PC[e], a1 = make_float2(0.f, 0.f);
       int q = 0;
       for (; q + 1 < R; q += 2) {
-        a0 = csub(a0, cmul(AH[mm * R + q], gM[q * R + r]));
-        a1 = csub(a1, cmul(AH[mm * R + q + 1], gM[(q + 1) * R + r]));
+        cfms(a0, AH[mm * R + q], gM[q * R + r]);
+        cfms(a1, AH[mm * R + q + 1], gM[(q + 1) * R + r]);
       }
-      if (q < R) a0 = csub(a0, cmul(AH[mm * R + q], gM[q * R + r]));
+      if (q < R) cfms(a0, AH[mm * R + q], gM[q * R + r]);
       QC[e] = cadd(a0, a1);
     }
     __syncthreads();
@@ -694,8 +695,8 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
       const float2 tt = cscale(cadd(t0[o], t1[o]), p.isx);
       const float2 grad = csub(cscale(a, frho), cmul(tt, cconj(sm.gam[ocol[o]])));
       float2 an;
-      an.x = c0 * a0.x + c1 * a.x - c2 * grad.x;
-      an.y = c0 * a0.y + c1 * a.y - c2 * grad.y;
+      an.x = fmaf(-c2, grad.x, fmaf(c1, a.x, c0 * a0.x));
+      an.y = fmaf(-c2, grad.y, fmaf(c1, a.y, c0 * a0.y));
       sm.A[e] = an;
       p.A[as.lo * R + e] = an;
     }
@@ -820,15 +821,15 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) 
       float2 tb0 = u[o], tb1 = make_float2(0.f, 0.f);
       int q = 0;
       for (; q + 1 < R; q += 2) {
-        tb0 = csub(tb0, cmul(sm.B[jl * R + q], gMA[q * R + r]));
-        tb1 = csub(tb1, cmul(sm.B[jl * R + q + 1], gMA[(q + 1) * R + r]));
+        cfms(tb0, sm.B[jl * R + q], gMA[q * R + r]);
+        cfms(tb1, sm.B[jl * R + q + 1], gMA[(q + 1) * R + r]);
       }
-      if (q < R) tb0 = csub(tb0, cmul(sm.B[jl * R + q], gMA[q * R + r]));
+      if (q < R) cfms(tb0, sm.B[jl * R + q], gMA[q * R + r]);
       const float2 tb = cadd(tb0, tb1);
       const float2 b = sm.B[e], b0 = sm.B0[e];
       const float2 grad = csub(cscale(b, frho), cmul(tb, cconj(sm.gam[r])));
-      nbv[o].x = c0 * b0.x + c1 * b.x - c2 * grad.x;
-      nbv[o].y = c0 * b0.y + c1 * b.y - c2 * grad.y;
+      nbv[o].x = fmaf(-c2, grad.x, fmaf(c1, b.x, c0 * b0.x));
+      nbv[o].y = fmaf(-c2, grad.y, fmaf(c1, b.y, c0 * b0.y));
     }
   }
   __syncthreads();
@@ -893,13 +894,12 @@ __device__ void step_reduce_B(const FrameParams& p, SM& sm, int cta) {
   }
 }
 
+// Steps [step_begin, step_end) of one frame, run by CTA `cta` of the cluster that owns it.
 template <int OWN>
-__global__ void __launch_bounds__(TTS_THREADS, 1) frame_kernel(FrameParams p, int step_begin, int step_end,
-                                                               int fused) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void frame_run(const FrameParams& p, unsigned char* smem_raw, int cta, int step_begin,
+                                          int step_end, int fused) {
   SM sm = carve(p, smem_raw);
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int cta = blockIdx.x;
   const int R = p.R;
   for (int e = tid; e < p.Nx; e += nth) sm.Wx[e] = p.Wx[e];
   for (int e = tid; e < p.Ny; e += nth) sm.Wy[fpad(e)] = p.Wy[e];
@@ -972,6 +972,42 @@ __global__ void __launch_bounds__(TTS_THREADS, 1) frame_kernel(FrameParams p, in
   }
 }
 
+template <int OWN>
+__global__ void __launch_bounds__(TTS_THREADS, 1) frame_kernel(FrameParams p, int step_begin, int step_end,
+                                                               int fused) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  frame_run<OWN>(p, smem_raw, blockIdx.x, step_begin, step_end, fused);
+}
+
+// Frames of many independent trackers (streams of any Nx, Ny, R) in one persistent
+// launch: each cluster takes the next frame from a queue of n parameter blocks, runs all
+// its steps, and takes another until the queue is empty. The queue counter
+// (queue_n[0]) is zero at launch; the number of frames is read from queue_n[1], so a
+// captured launch serves any batch up to its parameter capacity.
+template <int OWN>
+__global__ void __launch_bounds__(TTS_THREADS, 1) frame_batch_kernel(const FrameParams* __restrict__ ps,
+                                                                     int* queue_n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ FrameParams sp;
+  __shared__ int item;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int n = ((volatile int*)queue_n)[1];
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) item = atomicAdd(queue_n, 1);
+    cluster.sync();
+    const int it = *cluster.map_shared_rank(&item, 0);
+    cluster.sync();   // every CTA has read the item before rank 0 may overwrite it or exit
+    if (it >= n) break;
+    const int* src = (const int*)(ps + it);
+    int* dst = (int*)&sp;
+    for (int e = threadIdx.x; e < (int)(sizeof(FrameParams) / sizeof(int)); e += blockDim.x) dst[e] = src[e];
+    __syncthreads();
+    frame_run<OWN>(sp, smem_raw, rank, 0, frame_num_steps(sp.K), 1);
+    __syncthreads();
+  }
+}
+
 // The ridge solve alone on a given Hermitian positive-definite system (test hook): G and
 // h in FP64, split into float hi + lo parts; the same Gauss-Jordan + float-float
 // refinement as the frame kernel.
@@ -1024,10 +1060,15 @@ int launch_ridge(const double2* G, const double2* h, int R, double2* gamma, cuda
 }
 
 // Choose the cluster size and chunk length so that the shared-memory layout fits.
-int frame_configure(FrameParams& p, int requested_C) {
-  int maxsm = 0;
-  if (cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0) != cudaSuccess || maxsm <= 0)
-    maxsm = 227 * 1024;
+int frame_configure(FrameParams& p, int requested_C, int smem_limit) {
+  int maxsm = smem_limit;
+  if (maxsm <= 0) {
+    if (cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0) != cudaSuccess || maxsm <= 0)
+      maxsm = 227 * 1024;
+    // the persistent multi-stream kernel keeps its frame parameters in static shared
+    // memory: leave room for them so that one layout serves both kernels
+    maxsm -= 1024;
+  }
   const int preferred = std::max(1, std::min(8, std::min(p.Nx, p.Ny) / 8));
   const int cands[] = {1, 2, 4, 8, 16};
   for (int ci = 0; ci < 5; ++ci) {
@@ -1104,5 +1145,71 @@ int launch_frame(const FrameParams& p, int launch_mode, cudaStream_t st) {
     case 2: return launch_frame_t<2>(p, launch_mode, st);
     case 4: return launch_frame_t<4>(p, launch_mode, st);
     default: return launch_frame_t<8>(p, launch_mode, st);
+  }
+}
+
+template <int OWN>
+static int frame_batch_limits_t(int C, int* max_dyn_smem, int* max_clusters) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, frame_batch_kernel<OWN>) != cudaSuccess) return TTS_ECUDA;
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0) != cudaSuccess) return TTS_ECUDA;
+  const int dyn = optin - (int)fa.sharedSizeBytes;
+  if (cudaFuncSetAttribute(frame_batch_kernel<OWN>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess ||
+      cudaFuncSetAttribute(frame_batch_kernel<OWN>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return TTS_ECUDA;
+  *max_dyn_smem = dyn;
+  if (max_clusters) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(TTS_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = dyn;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, frame_batch_kernel<OWN>, &cfg) != cudaSuccess || nc < 1) return TTS_ECUDA;
+    *max_clusters = nc;
+  }
+  return TTS_OK;
+}
+
+int frame_batch_limits(int own, int C, int* max_dyn_smem, int* max_clusters) {
+  switch (own) {
+    case 1: return frame_batch_limits_t<1>(C, max_dyn_smem, max_clusters);
+    case 2: return frame_batch_limits_t<2>(C, max_dyn_smem, max_clusters);
+    case 4: return frame_batch_limits_t<4>(C, max_dyn_smem, max_clusters);
+    default: return frame_batch_limits_t<8>(C, max_dyn_smem, max_clusters);
+  }
+}
+
+template <int OWN>
+static int launch_frame_batch_t(int C, int clusters, int smem, const FrameParams* ps, int* queue_n, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(clusters * C, 1, 1);
+  cfg.blockDim = dim3(TTS_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, frame_batch_kernel<OWN>, ps, queue_n) == cudaSuccess ? TTS_OK : TTS_ECUDA;
+}
+
+int launch_frame_batch(int own, int C, int clusters, int smem, const FrameParams* ps, int* queue_n, cudaStream_t st) {
+  if (clusters <= 0) return TTS_OK;
+  switch (own) {
+    case 1: return launch_frame_batch_t<1>(C, clusters, smem, ps, queue_n, st);
+    case 2: return launch_frame_batch_t<2>(C, clusters, smem, ps, queue_n, st);
+    case 4: return launch_frame_batch_t<4>(C, clusters, smem, ps, queue_n, st);
+    default: return launch_frame_batch_t<8>(C, clusters, smem, ps, queue_n, st);
   }
 }

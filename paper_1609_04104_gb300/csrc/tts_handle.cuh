@@ -1,0 +1,48 @@
+// The tracker handle behind the C ABI (tts_handle in include/tts.h) and the host-side
+// pieces that the single-stream calls (tts_api.cu) and the multi-stream engine
+// (tts_engine.cu) share.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "tts_internal.cuh"
+
+struct tts_handle {
+  tts_config cfg;
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool own_mem = true;          // dmem came from cudaMalloc (else from an engine arena)
+  void* dmem = nullptr;
+  size_t dbytes = 0;
+  FrameParams fp;
+  float2* X = nullptr;          // image
+  float2* ystage = nullptr;     // acquired rows from host pushes
+  uint8_t* dmask_push = nullptr;
+  uint8_t* dmask_next = nullptr;
+  double* dp = nullptr;
+  int64_t t = 0;                // frames processed
+  bool have_next = false;
+  bool next_on_host = false;
+  std::vector<uint8_t> next_host;
+};
+
+// Validates a configuration (message through tts_last_error on failure).
+int handle_check_config(const tts_config* c);
+// Device bytes one tracker holds, for a cluster of C CTAs (C = 0: the size frame_configure
+// picks); 0 if no cluster size fits.
+size_t handle_footprint(const tts_config& cfg);
+// Creates a tracker whose device state lives in `mem` (at least handle_footprint bytes,
+// 256-byte aligned), or in its own allocation when mem is NULL. Initialisation runs on
+// cfg->cuda_stream (or a stream of its own) and is complete on return.
+int handle_create(const tts_config* cfg, void* mem, tts_handle** out);
+// Fills p (a copy of h->fp) with the frame's mask and rows, staging host inputs into the
+// handle's device buffers on h->stream, with the checks of tts_push_frame.
+int handle_stage_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line_mask, int flags, FrameParams* p);
+// Philox counter of the next draw: stream_id in the high bits, frames processed below.
+uint64_t handle_draw_counter(const tts_handle* h);
+// Lines a draw at this rate keeps: max(central, round(rate Nx)).
+int handle_k_lines(const tts_handle* h, double rate);
+int tts_fail(int code, const char* fmt, const char* detail = nullptr);
+int tts_cuda_fail(cudaError_t e, const char* where);

@@ -16,18 +16,21 @@
 // ------------------------------------------------------------------------------------
 // complex float / double helpers
 // ------------------------------------------------------------------------------------
+// Products are written with explicit fused multiply-adds and the library is compiled
+// without automatic contraction (-fmad=false): every rounding is fixed by the source, so a
+// routine gives bit-identical results in every kernel that inlines it.
 __host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  return make_float2(fmaf(a.x, b.x, -(a.y * b.y)), fmaf(a.x, b.y, a.y * b.x));
 }
 // conj(a) * b
 __host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
-  return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -(a.y * b.x)));
 }
 __host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
-__host__ __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
 // acc += a * b
 __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
   acc.x = fmaf(a.x, b.x, acc.x);
@@ -42,11 +45,18 @@ __device__ __forceinline__ void cfmac(float2& acc, float2 a, float2 b) {
   acc.y = fmaf(a.x, b.y, acc.y);
   acc.y = fmaf(-a.y, b.x, acc.y);
 }
+// acc -= a * b
+__device__ __forceinline__ void cfms(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(-a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(-a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+}
 __host__ __device__ __forceinline__ double2 zmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  return make_double2(fma(a.x, b.x, -(a.y * b.y)), fma(a.x, b.y, a.y * b.x));
 }
 __host__ __device__ __forceinline__ double2 zmulc(double2 a, double2 b) {  // conj(a) * b
-  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -(a.y * b.x)));
 }
 __host__ __device__ __forceinline__ double2 zsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 
@@ -371,9 +381,48 @@ struct FrameParams {
 // B partials}; the last iteration has no step 3.
 __host__ __device__ inline int frame_num_steps(int K) { return 4 * K + 2; }
 
-// host-side launchers (tts_kernels.cu)
+// One line-sampler call (probabilities, then the draw) as a job of a batched launch.
+struct SamplerJob {
+  const float2* A;
+  int Nx, Ny, R;
+  const double* p_in;   // given probabilities, or NULL
+  double* p_out;        // probabilities out, or NULL
+  int policy;
+  double vd_alpha;
+  int k_lines, central;
+  unsigned long long seed, ctr;
+  int with_replacement;
+  const float2* Wx;
+  uint8_t* mask_out;
+  uint8_t* mask_out2;   // optional second copy, or NULL
+  int fft_cols;         // columns of A transformed together
+};
+
+// One image X = A diag(gamma) B^T as a job of a batched launch: tiles [tile0, tile0 + tiles).
+struct ImageJob {
+  const float2* A;
+  const float2* B;
+  const float2* gamma;
+  float2* X;
+  int Nx, Ny, R;
+  int tile0, tiles;
+};
+
+// host-side launchers (tts_kernels.cu, tts_frame.cu)
 int launch_frame(const FrameParams& p, int launch_mode, cudaStream_t st);
-int frame_configure(FrameParams& p, int requested_C);
+// Cluster size and chunk length: requested_C = 0 picks the smallest preferred size whose
+// layout fits; smem_limit = 0 means the device's opt-in maximum.
+int frame_configure(FrameParams& p, int requested_C, int smem_limit = 0);
+int frame_own(const FrameParams& p);
+// Persistent launch over a queue of frames (queue_n[0] = 0, queue_n[1] = count): `clusters`
+// clusters of C CTAs with `smem` bytes of dynamic shared memory each.
+int frame_batch_limits(int own, int C, int* max_dyn_smem, int* max_clusters);
+int launch_frame_batch(int own, int C, int clusters, int smem, const FrameParams* ps, int* queue_n, cudaStream_t st);
+SamplerJob sampler_job(const float2* A, int Nx, int Ny, int R, const double* p_in, double* p_out, int policy,
+                       double vd_alpha, int k_lines, int central, uint64_t seed, uint64_t ctr, int with_replacement,
+                       const float2* Wx, uint8_t* mask_out, uint8_t* mask_out2);
+int launch_sampler_batch(const SamplerJob* jobs, const int* n, int capacity, cudaStream_t st);
+int launch_image_batch(const ImageJob* jobs, const int* n, int grid, cudaStream_t st);
 int launch_image(const float2* A, const float2* B, const float2* gamma, float2* X, int Nx, int Ny, int R,
                  cudaStream_t st);
 int launch_sampler(const float2* A, int Nx, int Ny, int R, const double* p_in, double* p_out, int policy,

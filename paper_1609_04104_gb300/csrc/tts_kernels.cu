@@ -10,13 +10,11 @@ namespace {
 // X = A diag(gamma) B^T  (the image of the most recent frame, cf. §IV-A X_t)
 // 32 x 32 output tile per CTA; A and B rows of the tile staged in shared memory.
 // ------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) image_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
-                                                    const float2* __restrict__ gamma, float2* __restrict__ X,
-                                                    int Nx, int Ny, int R) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void image_tile(const float2* __restrict__ A, const float2* __restrict__ B,
+                                           const float2* __restrict__ gamma, float2* __restrict__ X, int Nx, int Ny,
+                                           int R, int i0, int j0, unsigned char* smem_raw) {
   float2* sA = (float2*)smem_raw;     // 32 x (R+1), A[i][r] gamma_r
   float2* sB = sA + 32 * (R + 1);     // 32 x (R+1)
-  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
   const int tid = threadIdx.x;
   for (int base = tid; base < 32 * R; base += 4 * blockDim.x) {
     float2 va[4], vb[4], vg[4];
@@ -55,6 +53,36 @@ __global__ void __launch_bounds__(256) image_kernel(const float2* __restrict__ A
   }
 }
 
+__global__ void __launch_bounds__(256) image_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
+                                                    const float2* __restrict__ gamma, float2* __restrict__ X,
+                                                    int Nx, int Ny, int R) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  image_tile(A, B, gamma, X, Nx, Ny, R, blockIdx.y * 32, blockIdx.x * 32, smem_raw);
+}
+
+// Images of many trackers: the 32 x 32 tiles of all jobs form one list (job k owns tiles
+// [tile0, tile0 + tiles) in row-major tile order), walked grid-stride; the number of jobs
+// is read from device memory (*n).
+__global__ void __launch_bounds__(256) image_batch_kernel(const ImageJob* __restrict__ jobs, const int* n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nj = *n;
+  if (nj <= 0) return;
+  const int total = jobs[nj - 1].tile0 + jobs[nj - 1].tiles;
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    int lo = 0, hi = nj - 1;   // last job with tile0 <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].tile0 <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const ImageJob& j = jobs[lo];
+    const int tl = t - j.tile0, tx = (j.Ny + 31) / 32;
+    const int ti = tl / tx, tj = tl - ti * tx;
+    image_tile(j.A, j.B, j.gamma, j.X, j.Nx, j.Ny, j.R, ti * 32, tj * 32, smem_raw);
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------------------------
 // Line sampler, one CTA.
 //  (1) probabilities: informative scores of §V-B marginalised over readout (§VI-C),
@@ -78,11 +106,20 @@ __device__ __forceinline__ int upper_bound_u64(const unsigned long long* Q, int 
   return lo;
 }
 
-__global__ void __launch_bounds__(SAMPLER_THREADS) sampler_kernel(
-    const float2* __restrict__ A, int Nx, int Ny, int R, const double* __restrict__ p_in, double* p_out, int policy,
-    double vd_alpha, int k_lines, int central, unsigned long long seed, unsigned long long ctr, int with_replacement,
-    const float2* __restrict__ Wx, uint8_t* mask_out, uint8_t* mask_out2, int fft_cols) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void sampler_run(const SamplerJob& job, unsigned char* smem_raw) {
+  const float2* __restrict__ A = job.A;
+  const int Nx = job.Nx, Ny = job.Ny, R = job.R;
+  const double* __restrict__ p_in = job.p_in;
+  double* p_out = job.p_out;
+  const int policy = job.policy;
+  const double vd_alpha = job.vd_alpha;
+  const int k_lines = job.k_lines, central = job.central;
+  const unsigned long long seed = job.seed, ctr = job.ctr;
+  const int with_replacement = job.with_replacement;
+  const float2* __restrict__ Wx = job.Wx;
+  uint8_t* mask_out = job.mask_out;
+  uint8_t* mask_out2 = job.mask_out2;
+  const int fft_cols = job.fft_cols;
   double* p = (double*)smem_raw;                                   // Nx
   unsigned long long* Q = (unsigned long long*)(p + TTS_MAX_N);    // Nx
   float* rowacc = (float*)(Q + TTS_MAX_N);                          // Nx
@@ -291,6 +328,21 @@ __global__ void __launch_bounds__(SAMPLER_THREADS) sampler_kernel(
   }
 }
 
+__global__ void __launch_bounds__(SAMPLER_THREADS) sampler_kernel(SamplerJob job) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  sampler_run(job, smem_raw);
+}
+
+// One CTA per job; the number of jobs is read from device memory (*n), so a captured
+// launch sized for the capacity serves any smaller batch.
+__global__ void __launch_bounds__(SAMPLER_THREADS) sampler_batch_kernel(const SamplerJob* __restrict__ jobs,
+                                                                        const int* n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if ((int)blockIdx.x >= *n) return;
+  const SamplerJob job = jobs[blockIdx.x];
+  sampler_run(job, smem_raw);
+}
+
 // ------------------------------------------------------------------------------------
 // CN(0, 1/N) factor entries from Philox4x32-10 and the Box-Muller transform.
 // ------------------------------------------------------------------------------------
@@ -396,19 +448,72 @@ int launch_image(const float2* A, const float2* B, const float2* gamma, float2* 
   return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
 }
 
+SamplerJob sampler_job(const float2* A, int Nx, int Ny, int R, const double* p_in, double* p_out, int policy,
+                       double vd_alpha, int k_lines, int central, uint64_t seed, uint64_t ctr, int with_replacement,
+                       const float2* Wx, uint8_t* mask_out, uint8_t* mask_out2) {
+  SamplerJob j;
+  j.A = A;
+  j.Nx = Nx;
+  j.Ny = Ny;
+  j.R = R;
+  j.p_in = p_in;
+  j.p_out = p_out;
+  j.policy = policy;
+  j.vd_alpha = vd_alpha;
+  j.k_lines = k_lines;
+  j.central = central;
+  j.seed = (unsigned long long)seed;
+  j.ctr = (unsigned long long)ctr;
+  j.with_replacement = with_replacement;
+  j.Wx = Wx;
+  j.mask_out = mask_out;
+  j.mask_out2 = mask_out2;
+  j.fft_cols = max(1, min(min(R, 64), 8192 / max(Nx, 1)));
+  return j;
+}
+
+size_t sampler_smem(int Nx, int fft_cols) {
+  return sizeof(double) * TTS_MAX_N + sizeof(unsigned long long) * TTS_MAX_N + sizeof(float) * TTS_MAX_N +
+         sizeof(float) * 64 + sizeof(int) * TTS_MAX_N + TTS_MAX_N + sizeof(int) * 8 +
+         sizeof(float2) * fsz(TTS_MAX_N) + sizeof(float2) * 2 * fft_cols * (fsz(Nx) | 1) + 64;
+}
+
+int launch_image_batch(const ImageJob* jobs, const int* n, int grid, cudaStream_t st) {
+  const int smem = 2 * 32 * (TTS_MAX_R + 1) * (int)sizeof(float2);
+  if (grid <= 0) return TTS_OK;
+  image_batch_kernel<<<grid, 256, smem, st>>>(jobs, n);
+  return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
+}
+
 int launch_sampler(const float2* A, int Nx, int Ny, int R, const double* p_in, double* p_out, int policy,
                    double vd_alpha, int k_lines, int central, uint64_t seed, uint64_t ctr, int with_replacement,
                    const float2* Wx, uint8_t* mask_out, uint8_t* mask_out2, cudaStream_t st) {
-  const int fft_cols = max(1, min(min(R, 64), 8192 / max(Nx, 1)));
-  const size_t smem = sizeof(double) * TTS_MAX_N + sizeof(unsigned long long) * TTS_MAX_N +
-                      sizeof(float) * TTS_MAX_N + sizeof(float) * 64 + sizeof(int) * TTS_MAX_N + TTS_MAX_N +
-                      sizeof(int) * 8 + sizeof(float2) * fsz(TTS_MAX_N) +
-                      sizeof(float2) * 2 * fft_cols * (fsz(Nx) | 1) + 64;
+  const SamplerJob j = sampler_job(A, Nx, Ny, R, p_in, p_out, policy, vd_alpha, k_lines, central, seed, ctr,
+                                   with_replacement, Wx, mask_out, mask_out2);
+  const size_t smem = sampler_smem(Nx, j.fft_cols);
   cudaError_t e = cudaFuncSetAttribute(sampler_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return TTS_ECUDA;
-  sampler_kernel<<<1, SAMPLER_THREADS, smem, st>>>(A, Nx, Ny, R, p_in, p_out, policy, vd_alpha, k_lines, central,
-                                                   (unsigned long long)seed, (unsigned long long)ctr,
-                                                   with_replacement, Wx, mask_out, mask_out2, fft_cols);
+  sampler_kernel<<<1, SAMPLER_THREADS, smem, st>>>(j);
+  return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
+}
+
+// Largest shared memory any sampler job needs (Nx <= TTS_MAX_N, at most 8192 staged
+// entries of A): the capacity of a batched launch.
+size_t sampler_smem_max() {
+  size_t m = 0;
+  for (int Nx = 1; Nx <= TTS_MAX_N; ++Nx) m = std::max(m, sampler_smem(Nx, std::max(1, std::min(64, 8192 / Nx))));
+  return m;
+}
+
+// capacity 0 only sets the kernel's shared-memory attribute (done before any capture).
+int launch_sampler_batch(const SamplerJob* jobs, const int* n, int capacity, cudaStream_t st) {
+  const size_t smem = sampler_smem_max();
+  if (capacity <= 0) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(sampler_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e == cudaSuccess ? TTS_OK : TTS_ECUDA;
+  }
+  sampler_batch_kernel<<<capacity, SAMPLER_THREADS, smem, st>>>(jobs, n);
   return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
 }
 

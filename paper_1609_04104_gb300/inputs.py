@@ -190,3 +190,60 @@ def init_factors(Nx: int, Ny: int, R: int, seed: int = 0) -> tuple[np.ndarray, n
 def observed_rows(Y_t: np.ndarray, mask: np.ndarray) -> np.ndarray:
     """The acquired rows of one k-space frame, in increasing row order (|S| x Ny)."""
     return np.ascontiguousarray(Y_t[np.flatnonzero(mask)])
+
+
+# ---- many streams ------------------------------------------------------------------
+
+UNEVEN_SIZES = (128, 160, 192, 256, 320)
+UNEVEN_RANKS = (16, 32, 48)
+UNEVEN_RATES = (1.0 / 4.0, 1.0 / 6.0, 1.0 / 8.0)
+
+
+def uneven_streams(n: int = 64, T: int = 100, seed: int = 0) -> list[Workload]:
+    """Independent cine slices of uneven size: (Nx, Ny) drawn independently from
+    {128, 160, 192, 256, 320}, R from {16, 32, 48}, sampling rate from {1/4, 1/6, 1/8};
+    CINE256's phantom family, tracker parameters and warm start; stream k has seed k."""
+    rng = np.random.default_rng([seed, 0xBA7C])
+    out = []
+    for k in range(n):
+        Nx, Ny = (int(v) for v in rng.choice(UNEVEN_SIZES, size=2))
+        R = int(rng.choice(UNEVEN_RANKS))
+        rate = float(UNEVEN_RATES[int(rng.integers(len(UNEVEN_RATES)))])
+        out.append(dataclasses.replace(CINE256, name=f"stream{k}_{Nx}x{Ny}_r{R}", Nx=Nx, Ny=Ny, R=R, T=T,
+                                       rate=rate, seed=seed * 100003 + k))
+    return out
+
+
+# 5-smooth square sizes in [128, 384] (radices of the transforms stay in {2, 3, 5})
+SERVING_SIZES = (128, 144, 160, 180, 192, 200, 216, 240, 250, 256, 270, 288, 300, 320, 360, 384)
+
+
+@dataclasses.dataclass(frozen=True)
+class Arrival:
+    """One serving request: a cine stream that opens at `t_open` seconds and sends
+    `frames` frames at `fps` frames per second."""
+
+    t_open: float
+    fps: float
+    frames: int
+    work: Workload
+
+
+def serving_arrivals(n: int = 256, rate_per_s: float = 4.0, lifetime: int = 300, seed: int = 0,
+                     preload: bool = False) -> list[Arrival]:
+    """Poisson arrivals (mean `rate_per_s` new streams per second; all at t = 0 when
+    `preload`), each stream 20-50 frames/s for `lifetime` frames, square 5-smooth
+    matrix 128-384, R in {16, 24, 32, 40, 48}, informative sampling at 1/8."""
+    rng = np.random.default_rng([seed, 0x5E7E])
+    t = 0.0
+    out = []
+    for k in range(n):
+        if not preload:
+            t += float(rng.exponential(1.0 / rate_per_s))
+        N = int(rng.choice(SERVING_SIZES))
+        R = int(rng.choice((16, 24, 32, 40, 48)))
+        fps = float(rng.uniform(20.0, 50.0))
+        w = dataclasses.replace(CINE256, name=f"serve{k}_{N}_r{R}", Nx=N, Ny=N, R=R, T=lifetime,
+                                rate=1.0 / 8.0, seed=seed * 100003 + k)
+        out.append(Arrival(t_open=t, fps=fps, frames=lifetime, work=w))
+    return out

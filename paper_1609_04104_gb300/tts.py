@@ -17,6 +17,9 @@ LIB_PATH = os.path.join(HERE, "libtts.so")
 
 TTS_OK = 0
 TTS_EINVAL, TTS_ENOMEM, TTS_ECUDA, TTS_ERANGE, TTS_ENONFINITE, TTS_ETIMEOUT, TTS_ESTATE = -1, -2, -3, -4, -5, -6, -7
+TTS_EBUSY = -8
+TTS_ENGINE_GRAPH = 1
+TTS_ENGINE_MAX_SLOTS = 4096
 TTS_DEVICE_PTRS = 1
 TTS_FULL_FRAME = 2
 TTS_POLICY_UNIFORM, TTS_POLICY_VARDENS, TTS_POLICY_INFORMATIVE = 0, 1, 2
@@ -27,7 +30,10 @@ EXPORTS = [
     "tts_config_init", "tts_create", "tts_create_ex", "tts_destroy", "tts_set_factors", "tts_get_factors",
     "tts_get_stats", "tts_set_stats", "tts_get_gamma", "tts_push_frame", "tts_image", "tts_next_mask",
     "tts_line_probs", "tts_sample_lines_from_probs", "tts_save", "tts_load", "tts_synchronize",
-    "tts_launches_per_frame", "tts_ridge_solve", "tts_fft2d", "tts_push_frame_noalloc", "tts_last_error",
+    "tts_launches_per_frame", "tts_ridge_solve", "tts_fft2d", "tts_push_frame_noalloc",
+    "tts_stream_footprint", "tts_engine_create", "tts_engine_destroy", "tts_engine_admit", "tts_engine_release",
+    "tts_engine_handle", "tts_engine_step", "tts_engine_image", "tts_engine_mask", "tts_engine_synchronize",
+    "tts_engine_info", "tts_last_error",
 ]
 
 
@@ -55,6 +61,14 @@ class tts_frame_args(ctypes.Structure):
         ("mm_iters", ctypes.c_int), ("update", ctypes.c_int),
         ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("stats", ctypes.c_void_p), ("gamma", ctypes.c_void_p),
         ("y_rows", ctypes.c_void_p), ("line_mask", ctypes.c_void_p), ("flags", ctypes.c_int),
+    ]
+
+
+class tts_engine_stats(ctypes.Structure):
+    _fields_ = [
+        ("arena_bytes", ctypes.c_size_t), ("arena_used", ctypes.c_size_t), ("arena_largest_free", ctypes.c_size_t),
+        ("active", ctypes.c_int), ("max_slots", ctypes.c_int), ("cluster_ctas", ctypes.c_int),
+        ("resident_clusters", ctypes.c_int), ("owned_outputs", ctypes.c_int), ("steps", ctypes.c_int64),
     ]
 
 
@@ -96,6 +110,17 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "tts_ridge_solve": (I, [P, P, I, P]),
         "tts_fft2d": (I, [P, P, I, I, I, I, P]),
         "tts_push_frame_noalloc": (I, [ctypes.POINTER(tts_frame_args), P]),
+        "tts_stream_footprint": (I, [ctypes.POINTER(tts_config), ctypes.POINTER(ctypes.c_size_t)]),
+        "tts_engine_create": (I, [ctypes.c_size_t, I, I, I, P, ctypes.POINTER(H)]),
+        "tts_engine_destroy": (None, [H]),
+        "tts_engine_admit": (I, [H, ctypes.POINTER(tts_config), ctypes.POINTER(I)]),
+        "tts_engine_release": (I, [H, I]),
+        "tts_engine_handle": (I, [H, I, ctypes.POINTER(H)]),
+        "tts_engine_step": (I, [H, I, P, P, P, P, P, I]),
+        "tts_engine_image": (I, [H, I, P, I]),
+        "tts_engine_mask": (I, [H, I, P, I]),
+        "tts_engine_synchronize": (I, [H]),
+        "tts_engine_info": (I, [H, ctypes.POINTER(tts_engine_stats)]),
         "tts_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -254,7 +279,7 @@ def tts_launches_per_frame(h) -> int:
 
 
 def tts_ridge_solve(G: np.ndarray, h: np.ndarray) -> np.ndarray:
-    """FP64 LDL^H solve of G gamma = h on the device (G Hermitian positive definite)."""
+    """Solve of G gamma = h to FP64 accuracy on the device (G Hermitian positive definite)."""
     G = np.ascontiguousarray(G, np.complex128)
     h = np.ascontiguousarray(h, np.complex128)
     g = np.zeros(h.shape[0], np.complex128)
@@ -285,6 +310,149 @@ def tts_push_frame_noalloc(A, B, stats, gamma, y_rows, line_mask, lambda_forget,
                           line_mask.data_ptr(), TTS_FULL_FRAME if full_frame else 0)
     s = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(load().tts_push_frame_noalloc(ctypes.byref(args), s))
+
+
+def tts_stream_footprint(cfg: tts_config) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load().tts_stream_footprint(ctypes.byref(cfg), ctypes.byref(n)))
+    return n.value
+
+
+def tts_engine_create(arena_bytes, max_slots, cluster_ctas=0, flags=TTS_ENGINE_GRAPH, stream=None) -> int:
+    e = ctypes.c_void_p()
+    s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(load().tts_engine_create(arena_bytes, max_slots, cluster_ctas, flags, s, ctypes.byref(e)))
+    return e.value
+
+
+def tts_engine_destroy(e) -> None:
+    load().tts_engine_destroy(e)
+
+
+def tts_engine_admit(e, cfg: tts_config) -> int:
+    slot = ctypes.c_int(-1)
+    _check(load().tts_engine_admit(e, ctypes.byref(cfg), ctypes.byref(slot)))
+    return slot.value
+
+
+def tts_engine_release(e, slot) -> None:
+    _check(load().tts_engine_release(e, slot))
+
+
+def tts_engine_handle(e, slot) -> int:
+    h = ctypes.c_void_p()
+    _check(load().tts_engine_handle(e, slot, ctypes.byref(h)))
+    return h.value
+
+
+def tts_engine_step(e, slots, frames, rates, seeds, masks=None, full_frame=False) -> None:
+    """One frame for each listed slot: frames[k] (numpy host arrays or torch CUDA tensors,
+    all of one kind), masks None or a list (entries None = the drawn mask)."""
+    n = len(slots)
+    if not (len(frames) == len(rates) == len(seeds) == n) or (masks is not None and len(masks) != n):
+        raise ValueError("slots, frames, rates, seeds (and masks) must have one entry per slot")
+    if n == 0:
+        _check(load().tts_engine_step(e, 0, None, None, None, None, None, 0))
+        return
+    ptrs, kinds = [], set()
+    for f in frames:
+        p, k = _ptr(f, np.complex64)
+        ptrs.append(p)
+        kinds.add(k)
+    mptrs = None
+    if masks is not None:
+        mptrs = []
+        for m in masks:
+            p, k = _ptr(m, np.uint8)
+            mptrs.append(p or 0)
+            if m is not None:
+                kinds.add(k)
+    if len(kinds) > 1:
+        raise ValueError("mix of host and device buffers in one call")
+    flags = kinds.pop() | (TTS_FULL_FRAME if full_frame else 0)
+    c_slots = (ctypes.c_int * n)(*slots)
+    c_frames = (ctypes.c_void_p * n)(*ptrs)
+    c_masks = (ctypes.c_void_p * n)(*mptrs) if mptrs is not None else None
+    c_rates = (ctypes.c_double * n)(*rates)
+    c_seeds = (ctypes.c_uint64 * n)(*seeds)
+    _check(load().tts_engine_step(e, n, c_slots, c_frames, c_masks, c_rates, c_seeds, flags))
+
+
+def tts_engine_image(e, slot, out) -> None:
+    po, fo = _ptr(out, np.complex64)
+    _check(load().tts_engine_image(e, slot, po, fo))
+
+
+def tts_engine_mask(e, slot, out) -> None:
+    po, fo = _ptr(out, np.uint8)
+    _check(load().tts_engine_mask(e, slot, po, fo))
+
+
+def tts_engine_synchronize(e) -> None:
+    _check(load().tts_engine_synchronize(e))
+
+
+def tts_engine_info(e) -> dict:
+    st = tts_engine_stats()
+    _check(load().tts_engine_info(e, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in tts_engine_stats._fields_}
+
+
+class Engine:
+    """Convenience owner of one engine (same calls as the C ABI)."""
+
+    def __init__(self, arena_bytes, max_slots, cluster_ctas=0, graph=True, stream=None):
+        self.e = tts_engine_create(arena_bytes, max_slots, cluster_ctas, TTS_ENGINE_GRAPH if graph else 0, stream)
+        self.shapes = {}
+
+    def close(self):
+        if self.e:
+            tts_engine_destroy(self.e)
+            self.e = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def admit(self, Nx, Ny, R, lambda_forget, mu, **cfg) -> int:
+        slot = tts_engine_admit(self.e, tts_config_init(Nx, Ny, R, lambda_forget, mu, **cfg))
+        self.shapes[slot] = (Nx, Ny, R)
+        return slot
+
+    def release(self, slot):
+        tts_engine_release(self.e, slot)
+        self.shapes.pop(slot, None)
+
+    def step(self, slots, frames, rates, seeds, masks=None, full_frame=False):
+        tts_engine_step(self.e, slots, frames, rates, seeds, masks, full_frame)
+
+    def image(self, slot, out=None):
+        if out is None:
+            Nx, Ny, _ = self.shapes[slot]
+            out = np.zeros((Nx, Ny), np.complex64)
+        tts_engine_image(self.e, slot, out)
+        return out
+
+    def mask(self, slot, out=None):
+        if out is None:
+            out = np.zeros(self.shapes[slot][0], np.uint8)
+        tts_engine_mask(self.e, slot, out)
+        return out
+
+    def factors(self, slot):
+        Nx, Ny, R = self.shapes[slot]
+        A = np.zeros((Nx, R), np.complex64)
+        B = np.zeros((Ny, R), np.complex64)
+        tts_get_factors(tts_engine_handle(self.e, slot), A, B)
+        return A, B
+
+    def synchronize(self):
+        tts_engine_synchronize(self.e)
+
+    def info(self) -> dict:
+        return tts_engine_info(self.e)
 
 
 class Tracker:
