@@ -48,6 +48,15 @@ def frame_traffic():
     return FRAME_TRAFFIC_BYTES if h == FRAME_TRAFFIC_SRC_SHA else None
 
 
+def frame_flops(Nx, Ny, R, K, s):
+    """Real FLOPs of one frame in the separable form the frame kernel runs (|S| = s lines):
+    ingest (row transforms of the acquired rows, Ahat_S, B^H B, P) plus K MM iterations
+    (Gram, right-hand side, Theta conj(B), Theta'^T conj(A), refreshed partial sums)."""
+    ingest = 8 * (s * Ny * R + s * Nx * R + Ny * R * R) + s * 5 * Ny * math.log2(Ny)
+    it = 8 * (2 * R * R * s + s * R * R + 2 * Nx * s * R + 2 * Ny * s * R + 2 * Ny * R * R)
+    return ingest + K * it
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -61,6 +70,19 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--cpu-sample-frames", type=int, default=8)
+    ap.add_argument("--batched", action="store_true",
+                    help="64 uneven streams through the multi-stream engine vs one stream at a time")
+    ap.add_argument("--streams", type=int, default=64)
+    ap.add_argument("--stream-frames", type=int, default=100)
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="pick the engine's cluster size with the autotuner")
+    ap.add_argument("--serve", action="store_true",
+                    help="real-time serving loop: Poisson stream arrivals, admission by HBM footprint")
+    ap.add_argument("--serve-streams", type=int, default=256)
+    ap.add_argument("--serve-rate", type=float, default=4.0, help="mean new streams per second")
+    ap.add_argument("--serve-frames", type=int, default=300, help="frames per stream (lifetime)")
+    ap.add_argument("--preload", action="store_true", help="all streams arrive at t = 0")
+    ap.add_argument("--arena-mib", type=int, default=4096, help="engine arena (admission budget)")
     ap.add_argument("--fft2d", action="store_true", help="time the batched unitary 2D DFT kernel instead")
     ap.add_argument("--fft-n", type=int, default=256)
     ap.add_argument("--fft-batch", type=int, default=512)
@@ -269,12 +291,7 @@ def run_tts(args, rank, world):
     Nx, Ny, R, K = w.Nx, w.Ny, w.R, w.mm_iters
     S = w.k_lines
     nfull = min(w.warmup_frames, T)
-    flops = []
-    for t in range(T):
-        s = Nx if t < w.warmup_frames else S
-        ingest = 8 * (s * Ny * R + s * Nx * R + Ny * R * R) + s * 5 * Ny * math.log2(Ny)
-        it = 8 * (2 * R * R * s + s * R * R + 2 * Nx * s * R + 2 * Ny * s * R + 2 * Ny * R * R)
-        flops.append(ingest + K * it)
+    flops = [frame_flops(Nx, Ny, R, K, Nx if t < w.warmup_frames else S) for t in range(T)]
     flops_per_launch = float(np.mean(flops))
     sm_mhz = (clk or {}).get("sm_max_mhz", 2070.0) if clk else 2070.0
     peak_tflops = 152 * 128 * 2 * 2070e6 / 1e12
@@ -420,8 +437,337 @@ def run_fft2d(args):
                                                  "note": "algorithmic bytes 16 N^2 per image; two passes move 32 N^2"}}
 
 
+# ------------------------------------------------------------------------------------
+# many streams: the multi-stream engine against one stream at a time
+# ------------------------------------------------------------------------------------
+BANK_FRAMES = 20   # one period of the radius modulation
+
+
+def frame_banks(streams, F):
+    """k-space frames on the device, per (Nx, Ny): F frames of the first stream of that
+    size (generation on the host costs ~25 ms a frame, so streams of one size share them;
+    every stream keeps its own initial factors, line draws and state)."""
+    import torch
+    from paper_1609_04104_gb300 import inputs
+    banks = {}
+    for w in streams:
+        if (w.Nx, w.Ny) not in banks:
+            Y = inputs.kspace(w, inputs.phantom(w, F))
+            banks[(w.Nx, w.Ny)] = torch.from_numpy(Y).cuda()
+    return banks
+
+
+def run_batched(args):
+    import ctypes
+
+    import torch
+
+    from paper_1609_04104_gb300 import inputs, tts
+    lib = tts.load()
+    n, T = args.streams, args.stream_frames
+    ws = inputs.uneven_streams(n, T=T)
+    F = min(BANK_FRAMES, T)
+    banks = frame_banks(ws, F)
+    ones = {N: torch.ones(N, dtype=torch.uint8, device="cuda") for N in {w.Nx for w in ws}}
+    cfgs = [dict(mm_iters=w.mm_iters, central_lines=w.central_lines, init_seed=w.seed, stream_id=k)
+            for k, w in enumerate(ws)]
+    tuned = None
+    C = args.cluster or 4
+    if args.autotune:
+        C, tuned = tts.tts_engine_autotune([tts.tts_config_init(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, **cfgs[k])
+                                            for k, w in enumerate(ws)], steps=5)
+    # arena: every stream at the largest cluster size (footprints grow with the size)
+    foot = sum(tts.tts_stream_footprint(tts.tts_config_init(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, cluster_ctas=16,
+                                                            **cfgs[k])) for k, w in enumerate(ws))
+    stream = torch.cuda.Stream()
+    eng = tts.Engine(foot + (64 << 20), n, cluster_ctas=C, graph=not args.no_graph, stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    rates = (ctypes.c_double * n)(*[w.rate for w in ws])
+    seeds = (ctypes.c_uint64 * n)(*[w.seed + 1000 for w in ws])
+    flags = tts.TTS_DEVICE_PTRS | tts.TTS_FULL_FRAME
+
+    def admit_all():
+        return [eng.admit(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, **cfgs[k]) for k, w in enumerate(ws)]
+
+    def prepared(slots):
+        """ctypes arguments of every step, built before anything is timed."""
+        c_slots = (ctypes.c_int * n)(*slots)
+        out = []
+        for t in range(T):
+            fr = (ctypes.c_void_p * n)(*[banks[(w.Nx, w.Ny)][t % F].data_ptr() for w in ws])
+            ms = (ctypes.c_void_p * n)(*[ones[w.Nx].data_ptr() if t < w.warmup_frames else 0 for w in ws])
+            out.append((c_slots, fr, ms))
+        return out
+
+    def step(a):
+        rc = lib.tts_engine_step(eng.e, n, a[0], a[1], a[2], rates, seeds, flags)
+        if rc < 0:
+            raise tts.TtsError(rc, tts.tts_last_error())
+
+    slots = admit_all()
+    steps = prepared(slots)
+    with torch.cuda.stream(stream):
+        for t in range(max(3, args.warmup)):
+            step(steps[t % T])
+    torch.cuda.synchronize()
+    for s_ in slots:
+        eng.release(s_)
+    slots = admit_all()
+    steps = prepared(slots)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(T)]
+    clocks = ClockSampler(0, enabled=not args.no_clocks)
+    with torch.cuda.stream(stream):
+        for t in range(T):
+            flush.zero_()
+            ev[t][0].record(stream)
+            step(steps[t])
+            ev[t][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    value = n * T / (float(np.sum(step_ms)) / 1e3)
+    last = {k: eng.image(slots[k]) for k in range(n)}
+    slot_C = [eng.cluster_ctas(slots[k]) for k in range(n)]
+    info = eng.info()
+
+    # one stream at a time through its own handle, at the cluster size the library picks
+    # for a lone stream (latency-optimal); every 8th stream again at its engine cluster
+    # size, where the images must be bit-identical to the engine's
+    plain_ms, worst, same = 0.0, 0.0, True
+    mask = {N: torch.zeros(N, dtype=torch.uint8, device="cuda") for N in ones}
+
+    def alone(k, w, cluster, timed):
+        trk = tts.Tracker(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, cluster_ctas=cluster, cuda_stream=stream,
+                          **cfgs[k])
+        ring = torch.empty((w.Nx, w.Ny), dtype=torch.complex64, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            if timed:
+                flush.zero_()
+            e0.record(stream)
+            for t in range(T):
+                m = ones[w.Nx]
+                if t >= w.warmup_frames:
+                    tts.tts_next_mask(trk.h, w.rate, w.seed + 1000, mask[w.Nx])
+                    m = mask[w.Nx]
+                tts.tts_push_frame(trk.h, banks[(w.Nx, w.Ny)][t % F], m, full_frame=True)
+                tts.tts_image(trk.h, t, ring)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        trk.close()
+        return e0.elapsed_time(e1), ring.cpu().numpy()
+
+    for k, w in enumerate(ws):
+        ms_k, x = alone(k, w, 0, True)
+        plain_ms += ms_k
+        worst = max(worst, float(np.linalg.norm(last[k] - x) / max(np.linalg.norm(x), 1e-30)))
+        if k % 8 == 0:
+            _, x2 = alone(k, w, slot_C[k], False)
+            same = same and bool(np.array_equal(last[k].view(np.uint32), x2.view(np.uint32)))
+    plain = n * T / (plain_ms / 1e3)
+
+    # end to end: host frames (pinned) in, every stream's image back to the host, each step
+    e2e = None
+    if not args.no_e2e:
+        for s_ in slots:
+            eng.release(s_)
+        slots = admit_all()
+        hb = {key: b.cpu().pin_memory() for key, b in banks.items()}
+        outs = [torch.empty((w.Nx, w.Ny), dtype=torch.complex64).pin_memory() for w in ws]
+        hones = {N: np.ones(N, np.uint8) for N in ones}
+        c_slots = (ctypes.c_int * n)(*slots)
+        hflags = tts.TTS_FULL_FRAME
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2d = d2h = 0
+        for t in range(T):
+            fr = (ctypes.c_void_p * n)(*[hb[(w.Nx, w.Ny)][t % F].data_ptr() for w in ws])
+            ms = (ctypes.c_void_p * n)(*[hones[w.Nx].ctypes.data if t < w.warmup_frames else 0 for w in ws])
+            rc = lib.tts_engine_step(eng.e, n, c_slots, fr, ms, rates, seeds, hflags)
+            if rc < 0:
+                raise tts.TtsError(rc, tts.tts_last_error())
+            for k in range(n):
+                lib.tts_engine_image(eng.e, slots[k], ctypes.c_void_p(outs[k].data_ptr()), tts.TTS_DEVICE_PTRS * 0)
+            if t == 0:
+                h2d = sum(w.Nx * w.Ny * 8 + (w.Nx if t < w.warmup_frames else 0) for w in ws)
+                d2h = sum(w.Nx * w.Ny * 8 for w in ws)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        e2e = {"value": n * T / el, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "note": "one step = one frame of every stream; full host frames in, every image out"}
+    eng.close()
+
+    flops_step = float(np.mean([sum(frame_flops(w.Nx, w.Ny, w.R, w.mm_iters, w.Nx if t < w.warmup_frames else
+                                                w.k_lines) for w in ws) for t in range(T)]))
+    mean_s = float(np.mean(step_ms)) * 1e-3
+    peak_tflops = 152 * 128 * 2 * 2070e6 / 1e12
+    achieved = flops_step / mean_s / 1e12
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": T, "warmup": max(3, args.warmup),
+        "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (FP64 ridge solve)", "data": "synthetic",
+        "config": {"workload": f"uneven_streams_{n}", "streams": n, "T": T,
+                   "sizes": sorted({(w.Nx, w.Ny) for w in ws}), "ranks": sorted({w.R for w in ws}),
+                   "rates": sorted({round(w.rate, 4) for w in ws}), "mm_iters": 3, "cluster_ctas": C,
+                   "cluster_ctas_used": sorted(set(slot_C)), "autotune_ms_per_step": tuned,
+                   "graph": not args.no_graph, "frames": f"per-size bank of {F} phantom frames, cycled",
+                   "l2": "256 MiB buffer written before every timed step",
+                   "step": "one frame of every stream: MM iterations, image, next-frame line draw"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                       "note": "a frame completes with its step"},
+        "plain_path": {"value": plain, "unit": UNIT,
+                       "note": "the same streams one at a time, own handle each, lone-stream cluster size"},
+        "speedup_vs_plain": value / plain,
+        "nrmse_vs_plain_path": worst,
+        "bit_identical_at_same_cluster_size": same,
+        "engine": info,
+        "e2e": e2e,
+        "gpu_launches": 3 * T,
+        "roofline": {"bound": "alu", "kernel": "engine step (frame_batch_kernel + image + sampler)",
+                     "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                     "traffic": None, "flops_per_step": flops_step,
+                     "peak_note": "FP32 SIMT peak 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived)"},
+        "clocks": clk,
+    }
+
+
+def run_serve(args):
+    """Serving loop in real time. Streams open at their arrival times (Poisson, or all at
+    t = 0 with --preload) and are admitted as slots and arena memory allow (the rest wait
+    in arrival order); each stream's frame j arrives at t_open + j / fps. Every pass of
+    the loop takes the oldest waiting frame of each admitted stream into one engine step
+    (continuous batching: streams join, leave and skip steps freely) and waits for it;
+    a frame's latency runs from its arrival to the end of the step that processed it."""
+    import collections
+    import ctypes
+
+    import torch
+
+    from paper_1609_04104_gb300 import inputs, tts
+    lib = tts.load()
+    arr = inputs.serving_arrivals(n=args.serve_streams, rate_per_s=args.serve_rate, lifetime=args.serve_frames,
+                                  preload=args.preload)
+    F = BANK_FRAMES
+    banks = frame_banks([a.work for a in arr], F)
+    ones = {N: torch.ones(N, dtype=torch.uint8, device="cuda") for N in {a.work.Nx for a in arr}}
+    stream = torch.cuda.Stream()
+    eng = tts.Engine(args.arena_mib << 20, min(args.serve_streams, tts.TTS_ENGINE_MAX_SLOTS),
+                     cluster_ctas=args.cluster, stream=stream)
+    flags = tts.TTS_DEVICE_PTRS | tts.TTS_FULL_FRAME
+    done_ev = torch.cuda.Event()
+    waiting = collections.deque(range(len(arr)))
+    active = {}                    # stream -> [slot, next frame]
+    lat, step_sizes, busy = [], [], 0.0
+    refused = 0
+    max_active = 0
+    frames_done = 0
+    first_last = {}
+    t0 = time.perf_counter()
+    while waiting or active:
+        now = time.perf_counter() - t0
+        while waiting and arr[waiting[0]].t_open <= now:
+            k = waiting[0]
+            w = arr[k].work
+            try:
+                slot = eng.admit(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, mm_iters=w.mm_iters,
+                                 central_lines=w.central_lines, init_seed=w.seed, stream_id=k)
+            except tts.TtsError as ex:
+                if ex.code != tts.TTS_EBUSY:
+                    raise
+                refused += 1
+                break
+            waiting.popleft()
+            active[k] = [slot, 0]
+        max_active = max(max_active, len(active))
+        ready = [k for k, (slot, j) in active.items() if arr[k].t_open + j / arr[k].fps <= now]
+        if not ready:
+            nxt = [arr[k].t_open + j / arr[k].fps for k, (slot, j) in active.items()]
+            if waiting:
+                nxt.append(arr[waiting[0]].t_open)
+            if nxt:
+                time.sleep(max(0.0, min(nxt) - (time.perf_counter() - t0)))
+            continue
+        n = len(ready)
+        c_slots = (ctypes.c_int * n)(*[active[k][0] for k in ready])
+        c_fr = (ctypes.c_void_p * n)(*[banks[(arr[k].work.Nx, arr[k].work.Ny)][active[k][1] % F].data_ptr()
+                                       for k in ready])
+        c_ms = (ctypes.c_void_p * n)(*[ones[arr[k].work.Nx].data_ptr() if active[k][1] < arr[k].work.warmup_frames
+                                       else 0 for k in ready])
+        c_rates = (ctypes.c_double * n)(*[arr[k].work.rate for k in ready])
+        c_seeds = (ctypes.c_uint64 * n)(*[arr[k].work.seed + 1000 for k in ready])
+        ts = time.perf_counter()
+        rc = lib.tts_engine_step(eng.e, n, c_slots, c_fr, c_ms, c_rates, c_seeds, flags)
+        if rc < 0:
+            raise tts.TtsError(rc, tts.tts_last_error())
+        done_ev.record(stream)
+        done_ev.synchronize()
+        te = time.perf_counter()
+        busy += te - ts
+        step_sizes.append(n)
+        for k in ready:
+            j = active[k][1]
+            lat.append((te - t0) - (arr[k].t_open + j / arr[k].fps))
+            active[k][1] = j + 1
+            frames_done += 1
+            if active[k][1] == arr[k].frames:
+                if len(first_last) < 4:
+                    w = arr[k].work
+                    img = np.zeros((w.Nx, w.Ny), np.complex64)
+                    tts.tts_engine_image(eng.e, active[k][0], img)
+                    first_last[k] = (img, eng.cluster_ctas(active[k][0]))
+                eng.release(active[k][0])
+                del active[k]
+    wall = time.perf_counter() - t0
+    info = eng.info()
+    eng.close()
+
+    # a few finished streams alone through their own handles: bit-identical images
+    same = True
+    for k, (img, C) in first_last.items():
+        w = arr[k].work
+        trk = tts.Tracker(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, mm_iters=w.mm_iters, central_lines=w.central_lines,
+                          init_seed=w.seed, stream_id=k, cluster_ctas=C)
+        mask = torch.zeros(w.Nx, dtype=torch.uint8, device="cuda")
+        ring = torch.empty((w.Nx, w.Ny), dtype=torch.complex64, device="cuda")
+        for j in range(arr[k].frames):
+            m = ones[w.Nx]
+            if j >= w.warmup_frames:
+                tts.tts_next_mask(trk.h, w.rate, w.seed + 1000, mask)
+                m = mask
+            tts.tts_push_frame(trk.h, banks[(w.Nx, w.Ny)][j % F], m, full_frame=True)
+        tts.tts_image(trk.h, arr[k].frames - 1, ring)
+        torch.cuda.synchronize()
+        same = same and bool(np.array_equal(ring.cpu().numpy().view(np.uint32), img.view(np.uint32)))
+        trk.close()
+    lat_ms = np.array(lat) * 1e3
+    return {
+        "metric": METRIC, "value": frames_done / wall, "unit": UNIT, "n_gpus": 1, "steps": len(step_sizes),
+        "warmup": 0, "ms_per_step": busy / max(1, len(step_sizes)) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 ridge solve)", "data": "synthetic",
+        "config": {"workload": "serving_poisson" if not args.preload else "serving_preloaded",
+                   "streams": len(arr), "arrival_rate_per_s": None if args.preload else args.serve_rate,
+                   "frames_per_stream": args.serve_frames, "fps_range": [20, 50],
+                   "sizes": sorted({a.work.Nx for a in arr}), "ranks": sorted({a.work.R for a in arr}),
+                   "rate": 0.125, "arena_mib": args.arena_mib, "cluster_ctas": info["cluster_ctas"],
+                   "frames": f"per-size bank of {F} phantom frames, cycled; device resident (scanner writes HBM)"},
+        "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                       "max": float(lat_ms.max()), "note": "frame arrival to the end of its engine step"},
+        "serving": {"wall_s": wall, "frames": frames_done, "max_concurrent": max_active,
+                    "mean_frames_per_step": float(np.mean(step_sizes)), "gpu_busy_frac": busy / wall,
+                    "admission_waits": refused, "alone_equals_mix_bitwise": same, "checked_streams": len(first_last)},
+        "engine": info,
+        "gpu_launches": 3 * len(step_sizes),
+    }
+
+
 def main():
     args = parse()
+    if args.serve:
+        print(json.dumps(run_serve(args)))
+        return
+    if args.batched:
+        print(json.dumps(run_batched(args)))
+        return
     if args.fft2d:
         print(json.dumps(run_fft2d(args)))
         return

@@ -126,6 +126,9 @@ int tts_get_stats(tts_handle* h, double* abar_A, double* abar_B, double* w, int6
 int tts_set_stats(tts_handle* h, double abar_A, double abar_B, double w, int64_t t);
 /* gamma_t of the most recent frame (R values, host). Waits. */
 int tts_get_gamma(tts_handle* h, tts_c64* gamma);
+/* The handle's configuration as it runs: cluster_ctas is the size the library chose (or
+ * the engine assigned), cuda_stream the stream its work is ordered on. */
+int tts_get_config(tts_handle* h, tts_config* cfg);
 
 /* Process frame t = (frames processed so far): y_rows holds the acquired k-space rows
  * (|S| x Ny, rows in increasing i) and line_mask the Nx-byte mask of S. line_mask NULL
@@ -266,29 +269,32 @@ typedef struct {
   size_t arena_largest_free;  /* largest stream footprint that admission can place now */
   int active;                 /* admitted streams */
   int max_slots;
-  int cluster_ctas;           /* CTAs per frame (one cluster) */
-  int resident_clusters;      /* clusters the persistent frame launch keeps on the GPU */
-  int owned_outputs;          /* per-thread outputs of the persistent frame kernel */
+  int cluster_ctas;           /* preferred CTAs per frame (one cluster) */
+  int groups;                 /* cluster sizes in use: one persistent frame launch each */
+  int resident_clusters;      /* clusters those launches can keep on the GPU at once, summed */
   int64_t steps;              /* tts_engine_step calls that launched work */
 } tts_engine_stats;
 
 /* Device bytes a stream with this configuration holds in an engine arena (the same
- * workspace a handle allocates); cfg->cluster_ctas 0 means 8, the engine default. */
+ * workspace a handle allocates) when it runs on clusters of cfg->cluster_ctas CTAs
+ * (0 = 4, the engine default); TTS_EINVAL if its layout does not fit that size. */
 int tts_stream_footprint(const tts_config* cfg, size_t* bytes);
 
 /* Create an engine on the current device. arena_bytes >= 4096; max_slots in
  * 1..TTS_ENGINE_MAX_SLOTS (at most that many streams at once); cluster_ctas in
- * {0 (= 8), 1, 2, 4, 8, 16}: CTAs of the cluster that runs one frame, the same for every
- * stream; flags 0 or TTS_ENGINE_GRAPH; cuda_stream NULL = a stream the engine creates.
- * TTS_ENOMEM if the arena or the parameter block cannot be allocated. */
+ * {0 (= 4), 1, 2, 4, 8, 16}: the preferred number of CTAs of the cluster that runs one
+ * frame (a stream whose layout does not fit takes the next larger size that fits;
+ * tts_get_config shows the size a stream got); flags 0 or TTS_ENGINE_GRAPH; cuda_stream
+ * NULL = a stream the engine creates. TTS_ENOMEM if the arena or the parameter block
+ * cannot be allocated. */
 int tts_engine_create(size_t arena_bytes, int max_slots, int cluster_ctas, int flags, void* cuda_stream,
                       tts_engine** out);
 /* Waits for the engine's work, then frees everything it owns, admitted streams included. */
 void tts_engine_destroy(tts_engine* e);
 
 /* Admission: create a tracker for cfg in a free slot whose footprint fits in the arena
- * (first fit). cfg->cluster_ctas, cfg->launch and cfg->cuda_stream are replaced by the
- * engine's. On success *slot is the stream's slot (0..max_slots-1). TTS_EBUSY when every
+ * (first fit). cfg->cluster_ctas is replaced by the engine's preferred size (or the next
+ * larger that fits the stream), cfg->launch and cfg->cuda_stream by the engine's. On success *slot is the stream's slot (0..max_slots-1). TTS_EBUSY when every
  * slot is taken or no free arena block is large enough; TTS_EINVAL for a bad cfg. Does
  * not wait for steps in flight. */
 int tts_engine_admit(tts_engine* e, const tts_config* cfg, int* slot);
@@ -321,6 +327,18 @@ int tts_engine_mask(tts_engine* e, int slot, uint8_t* out, int flags);
 /* Waits for the engine's stream; TTS_ENONFINITE (once) if any slot skipped a frame. */
 int tts_engine_synchronize(tts_engine* e);
 int tts_engine_info(tts_engine* e, tts_engine_stats* stats);
+
+/* Autotuner of the engine's cluster size for a mix of streams: for each candidate C in
+ * {1, 2, 4, 8, 16} that has a layout for every cfgs[k] (n configurations), builds a
+ * temporary engine with those streams, runs two untimed steps (the first fully sampled,
+ * then drawn masks) and `steps` timed steps on synthetic CN(0, 1) frames, and returns the
+ * C with the least time per step in *best_C. step_ms (optional, 5 doubles) receives the
+ * time per step of each candidate in that order, -1 where a candidate does not fit.
+ * Fewer, larger clusters give each frame lower latency; more, smaller clusters keep more
+ * frames on the GPU at once; which wins depends on the mix (streams that do not fit a
+ * candidate run at their next larger size that fits, as in an engine). Synchronous; allocates the
+ * temporary engines and frames on the current device and frees them before returning. */
+int tts_engine_autotune(const tts_config* cfgs, int n, int steps, int* best_C, double* step_ms);
 
 const char* tts_last_error(void);
 

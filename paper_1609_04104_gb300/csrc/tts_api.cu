@@ -337,6 +337,14 @@ int tts_get_gamma(tts_handle* h, tts_c64* gamma) {
   return TTS_OK;
 }
 
+int tts_get_config(tts_handle* h, tts_config* cfg) {
+  if (!h || !cfg) return fail(TTS_EINVAL, "NULL argument%s");
+  *cfg = h->cfg;
+  cfg->cluster_ctas = h->fp.C;
+  cfg->cuda_stream = (void*)h->stream;
+  return TTS_OK;
+}
+
 int tts_push_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line_mask, int flags) {
   if (!h || !y_rows) return fail(TTS_EINVAL, "NULL argument%s");
   FrameParams p;

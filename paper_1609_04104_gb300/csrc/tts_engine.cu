@@ -4,16 +4,19 @@
 // Every stream (a cine slice with its own Nx, Ny, R, lambda_forget, mu, K, rate) is a
 // tracker handle whose device state lives in one slot of a device arena that the engine
 // reserves once; admission asks the arena for the stream's footprint and is refused when
-// it has no room. One engine step takes one frame for each of a set of slots and runs
-//   (1) all their MM iterations in one persistent launch: clusters of C CTAs pull frames
-//       from a queue ordered largest first, each frame staying on one cluster;
+// it has no room. A stream runs its frames on a cluster of C CTAs: the engine's preferred
+// C when the stream's layout fits it, else the next larger size that fits. One engine step
+// takes one frame for each of a set of slots and runs
+//   (1) their MM iterations in one persistent launch per cluster size (launched on forked
+//       streams, so the groups overlap): clusters pull frames from a queue ordered
+//       largest first, each frame staying on one cluster;
 //   (2) all their images X_t = A diag(gamma) B^T in one launch over the union of tiles;
 //   (3) all their next-frame line draws in one launch, one CTA per stream;
-// with the parameters of the step in one block copied from pinned host memory. The four
+// with the parameters of the step in one block copied from pinned host memory. The
 // operations are captured once in a CUDA graph and replayed; the kernels read the step's
 // counts from the parameter block, so one graph serves any subset of the slots.
-// Each stream's arithmetic is exactly that of its handle run alone (same cluster size,
-// same chunking), so its results do not depend on what else is in the step.
+// Each stream's arithmetic is exactly that of its handle run alone with the same cluster
+// size, so its results do not depend on what else is in the step.
 #include <math.h>
 #include <string.h>
 
@@ -27,14 +30,19 @@ namespace {
 
 size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
 
+constexpr int kMaxGroups = 5;   // cluster sizes 1, 2, 4, 8, 16
+
 struct BlockHeader {
-  int queue;        // frame queue counter (0 at launch)
-  int n_frames;
+  int q[8][4];      // per group: queue counter (0 at launch), frames, offset of its blocks
   int n_samplers;
   int n_images;
-  int pad[60];
+  int pad[30];
 };
 static_assert(sizeof(BlockHeader) == 256, "parameter block header is 256 bytes");
+
+struct Group {
+  int C = 0, own = 0, smem = 0, clusters = 0;
+};
 
 #define ECK(call)                                               \
   do {                                                          \
@@ -67,10 +75,13 @@ struct tts_engine {
   cudaEvent_t done[2] = {nullptr, nullptr};
   bool pending[2] = {false, false};
   int cur = 0;
-  // launch shape of the persistent frame kernel
-  int own = 0, frame_smem = 0, frame_clusters = 0, image_grid = 0;
+  // one persistent frame launch per cluster size in use, on its own forked stream
+  std::vector<Group> groups;
+  cudaStream_t side[kMaxGroups] = {};
+  cudaEvent_t fork = nullptr, join[kMaxGroups] = {};
+  int image_grid = 0;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-  int graph_own[2] = {0, 0};
+  std::vector<Group> graph_groups[2];
   int64_t steps = 0;
 };
 
@@ -107,27 +118,69 @@ void arena_give(tts_engine* e, size_t off, size_t bytes) {
   }
 }
 
-// OWN of the persistent launch: the largest that any admitted slot needs.
-int refresh_shape(tts_engine* e) {
-  int own = 1;
-  for (tts_handle* h : e->slot)
-    if (h) own = std::max(own, frame_own(h->fp));
-  if (own == e->own && e->frame_clusters > 0) return TTS_OK;
-  int dyn = 0, clusters = 0;
-  const int rc = frame_batch_limits(own, e->C, &dyn, &clusters);
-  if (rc != TTS_OK) return tts_fail(rc, "cannot size the persistent frame launch%s");
-  e->own = own;
-  e->frame_smem = dyn;
-  e->frame_clusters = clusters;
+bool same_groups(const std::vector<Group>& a, const std::vector<Group>& b) {
+  if (a.size() != b.size()) return false;
+  for (size_t i = 0; i < a.size(); ++i)
+    if (a[i].C != b[i].C || a[i].own != b[i].own) return false;
+  return true;
+}
+
+// The cluster sizes in use and, per size, the largest per-thread output count (OWN) of
+// its streams and the launch limits.
+int refresh_groups(tts_engine* e) {
+  std::vector<Group> g;
+  for (tts_handle* h : e->slot) {
+    if (!h) continue;
+    const int C = h->fp.C, own = frame_own(h->fp);
+    bool found = false;
+    for (Group& x : g)
+      if (x.C == C) {
+        x.own = std::max(x.own, own);
+        found = true;
+      }
+    if (!found) {
+      Group x;
+      x.C = C;
+      x.own = own;
+      g.push_back(x);
+    }
+  }
+  std::sort(g.begin(), g.end(), [](const Group& a, const Group& b) { return a.C < b.C; });
+  for (Group& x : g) {
+    bool reuse = false;
+    for (const Group& o : e->groups)
+      if (o.C == x.C && o.own == x.own) {
+        x = o;
+        reuse = true;
+      }
+    if (reuse) continue;
+    const int rc = frame_batch_limits(x.own, x.C, &x.smem, &x.clusters);
+    if (rc != TTS_OK) return tts_fail(rc, "cannot size the persistent frame launch%s");
+  }
+  e->groups = g;
   return TTS_OK;
+}
+
+int group_index(const tts_engine* e, int C) {
+  for (size_t i = 0; i < e->groups.size(); ++i)
+    if (e->groups[i].C == C) return (int)i;
+  return -1;
 }
 
 int enqueue_step(tts_engine* e, int b) {
   char* d = e->d_block;
   BlockHeader* hd = (BlockHeader*)d;
   ECK(cudaMemcpyAsync(d, e->h_block[b], e->block_bytes, cudaMemcpyHostToDevice, e->stream));
-  int rc = launch_frame_batch(e->own, e->C, e->frame_clusters, e->frame_smem, (const FrameParams*)(d + e->off_frames),
-                              &hd->queue, e->stream);
+  ECK(cudaEventRecord(e->fork, e->stream));
+  int rc = TTS_OK;
+  for (size_t g = 0; g < e->groups.size() && rc == TTS_OK; ++g) {
+    const Group& x = e->groups[g];
+    ECK(cudaStreamWaitEvent(e->side[g], e->fork, 0));
+    rc = launch_frame_batch(x.own, x.C, std::min(x.clusters, e->max_slots), x.smem,
+                            (const FrameParams*)(d + e->off_frames), &hd->q[g][0], e->side[g]);
+    ECK(cudaEventRecord(e->join[g], e->side[g]));
+    ECK(cudaStreamWaitEvent(e->stream, e->join[g], 0));
+  }
   if (rc == TTS_OK)
     rc = launch_image_batch((const ImageJob*)(d + e->off_images), &hd->n_images, e->image_grid, e->stream);
   if (rc == TTS_OK)
@@ -153,8 +206,22 @@ int capture_step(tts_engine* e, int b) {
   const cudaError_t ie = cudaGraphInstantiate(&e->gexec[b], g, 0);
   cudaGraphDestroy(g);
   if (ie != cudaSuccess) return tts_cuda_fail(ie, "cudaGraphInstantiate");
-  e->graph_own[b] = e->own;
+  e->graph_groups[b] = e->groups;
   return TTS_OK;
+}
+
+// Footprint of a stream on the preferred cluster size, else on the next larger size that
+// holds its layout (0 if none does); the size in *C_out.
+size_t engine_footprint(tts_config c, int C_pref, int* C_out) {
+  for (int C = C_pref; C <= TTS_MAX_CLUSTER; C *= 2) {
+    c.cluster_ctas = C;
+    const size_t f = handle_footprint(c);
+    if (f) {
+      if (C_out) *C_out = C;
+      return f;
+    }
+  }
+  return 0;
 }
 
 double frame_cost(const FrameParams& p) {
@@ -171,9 +238,9 @@ int tts_stream_footprint(const tts_config* cfg, size_t* bytes) {
   const int rc = handle_check_config(cfg);
   if (rc) return rc;
   tts_config c = *cfg;
-  if (c.cluster_ctas == 0) c.cluster_ctas = 8;
+  if (c.cluster_ctas == 0) c.cluster_ctas = 4;
   const size_t b = handle_footprint(c);
-  if (!b) return tts_fail(TTS_EINVAL, "no cluster size fits the shared memory for these Nx, Ny, R%s");
+  if (!b) return tts_fail(TTS_EINVAL, "the stream's layout does not fit clusters of this size%s");
   *bytes = b;
   return TTS_OK;
 }
@@ -193,7 +260,7 @@ int tts_engine_create(size_t arena_bytes, int max_slots, int cluster_ctas, int f
     return tts_fail(TTS_ECUDA, "no CUDA device available (no CPU fallback)%s");
   tts_engine* e = new tts_engine();
   cudaGetDevice(&e->dev);
-  e->C = cluster_ctas ? cluster_ctas : 8;
+  e->C = cluster_ctas ? cluster_ctas : 4;
   e->max_slots = max_slots;
   e->use_graph = (flags & TTS_ENGINE_GRAPH) != 0;
   cudaDeviceGetAttribute(&e->sms, cudaDevAttrMultiProcessorCount, e->dev);
@@ -241,9 +308,15 @@ int tts_engine_create(size_t arena_bytes, int max_slots, int cluster_ctas, int f
     ce = cudaEventCreateWithFlags(&e->done[b], cudaEventDisableTiming);
     if (ce != cudaSuccess) return bail(tts_cuda_fail(ce, "cudaEventCreate"));
   }
+  for (int g = 0; g < kMaxGroups; ++g) {
+    ce = cudaStreamCreateWithFlags(&e->side[g], cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&e->join[g], cudaEventDisableTiming);
+    if (ce != cudaSuccess) return bail(tts_cuda_fail(ce, "engine streams"));
+  }
+  ce = cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming);
+  if (ce != cudaSuccess) return bail(tts_cuda_fail(ce, "cudaEventCreate"));
   // kernel attributes are set here, outside any capture
-  int rc = refresh_shape(e);
-  if (rc == TTS_OK) rc = launch_sampler_batch(nullptr, nullptr, 0, e->stream);
+  int rc = launch_sampler_batch(nullptr, nullptr, 0, e->stream);
   if (rc != TTS_OK) return bail(rc);
   *out = e;
   return TTS_OK;
@@ -259,6 +332,11 @@ void tts_engine_destroy(tts_engine* e) {
     if (e->done[b]) cudaEventDestroy(e->done[b]);
     if (e->h_block[b]) cudaFreeHost(e->h_block[b]);
   }
+  for (int g = 0; g < kMaxGroups; ++g) {
+    if (e->join[g]) cudaEventDestroy(e->join[g]);
+    if (e->side[g]) cudaStreamDestroy(e->side[g]);
+  }
+  if (e->fork) cudaEventDestroy(e->fork);
   if (e->d_block) cudaFree(e->d_block);
   if (e->arena) cudaFree(e->arena);
   if (e->admin) cudaStreamDestroy(e->admin);
@@ -270,13 +348,15 @@ int tts_engine_admit(tts_engine* e, const tts_config* cfg, int* slot_out) {
   if (!e || !cfg || !slot_out) return tts_fail(TTS_EINVAL, "NULL argument%s");
   *slot_out = -1;
   tts_config c = *cfg;
-  c.cluster_ctas = e->C;
   c.launch = TTS_LAUNCH_FUSED;
   c.cuda_stream = e->admin;
   int rc = handle_check_config(&c);
   if (rc) return rc;
-  const size_t need = handle_footprint(c);
-  if (!need) return tts_fail(TTS_EINVAL, "no layout of this stream fits the engine's cluster size%s");
+  // the preferred cluster size, else the next larger one that holds the stream's layout
+  int C = 0;
+  const size_t need = engine_footprint(c, e->C, &C);
+  if (!need) return tts_fail(TTS_EINVAL, "no cluster size holds this stream's layout%s");
+  c.cluster_ctas = C;
   int s = -1;
   for (int i = 0; i < e->max_slots; ++i)
     if (!e->slot[i]) {
@@ -299,7 +379,7 @@ int tts_engine_admit(tts_engine* e, const tts_config* cfg, int* slot_out) {
   e->slot_off[s] = off;
   e->slot_len[s] = need;
   e->active += 1;
-  rc = refresh_shape(e);
+  rc = refresh_groups(e);
   if (rc != TTS_OK) {
     e->slot[s] = nullptr;
     e->active -= 1;
@@ -320,7 +400,7 @@ int tts_engine_release(tts_engine* e, int slot) {
   e->slot[slot] = nullptr;
   arena_give(e, e->slot_off[slot], e->slot_len[slot]);
   e->active -= 1;
-  return refresh_shape(e);
+  return refresh_groups(e);
 }
 
 int tts_engine_handle(tts_engine* e, int slot, tts_handle** h) {
@@ -377,12 +457,21 @@ int tts_engine_step(tts_engine* e, int n, const int* slots, const tts_c64* const
     const int rc = handle_stage_frame(h, y_rows[i], m, flags, &staged[i]);
     if (rc != TTS_OK) return rc;
   }
-  // the queue hands out the largest frames first
+  // frames grouped by cluster size; each group's queue hands out its largest frames first
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int a, int c) { return frame_cost(staged[a]) > frame_cost(staged[c]); });
-  for (int k = 0; k < n; ++k) fps[k] = staged[order[k]];
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    if (staged[a].C != staged[c].C) return staged[a].C < staged[c].C;
+    return frame_cost(staged[a]) > frame_cost(staged[c]);
+  });
+  memset(hd->q, 0, sizeof(hd->q));
+  for (int k = 0; k < n; ++k) {
+    fps[k] = staged[order[k]];
+    const int g = group_index(e, fps[k].C);
+    if (g < 0) return tts_fail(TTS_ESTATE, "a stream's cluster size has no launch group%s");
+    if (hd->q[g][1] == 0) hd->q[g][2] = k;
+    hd->q[g][1] += 1;
+  }
   int tile0 = 0;
   for (int i = 0; i < n; ++i) {
     tts_handle* h = e->slot[slots[i]];
@@ -405,13 +494,11 @@ int tts_engine_step(tts_engine* e, int n, const int* slots, const tts_c64* const
     ij.tiles = ((c.Nx + 31) / 32) * ((c.Ny + 31) / 32);
     tile0 += ij.tiles;
   }
-  hd->queue = 0;
-  hd->n_frames = n;
   hd->n_samplers = n;
   hd->n_images = n;
   int rc = TTS_OK;
   if (e->use_graph) {
-    if (!e->gexec[b] || e->graph_own[b] != e->own) rc = capture_step(e, b);
+    if (!e->gexec[b] || !same_groups(e->graph_groups[b], e->groups)) rc = capture_step(e, b);
     if (rc == TTS_OK) {
       const cudaError_t ge = cudaGraphLaunch(e->gexec[b], e->stream);
       if (ge != cudaSuccess) rc = tts_cuda_fail(ge, "cudaGraphLaunch");
@@ -472,6 +559,97 @@ int tts_engine_synchronize(tts_engine* e) {
   return TTS_OK;
 }
 
+int tts_engine_autotune(const tts_config* cfgs, int n, int steps, int* best_C, double* step_ms) {
+  if (!cfgs || !best_C || n < 1 || n > TTS_ENGINE_MAX_SLOTS || steps < 1)
+    return tts_fail(TTS_EINVAL, "bad autotune arguments%s");
+  static const int kCand[5] = {1, 2, 4, 8, 16};
+  *best_C = 0;
+  double best = 0.0;
+  for (int ci = 0; ci < 5; ++ci) {
+    const int C = kCand[ci];
+    if (step_ms) step_ms[ci] = -1.0;
+    // every stream runs on this size or, as in an engine, the next larger that fits it;
+    // a candidate no stream can use is skipped
+    size_t arena = 64u << 20;
+    bool ok = true, used = false;
+    for (int k = 0; k < n && ok; ++k) {
+      tts_config c = cfgs[k];
+      if (handle_check_config(&c) != TTS_OK) return TTS_EINVAL;
+      int Ck = 0;
+      const size_t f = engine_footprint(c, C, &Ck);
+      if (!f) ok = false;
+      used = used || Ck == C;
+      arena += f;
+    }
+    if (!ok || !used) continue;
+    tts_engine* e = nullptr;
+    int rc = tts_engine_create(arena, n, C, TTS_ENGINE_GRAPH, nullptr, &e);
+    if (rc != TTS_OK) return rc;
+    std::vector<int> slots(n);
+    std::vector<const tts_c64*> frames(n);
+    std::vector<const uint8_t*> masks(n, nullptr);
+    std::vector<double> rates(n);
+    std::vector<uint64_t> seeds(n);
+    size_t fbytes = 0, mbytes = 0;
+    for (int k = 0; k < n; ++k) {
+      fbytes += up256(sizeof(float2) * (size_t)cfgs[k].Nx * cfgs[k].Ny);
+      mbytes += up256((size_t)cfgs[k].Nx);
+    }
+    char* dbuf = nullptr;
+    cudaError_t ce = cudaMalloc((void**)&dbuf, fbytes + mbytes);
+    if (ce != cudaSuccess) {
+      tts_engine_destroy(e);
+      return tts_fail(TTS_ENOMEM, "autotune frame buffers%s");
+    }
+    // synthetic fully sampled frames: CN(0, 1) samples from the factor initialiser
+    size_t fo = 0, mo = fbytes;
+    for (int k = 0; k < n && rc == TTS_OK; ++k) {
+      tts_config c = cfgs[k];
+      rc = tts_engine_admit(e, &c, &slots[k]);
+      if (rc != TTS_OK) break;
+      frames[k] = (const tts_c64*)(dbuf + fo);
+      masks[k] = (const uint8_t*)(dbuf + mo);
+      rc = launch_init_factors((float2*)(dbuf + fo), c.Nx, c.Ny, 0x7u + k, 3, e->stream);
+      if (cudaMemsetAsync(dbuf + mo, 1, c.Nx, e->stream) != cudaSuccess) rc = TTS_ECUDA;
+      fo += up256(sizeof(float2) * (size_t)c.Nx * c.Ny);
+      mo += up256((size_t)c.Nx);
+      rates[k] = 1.0 / 8.0;
+      seeds[k] = 1 + k;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == TTS_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = TTS_ECUDA;
+    float ms = 0.f;
+    if (rc == TTS_OK) {
+      // the first step is fully sampled and untimed (graph capture); later steps use the
+      // drawn masks
+      rc = tts_engine_step(e, n, slots.data(), frames.data(), masks.data(), rates.data(), seeds.data(),
+                           TTS_DEVICE_PTRS | TTS_FULL_FRAME);
+      if (rc == TTS_OK) rc = tts_engine_step(e, n, slots.data(), frames.data(), nullptr, rates.data(), seeds.data(),
+                                             TTS_DEVICE_PTRS | TTS_FULL_FRAME);
+      if (rc == TTS_OK && cudaEventRecord(e0, e->stream) != cudaSuccess) rc = TTS_ECUDA;
+      for (int s = 0; s < steps && rc == TTS_OK; ++s)
+        rc = tts_engine_step(e, n, slots.data(), frames.data(), nullptr, rates.data(), seeds.data(),
+                             TTS_DEVICE_PTRS | TTS_FULL_FRAME);
+      if (rc == TTS_OK && (cudaEventRecord(e1, e->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        rc = TTS_ECUDA;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    tts_engine_destroy(e);
+    cudaFree(dbuf);
+    if (rc != TTS_OK) return rc;
+    const double per = (double)ms / steps;
+    if (step_ms) step_ms[ci] = per;
+    if (*best_C == 0 || per < best) {
+      best = per;
+      *best_C = C;
+    }
+  }
+  if (*best_C == 0) return tts_fail(TTS_EINVAL, "no cluster size fits every stream%s");
+  return TTS_OK;
+}
+
 int tts_engine_info(tts_engine* e, tts_engine_stats* st) {
   if (!e || !st) return tts_fail(TTS_EINVAL, "NULL argument%s");
   size_t largest = 0;
@@ -482,8 +660,9 @@ int tts_engine_info(tts_engine* e, tts_engine_stats* st) {
   st->active = e->active;
   st->max_slots = e->max_slots;
   st->cluster_ctas = e->C;
-  st->resident_clusters = e->frame_clusters;
-  st->owned_outputs = e->own;
+  st->groups = (int)e->groups.size();
+  st->resident_clusters = 0;
+  for (const Group& g : e->groups) st->resident_clusters += g.clusters;
   st->steps = e->steps;
   return TTS_OK;
 }

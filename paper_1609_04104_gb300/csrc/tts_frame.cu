@@ -980,10 +980,10 @@ __global__ void __launch_bounds__(TTS_THREADS, 1) frame_kernel(FrameParams p, in
 }
 
 // Frames of many independent trackers (streams of any Nx, Ny, R) in one persistent
-// launch: each cluster takes the next frame from a queue of n parameter blocks, runs all
-// its steps, and takes another until the queue is empty. The queue counter
-// (queue_n[0]) is zero at launch; the number of frames is read from queue_n[1], so a
-// captured launch serves any batch up to its parameter capacity.
+// launch: each cluster takes the next frame from a queue of parameter blocks, runs all
+// its steps, and takes another until the queue is empty. queue_n = {counter (zero at
+// launch), number of frames, offset of the first block in ps}: read from device memory,
+// so a captured launch serves any batch up to its parameter capacity.
 template <int OWN>
 __global__ void __launch_bounds__(TTS_THREADS, 1) frame_batch_kernel(const FrameParams* __restrict__ ps,
                                                                      int* queue_n) {
@@ -993,6 +993,7 @@ __global__ void __launch_bounds__(TTS_THREADS, 1) frame_batch_kernel(const Frame
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int n = ((volatile int*)queue_n)[1];
+  ps += ((volatile int*)queue_n)[2];
   for (;;) {
     if (rank == 0 && threadIdx.x == 0) item = atomicAdd(queue_n, 1);
     cluster.sync();

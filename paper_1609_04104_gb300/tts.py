@@ -28,12 +28,12 @@ TTS_LAUNCH_FUSED, TTS_LAUNCH_PHASES = 0, 1
 
 EXPORTS = [
     "tts_config_init", "tts_create", "tts_create_ex", "tts_destroy", "tts_set_factors", "tts_get_factors",
-    "tts_get_stats", "tts_set_stats", "tts_get_gamma", "tts_push_frame", "tts_image", "tts_next_mask",
+    "tts_get_stats", "tts_set_stats", "tts_get_gamma", "tts_get_config", "tts_push_frame", "tts_image", "tts_next_mask",
     "tts_line_probs", "tts_sample_lines_from_probs", "tts_save", "tts_load", "tts_synchronize",
     "tts_launches_per_frame", "tts_ridge_solve", "tts_fft2d", "tts_push_frame_noalloc",
     "tts_stream_footprint", "tts_engine_create", "tts_engine_destroy", "tts_engine_admit", "tts_engine_release",
     "tts_engine_handle", "tts_engine_step", "tts_engine_image", "tts_engine_mask", "tts_engine_synchronize",
-    "tts_engine_info", "tts_last_error",
+    "tts_engine_info", "tts_engine_autotune", "tts_last_error",
 ]
 
 
@@ -68,7 +68,7 @@ class tts_engine_stats(ctypes.Structure):
     _fields_ = [
         ("arena_bytes", ctypes.c_size_t), ("arena_used", ctypes.c_size_t), ("arena_largest_free", ctypes.c_size_t),
         ("active", ctypes.c_int), ("max_slots", ctypes.c_int), ("cluster_ctas", ctypes.c_int),
-        ("resident_clusters", ctypes.c_int), ("owned_outputs", ctypes.c_int), ("steps", ctypes.c_int64),
+        ("groups", ctypes.c_int), ("resident_clusters", ctypes.c_int), ("steps", ctypes.c_int64),
     ]
 
 
@@ -98,6 +98,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
                               ctypes.POINTER(ctypes.c_int64)]),
         "tts_set_stats": (I, [H, D, D, D, ctypes.c_int64]),
         "tts_get_gamma": (I, [H, P]),
+        "tts_get_config": (I, [H, ctypes.POINTER(tts_config)]),
         "tts_push_frame": (I, [H, P, P, I]),
         "tts_image": (I, [H, ctypes.c_int64, P, I]),
         "tts_next_mask": (I, [H, D, U64, P, I]),
@@ -121,6 +122,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "tts_engine_mask": (I, [H, I, P, I]),
         "tts_engine_synchronize": (I, [H]),
         "tts_engine_info": (I, [H, ctypes.POINTER(tts_engine_stats)]),
+        "tts_engine_autotune": (I, [ctypes.POINTER(tts_config), I, I, ctypes.POINTER(I), P]),
         "tts_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -223,6 +225,12 @@ def tts_get_gamma(h, R) -> np.ndarray:
     g = np.zeros(R, np.complex64)
     _check(load().tts_get_gamma(h, g.ctypes.data))
     return g
+
+
+def tts_get_config(h) -> tts_config:
+    cfg = tts_config()
+    _check(load().tts_get_config(h, ctypes.byref(cfg)))
+    return cfg
 
 
 def tts_push_frame(h, y_rows, line_mask=None, full_frame=False) -> None:
@@ -398,6 +406,16 @@ def tts_engine_info(e) -> dict:
     return {k: getattr(st, k) for k, _ in tts_engine_stats._fields_}
 
 
+def tts_engine_autotune(cfgs, steps=5):
+    """(best cluster size, {C: ms per step or None}) for a list of tts_config."""
+    n = len(cfgs)
+    arr = (tts_config * n)(*cfgs)
+    best = ctypes.c_int(0)
+    ms = (ctypes.c_double * 5)()
+    _check(load().tts_engine_autotune(arr, n, steps, ctypes.byref(best), ms))
+    return best.value, {c: (ms[i] if ms[i] >= 0 else None) for i, c in enumerate((1, 2, 4, 8, 16))}
+
+
 class Engine:
     """Convenience owner of one engine (same calls as the C ABI)."""
 
@@ -440,6 +458,9 @@ class Engine:
             out = np.zeros(self.shapes[slot][0], np.uint8)
         tts_engine_mask(self.e, slot, out)
         return out
+
+    def cluster_ctas(self, slot) -> int:
+        return tts_get_config(tts_engine_handle(self.e, slot)).cluster_ctas
 
     def factors(self, slot):
         Nx, Ny, R = self.shapes[slot]

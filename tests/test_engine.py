@@ -16,8 +16,9 @@ pytestmark = pytest.mark.gpu
 
 # (Nx, Ny, R, K, rate): uneven sizes, ranks (small and large per-thread output counts),
 # iteration counts and rates in one mix
+# (384 x 384, R 48 does not fit clusters of 4 CTAs: it runs in a second launch group of 8)
 MIX = [(64, 64, 8, 5, 0.25), (96, 80, 16, 3, 1 / 6), (128, 128, 48, 3, 1 / 8), (80, 96, 32, 2, 0.25),
-       (48, 64, 4, 4, 0.25), (160, 128, 24, 3, 1 / 8)]
+       (48, 64, 4, 4, 0.25), (160, 128, 24, 3, 1 / 8), (384, 384, 48, 2, 1 / 8)]
 T = 7
 
 
@@ -37,9 +38,10 @@ def cfg_of(w, k):
     return dict(mm_iters=w.mm_iters, central_lines=w.central_lines, init_seed=w.seed, stream_id=k)
 
 
-def run_alone(tts, w, k, Y, frames):
-    """The stream alone through its own handle: push, image, next mask per frame."""
-    trk = tts.Tracker(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, cluster_ctas=8, **cfg_of(w, k))
+def run_alone(tts, w, k, Y, frames, C):
+    """The stream alone through its own handle (clusters of C CTAs): push, image, next
+    mask per frame."""
+    trk = tts.Tracker(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, cluster_ctas=C, **cfg_of(w, k))
     imgs, masks = [], []
     m = drawn = np.ones(w.Nx, np.uint8)
     for t in range(frames):
@@ -75,7 +77,7 @@ def schedule():
 def run_engine(tts, ws, Ys, graph=True, device_inputs=False):
     import torch
     eng = tts.Engine(1 << 30, 16, graph=graph)
-    slots, t_of = {}, {}
+    slots, t_of, cs = {}, {}, {}
     imgs = {k: [] for k in range(len(ws))}
     masks = {k: [] for k in range(len(ws))}
     drawn = {}
@@ -85,6 +87,7 @@ def run_engine(tts, ws, Ys, graph=True, device_inputs=False):
             if k not in slots:
                 w = ws[k]
                 slots[k] = eng.admit(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, **cfg_of(w, k))
+                cs[k] = eng.cluster_ctas(slots[k])
                 t_of[k] = 0
         if not part:
             continue
@@ -110,7 +113,8 @@ def run_engine(tts, ws, Ys, graph=True, device_inputs=False):
     facs = {k: eng.factors(slots[k]) for k in slots}
     info = eng.info()
     eng.close()
-    return ({k: np.array(v) for k, v in imgs.items()}, {k: np.array(v) for k, v in masks.items()}, facs, info)
+    return ({k: np.array(v) for k, v in imgs.items()}, {k: np.array(v) for k, v in masks.items()}, facs, info,
+            cs)
 
 
 @pytest.fixture(scope="module")
@@ -127,12 +131,14 @@ def engine_run(tts, mix):
 
 def test_engine_equals_alone(tts, mix, engine_run):
     ws, Ys = mix
-    imgs, masks, facs, info = engine_run
+    imgs, masks, facs, info, cs = engine_run
     assert info["active"] == len(MIX) - 1 and info["steps"] >= T
+    assert info["cluster_ctas"] == 4 and info["groups"] == 2
+    assert cs[6] == 8 and all(cs[k] == 4 for k in range(6))
     for k, w in enumerate(ws):
         n = len(imgs[k])
         assert n == (4 if k == 5 else T)
-        ai, am, A, B = run_alone(tts, w, k, Ys[k], n)
+        ai, am, A, B = run_alone(tts, w, k, Ys[k], n, cs[k])
         assert np.array_equal(imgs[k].view(np.uint32), ai.view(np.uint32)), f"stream {k}: images differ"
         assert np.array_equal(masks[k], am), f"stream {k}: drawn masks differ"
         if k in facs:
@@ -143,8 +149,8 @@ def test_engine_equals_alone(tts, mix, engine_run):
 
 def test_engine_graph_and_direct_launch_agree(tts, mix, engine_run):
     ws, Ys = mix
-    imgs, masks, _, _ = engine_run
-    imgs2, masks2, _, _ = run_engine(tts, ws, Ys, graph=False, device_inputs=True)
+    imgs, masks = engine_run[0], engine_run[1]
+    imgs2, masks2 = run_engine(tts, ws, Ys, graph=False, device_inputs=True)[:2]
     for k in range(len(ws)):
         assert np.array_equal(imgs[k].view(np.uint32), imgs2[k].view(np.uint32))
         assert np.array_equal(masks[k], masks2[k])
@@ -182,8 +188,9 @@ def test_engine_stream_matches_oracle(tts):
 def test_engine_admission_by_footprint(tts):
     cfg = tts.tts_config_init(256, 256, 32, 0.95, 1e-2, mm_iters=3)
     f = tts.tts_stream_footprint(cfg)
+    cfg4 = tts.tts_config_init(256, 256, 32, 0.95, 1e-2, mm_iters=3, cluster_ctas=4)
     cfg8 = tts.tts_config_init(256, 256, 32, 0.95, 1e-2, mm_iters=3, cluster_ctas=8)
-    assert f == tts.tts_stream_footprint(cfg8)
+    assert f == tts.tts_stream_footprint(cfg4) < tts.tts_stream_footprint(cfg8)   # partial sums per CTA
     assert f >= 8 * 256 * 256 * 3   # frame staging, Yt and image planes at least
     eng = tts.Engine(2 * f + 65536, 8)
     a = eng.admit(256, 256, 32, 0.95, 1e-2, mm_iters=3)
@@ -247,3 +254,14 @@ def test_engine_errors_leave_streams_unchanged(tts):
         assert eng.mask(s).sum() == (16 if Nx == 32 else 24)
     eng.synchronize()
     eng.close()
+
+
+def test_engine_autotune(tts):
+    cfgs = [tts.tts_config_init(Nx, Ny, R, 0.95, 1e-2, mm_iters=3, stream_id=k)
+            for k, (Nx, Ny, R) in enumerate([(128, 128, 16), (192, 160, 32), (256, 256, 48), (320, 320, 48)] * 4)]
+    best, ms = tts.tts_engine_autotune(cfgs, steps=3)
+    assert best in (1, 2, 4, 8, 16) and ms[best] is not None
+    timed = {c: v for c, v in ms.items() if v is not None}
+    assert ms[best] == min(timed.values()) and len(timed) >= 3
+    with pytest.raises(tts.TtsError):
+        tts.tts_engine_autotune([], steps=1)
