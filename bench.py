@@ -34,8 +34,8 @@ UNIT = "frames/s"
 # DRAM traffic of one fused frame_kernel launch on an informative cine-256 frame (|S| = 32),
 # dram__bytes_read.sum + dram__bytes_write.sum from the ncu capture summarised in
 # profiles/frame_kernel_cine256.md, valid only for the kernel source with this hash.
-FRAME_TRAFFIC_BYTES = 410624
-FRAME_TRAFFIC_SRC_SHA = "73b3d8a927cb1c42"
+FRAME_TRAFFIC_BYTES = 420096
+FRAME_TRAFFIC_SRC_SHA = "b8946b617e17bc05"
 
 
 def frame_traffic():

@@ -77,6 +77,7 @@ struct tts_engine {
   int cur = 0;
   // one persistent frame launch per cluster size in use, on its own forked stream
   std::vector<Group> groups;
+  Group limits[4][kMaxGroups];     // launch limits per (OWN 1/2/4/8, C 1/2/4/8/16), at creation
   cudaStream_t side[kMaxGroups] = {};
   cudaEvent_t fork = nullptr, join[kMaxGroups] = {};
   int image_grid = 0;
@@ -147,17 +148,27 @@ int refresh_groups(tts_engine* e) {
   }
   std::sort(g.begin(), g.end(), [](const Group& a, const Group& b) { return a.C < b.C; });
   for (Group& x : g) {
-    bool reuse = false;
-    for (const Group& o : e->groups)
-      if (o.C == x.C && o.own == x.own) {
-        x = o;
-        reuse = true;
-      }
-    if (reuse) continue;
-    const int rc = frame_batch_limits(x.own, x.C, &x.smem, &x.clusters);
-    if (rc != TTS_OK) return tts_fail(rc, "cannot size the persistent frame launch%s");
+    const Group& l = e->limits[x.own == 1 ? 0 : x.own == 2 ? 1 : x.own == 4 ? 2 : 3][__builtin_ctz(x.C)];
+    if (l.clusters <= 0) return tts_fail(TTS_ECUDA, "no launch limits for this cluster size%s");
+    x = l;
   }
   e->groups = g;
+  return TTS_OK;
+}
+
+// Launch limits of every kernel variant a stream may need, computed (and the variants
+// loaded) once, so that admitting a stream never waits on module loading.
+int prepare_limits(tts_engine* e) {
+  static const int owns[4] = {1, 2, 4, 8};
+  for (int oi = 0; oi < 4; ++oi)
+    for (int ci = 0; ci < kMaxGroups; ++ci) {
+      Group& l = e->limits[oi][ci];
+      l.C = 1 << ci;
+      l.own = owns[oi];
+      if (l.C < e->C) continue;
+      const int rc = frame_batch_limits(l.own, l.C, &l.smem, &l.clusters);
+      if (rc != TTS_OK) return tts_fail(rc, "cannot size the persistent frame launch%s");
+    }
   return TTS_OK;
 }
 
@@ -317,6 +328,8 @@ int tts_engine_create(size_t arena_bytes, int max_slots, int cluster_ctas, int f
   if (ce != cudaSuccess) return bail(tts_cuda_fail(ce, "cudaEventCreate"));
   // kernel attributes are set here, outside any capture
   int rc = launch_sampler_batch(nullptr, nullptr, 0, e->stream);
+  if (rc == TTS_OK) rc = launch_image_batch(nullptr, nullptr, 0, e->stream);
+  if (rc == TTS_OK) rc = prepare_limits(e);
   if (rc != TTS_OK) return bail(rc);
   *out = e;
   return TTS_OK;

@@ -478,9 +478,13 @@ size_t sampler_smem(int Nx, int fft_cols) {
          sizeof(float2) * fsz(TTS_MAX_N) + sizeof(float2) * 2 * fft_cols * (fsz(Nx) | 1) + 64;
 }
 
+// grid 0 only loads the kernel (done before any capture).
 int launch_image_batch(const ImageJob* jobs, const int* n, int grid, cudaStream_t st) {
   const int smem = 2 * 32 * (TTS_MAX_R + 1) * (int)sizeof(float2);
-  if (grid <= 0) return TTS_OK;
+  if (grid <= 0) {
+    cudaFuncAttributes fa;
+    return cudaFuncGetAttributes(&fa, image_batch_kernel) == cudaSuccess ? TTS_OK : TTS_ECUDA;
+  }
   image_batch_kernel<<<grid, 256, smem, st>>>(jobs, n);
   return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
 }
