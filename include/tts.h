@@ -202,6 +202,22 @@ int tts_ridge_solve(const double* G, const double* h, int R, double* gamma);
  * in {2, 3, 5}. Asynchronous. */
 int tts_fft2d(const tts_c64* in, tts_c64* out, int batch, int Nx, int Ny, int inverse, void* cuda_stream);
 
+/* The same unitary 2D DFT as dense complex matrix products on the tensor cores (tcgen05,
+ * BF16 operands, FP32 accumulation): the paper writes the 2D transform as F_Nx X F_Ny
+ * (§IV); here each of the two products multiplies the interleaved real rows by the real
+ * 2N x 2N embedding of the DFT matrix. precision TTS_DFT_BF16X3 splits both operands into
+ * bf16 hi + lo parts and accumulates hi*hi + hi*lo + lo*hi (relative error ~1e-5, within
+ * the 1e-4 image bound); TTS_DFT_BF16 uses hi*hi only (~4e-3: plain BF16 does not meet the
+ * bound). in, out, tmp: device, batch x Nx x Ny complex64, row-major; tmp (same size) holds
+ * the intermediate transposes and must not alias in or out (in == out is allowed). Nx, Ny
+ * multiples of 32 in [32, 256]. dev_status: NULL, or a device int the kernel sets to 1 if
+ * one of its bounded waits ran out (the results are then invalid). Asynchronous on
+ * cuda_stream (NULL = default stream). */
+#define TTS_DFT_BF16X3 0
+#define TTS_DFT_BF16 1
+int tts_dft2d_gemm(const tts_c64* in, tts_c64* out, tts_c64* tmp, int batch, int Nx, int Ny, int inverse,
+                   int precision, int* dev_status, void* cuda_stream);
+
 /* ---- Frame update without allocation ------------------------------------------------
  * The paper has no counterpart of this call; it serves callers that cannot allocate
  * device memory while they run: code whose device memory is handed out by an allocator

@@ -593,4 +593,35 @@ int tts_fft2d(const tts_c64* in, tts_c64* out, int batch, int Nx, int Ny, int in
   return rc == TTS_OK ? TTS_OK : fail(rc, "fft kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
 }
 
+namespace {
+std::mutex g_status_mu;
+int* g_status[64];
+}  // namespace
+
+int tts_dft2d_gemm(const tts_c64* in, tts_c64* out, tts_c64* tmp, int batch, int Nx, int Ny, int inverse,
+                   int precision, int* dev_status, void* cuda_stream) {
+  if (!in || !out || !tmp) return fail(TTS_EINVAL, "NULL argument%s");
+  if (batch < 0 || !dft_gemm_size_ok(Nx) || !dft_gemm_size_ok(Ny))
+    return fail(TTS_EINVAL, "sizes must be multiples of 32 in [32, 256]%s");
+  if (precision != TTS_DFT_BF16X3 && precision != TTS_DFT_BF16) return fail(TTS_EINVAL, "unknown precision%s");
+  if ((const void*)tmp == (const void*)in || (const void*)tmp == (const void*)out)
+    return fail(TTS_EINVAL, "tmp must not alias in or out%s");
+  if (batch == 0) return TTS_OK;
+  int* st = dev_status;
+  if (!st) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return fail(TTS_ECUDA, "device ordinal out of range%s");
+    std::lock_guard<std::mutex> lk(g_status_mu);
+    if (!g_status[dev]) {
+      CK(cudaMalloc(&g_status[dev], sizeof(int)));
+      CK(cudaMemset(g_status[dev], 0, sizeof(int)));
+    }
+    st = g_status[dev];
+  }
+  const int rc = launch_dft2d_gemm((const float2*)in, (float2*)out, (float2*)tmp, batch, Nx, Ny, inverse,
+                                   precision == TTS_DFT_BF16X3 ? 1 : 0, st, (cudaStream_t)cuda_stream);
+  return rc == TTS_OK ? TTS_OK : fail(rc, "tensor-core DFT launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+}
+
 }  // extern "C"

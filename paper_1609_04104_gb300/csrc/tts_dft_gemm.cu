@@ -1,0 +1,381 @@
+// The unitary 2D DFT as dense complex matrix products on the 5th-generation tensor cores
+// (tcgen05), the "DFT as F_l X F_r" form of the paper's 2D transform (§IV: F(X) =
+// F_Nx X F_Ny), in BF16 with FP32 accumulation, optionally with hi + lo split operands.
+//
+// One pass multiplies every length-N row of a batch by the DFT matrix and writes the
+// result transposed per image; two passes (rows, then the rows of the transpose) give
+// F_Nx X F_Ny. A complex row x (N values) times W (N x N) is the real product of the
+// interleaved row [Re x0, Im x0, Re x1, ...] (K' = 2N) with the 2N x 2N real embedding
+//   Bt[2j][2k] = Re W_kj, Bt[2j][2k+1] = -Im W_kj, Bt[2j+1][2k] = Im W_kj, Bt[2j+1][2k+1] = Re W_kj,
+// whose output row is again interleaved (N' = 2N). Split precision writes each operand as
+// hi + lo with hi = bf16(v), lo = bf16(v - hi) and accumulates hi*hi + hi*lo + lo*hi in FP32
+// (the lo*lo term, ~2^-16 relative, is dropped); plain precision uses hi*hi only.
+//
+// Kernel: one CTA of 128 threads per 128 rows. K' is consumed in chunks of 32 through two
+// shared-memory stages: the threads load the fp32 rows (coalesced), split them to bf16 and
+// store them in the canonical K-major no-swizzle layout (8 x 16-byte core matrices, 128 B
+// each); the DFT-matrix chunk, pre-arranged in that layout in global memory, arrives by one
+// bulk copy per operand on an mbarrier. One thread issues the tcgen05.mma instructions
+// (M = 128, N' up to 256 per accumulator, two accumulators for N' = 2N > 256, K = 16 each)
+// into tensor memory and commits them to the stage's mbarrier, which frees the stage for
+// the chunk after next. The epilogue reads the accumulators with tcgen05.ld (warp w owns
+// TMEM lanes 32w..32w+31 = rows) and writes complex outputs transposed, 256 contiguous
+// bytes per warp and output column. Every mbarrier wait is bounded; on timeout the CTA
+// records an error and stops issuing work.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "tts_internal.cuh"
+
+namespace {
+
+constexpr int kRows = 128;     // rows per CTA (UMMA M)
+constexpr int kKC = 32;        // K' chunk (bf16 elements) per stage
+constexpr int kThreads = 128;
+constexpr int kStages = 2;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading-dimension byte offset
+// (between core matrices along K) and stride byte offset (between 8-row groups), all >> 4;
+// bit 46 = descriptor version 1; no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N and M.
+__host__ __device__ __forceinline__ uint32_t instr_desc(int n, int m) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after ~1 s of SM clock.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try(a, parity))
+    if (clock64() - t0 > 2000000000LL) return false;
+  return true;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void umma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct GemmArgs {
+  const float2* x;        // rows of length N (complex), M rows in all
+  float2* out;            // transposed per image: out[b][j][i]
+  const uint4* bhi;       // DFT embedding, pre-arranged chunks (see dft_embedding)
+  const uint4* blo;
+  int M;                  // rows in all (batch * rows per image)
+  int rows;               // rows per image
+  int N;                  // row length (complex), K' = N' = 2N
+  int nh;                 // accumulators (1, or 2 when 2N > 256)
+  int split;              // 1: hi*hi + hi*lo + lo*hi; 0: hi*hi
+  int* err;               // set to 1 when a wait ran out
+};
+
+// Shared memory of one CTA (bytes): per stage A_hi, A_lo (128 x 32 bf16 = 8 KB each) and
+// B_hi, B_lo (N' x 32 bf16 each); then the mbarriers and the TMEM address slot.
+__host__ __device__ inline int stage_bytes(int N) { return 2 * (kRows * kKC * 2) + 2 * (2 * N * kKC * 2); }
+
+__global__ void __launch_bounds__(kThreads, 1) dft_gemm_kernel(GemmArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int N = g.N, Np = 2 * N, NT = Np / g.nh;
+  const int SB = stage_bytes(N);
+  uint64_t* bars = (uint64_t*)(smem + kStages * SB);   // full[2], empty[2], done
+  uint32_t* slot = (uint32_t*)(bars + 8);
+  __shared__ int abort_flag;
+  const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[2]), done = smem_u32(&bars[4]);
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  const uint32_t ncols = g.nh == 1 ? 256u : 512u;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *slot;
+
+  const int m0 = blockIdx.x * kRows;
+  const int nK = Np / kKC;
+  const uint32_t idesc = instr_desc(NT, kRows);
+  const size_t bchunk = (size_t)Np * kKC * 2;   // bytes of one K' chunk of the embedding (all N')
+  bool ok = true;
+  for (int kc = 0; kc < nK; ++kc) {
+    const int s = kc & 1, use = kc >> 1;
+    unsigned char* st = smem + s * SB;
+    unsigned char* ahi = st;
+    unsigned char* alo = st + kRows * kKC * 2;
+    unsigned char* bhi = st + 2 * kRows * kKC * 2;
+    unsigned char* blo = bhi + Np * kKC * 2;
+    if (kc >= kStages && ok) ok = mbar_wait(empty0 + 8 * s, (use - 1) & 1);
+    if (!ok) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) break;
+    if (tid == 0) {
+      mbar_expect_tx(full0 + 8 * s, (uint32_t)(g.split ? 2 * bchunk : bchunk));
+      bulk_g2s(smem_u32(bhi), (const char*)g.bhi + kc * bchunk, (uint32_t)bchunk, full0 + 8 * s);
+      if (g.split) bulk_g2s(smem_u32(blo), (const char*)g.blo + kc * bchunk, (uint32_t)bchunk, full0 + 8 * s);
+    }
+    // A chunk: 128 rows x 32 floats (16 complex), 8 threads per row, float4 each
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = tid + kThreads * u;
+      const int r = idx >> 3, q = idx & 7;
+      const int m = m0 + r;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m < g.M) v = *(const float4*)((const float*)(g.x + (size_t)m * N) + kc * kKC + 4 * q);
+      const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+      // byte offset: 8-row group (r / 8) x 512, core matrix along K (q / 2) x 128, row (r % 8) x 16, half (q % 2) x 8
+      const int off = (r >> 3) * 512 + (q >> 1) * 128 + (r & 7) * 16 + (q & 1) * 8;
+      uint2 hv;
+      hv.x = *(const uint32_t*)&h01;
+      hv.y = *(const uint32_t*)&h23;
+      *(uint2*)(ahi + off) = hv;
+      if (g.split) {
+        const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+        const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
+        const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+        uint2 lv;
+        lv.x = *(const uint32_t*)&l01;
+        lv.y = *(const uint32_t*)&l23;
+        *(uint2*)(alo + off) = lv;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      if (!mbar_wait(full0 + 8 * s, use & 1)) {
+        abort_flag = 1;
+      } else {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a_hi = smem_u32(ahi), a_lo = smem_u32(alo);
+        const uint32_t b_hi = smem_u32(bhi), b_lo = smem_u32(blo);
+#pragma unroll
+        for (int ks = 0; ks < kKC / 16; ++ks) {
+          const uint64_t dah = smem_desc(a_hi + ks * 256, 128, 512);
+          const uint64_t dal = smem_desc(a_lo + ks * 256, 128, 512);
+          for (int h = 0; h < g.nh; ++h) {
+            const uint32_t boff = h * NT * kKC * 2 + ks * 256;
+            const uint64_t dbh = smem_desc(b_hi + boff, 128, 512);
+            const uint32_t d = tmem + h * 256;
+            umma(d, dah, dbh, idesc, (kc | ks) != 0);
+            if (g.split) {
+              const uint64_t dbl = smem_desc(b_lo + boff, 128, 512);
+              umma(d, dah, dbl, idesc, 1);
+              umma(d, dal, dbh, idesc, 1);
+            }
+          }
+        }
+        umma_commit(empty0 + 8 * s);
+      }
+    }
+  }
+  if (tid == 0) umma_commit(done);   // arrives once every MMA issued above has completed
+  const bool fin = mbar_wait(done, 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (abort_flag || !fin) {
+    if (tid == 0) atomicExch(g.err, 1);
+  } else {
+    // epilogue: warp w reads TMEM lanes 32w.. (rows), 32 fp32 columns per load
+    const int r = warp * 32 + lane;
+    const int m = m0 + r;
+    const int b = m / g.rows, i = m - b * g.rows;
+    float2* ob = g.out + (size_t)b * N * g.rows;
+    for (int h = 0; h < g.nh; ++h) {
+      for (int c0 = 0; c0 < NT; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + h * 256 + c0, v);
+        if (m < g.M) {
+          const int j0 = (h * NT + c0) >> 1;
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj)
+            ob[(size_t)(j0 + jj) * g.rows + i] = make_float2(__uint_as_float(v[2 * jj]), __uint_as_float(v[2 * jj + 1]));
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// ---- DFT-matrix embeddings, per (N, direction), cached on each device ---------------------
+struct Embedding {
+  int dev, N, inverse;
+  uint4* hi;
+  uint4* lo;
+};
+std::mutex g_mu;
+std::vector<Embedding> g_emb;
+
+uint16_t bf16_bits(float f) {
+  // round to nearest even (finite inputs)
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  const uint32_t r = ((u >> 16) & 1u) + 0x7FFFu;
+  return (uint16_t)((u + r) >> 16);
+}
+float bf16_float(uint16_t b) {
+  const uint32_t u = (uint32_t)b << 16;
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+}
+
+// The real 2N x 2N embedding of W = N^{-1/2} exp(-+2 pi i jk / N), as rows c (output,
+// N' = 2N) and columns k' (input, K' = 2N), laid out chunk by chunk (32 columns k') in the
+// canonical K-major no-swizzle layout: byte (c / 8) * 512 + (k'_in_chunk / 8) * 128 +
+// (c % 8) * 16 + (k'_in_chunk % 8) * 2 within the chunk.
+int embedding(int N, int inverse, const uint4** hi, const uint4** lo) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto& e : g_emb)
+    if (e.dev == dev && e.N == N && e.inverse == inverse) {
+      *hi = e.hi;
+      *lo = e.lo;
+      return TTS_OK;
+    }
+  const int Np = 2 * N, nK = Np / kKC;
+  const size_t chunk = (size_t)Np * kKC;   // bf16 elements per chunk
+  std::vector<uint16_t> H(chunk * nK), L(chunk * nK);
+  const double sc = 1.0 / sqrt((double)N), sgn = inverse ? 1.0 : -1.0;
+  for (int c = 0; c < Np; ++c) {
+    const int j = c >> 1;
+    for (int kp = 0; kp < Np; ++kp) {
+      const int k = kp >> 1;
+      const double ang = sgn * 2.0 * M_PI * (double)(((long long)j * k) % N) / (double)N;
+      const double wr = sc * cos(ang), wi = sc * sin(ang);
+      double v;
+      if ((c & 1) == 0) v = (kp & 1) == 0 ? wr : -wi;
+      else v = (kp & 1) == 0 ? wi : wr;
+      const float f = (float)v;
+      const uint16_t h = bf16_bits(f);
+      const uint16_t l = bf16_bits(f - bf16_float(h));
+      const int kc = kp / kKC, kk = kp % kKC;
+      const size_t idx = (size_t)kc * chunk + (size_t)(c >> 3) * 256 + (kk >> 3) * 64 + (c & 7) * 8 + (kk & 7);
+      H[idx] = h;
+      L[idx] = l;
+    }
+  }
+  uint4* dh = nullptr;
+  uint4* dl = nullptr;
+  const size_t bytes = H.size() * 2;
+  if (cudaMalloc(&dh, bytes) != cudaSuccess) return TTS_ENOMEM;
+  if (cudaMalloc(&dl, bytes) != cudaSuccess) {
+    cudaFree(dh);
+    return TTS_ENOMEM;
+  }
+  if (cudaMemcpy(dh, H.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dl, L.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(dh);
+    cudaFree(dl);
+    return TTS_ECUDA;
+  }
+  g_emb.push_back({dev, N, inverse, dh, dl});
+  *hi = dh;
+  *lo = dl;
+  return TTS_OK;
+}
+
+int launch_pass(const float2* x, float2* out, int batch, int rows, int N, int inverse, int split, int* err,
+                cudaStream_t st) {
+  const uint4 *hi = nullptr, *lo = nullptr;
+  int rc = embedding(N, inverse, &hi, &lo);
+  if (rc != TTS_OK) return rc;
+  GemmArgs a;
+  a.x = x;
+  a.out = out;
+  a.bhi = hi;
+  a.blo = lo;
+  a.M = batch * rows;
+  a.rows = rows;
+  a.N = N;
+  a.nh = 2 * N > 256 ? 2 : 1;
+  a.split = split;
+  a.err = err;
+  // TMEM holds 512 columns per SM: ask for enough shared memory that the CTAs resident on
+  // one SM never need more (two CTAs of 256 columns, or one of 512), so an allocation never
+  // waits on a CTA that cannot finish
+  const int smem = std::max(kStages * stage_bytes(N) + 128, a.nh == 1 ? 80 * 1024 : 120 * 1024);
+  if (cudaFuncSetAttribute(dft_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return TTS_ECUDA;
+  const int grid = (a.M + kRows - 1) / kRows;
+  dft_gemm_kernel<<<grid, kThreads, smem, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
+}
+
+}  // namespace
+
+// Sizes the tensor-core form supports: N a multiple of 32 in [32, 256] (K' chunks of 32,
+// at most two accumulators of 256 columns).
+bool dft_gemm_size_ok(int N) { return N >= 32 && N <= 256 && N % 32 == 0; }
+
+int launch_dft2d_gemm(const float2* in, float2* out, float2* tmp, int batch, int Nx, int Ny, int inverse,
+                      int split, int* err, cudaStream_t st) {
+  // rows of each image (length Ny) -> tmp holds the transposes (Ny x Nx); then the rows of
+  // the transposes (length Nx) -> out holds F_Nx X F_Ny (Nx x Ny)
+  int rc = launch_pass(in, tmp, batch, Nx, Ny, inverse, split, err, st);
+  if (rc == TTS_OK) rc = launch_pass(tmp, out, batch, Ny, Nx, inverse, split, err, st);
+  return rc;
+}

@@ -432,4 +432,8 @@ void tts_internal_set_error(const char* msg);   // message returned by tts_last_
 int launch_fft2d(const float2* in, float2* out, int batch, int Nx, int Ny, int inverse, const float2* Wx,
                  const float2* Wy, float2* scratch, cudaStream_t st);
 int launch_ridge(const double2* G, const double2* h, int R, double2* gamma, cudaStream_t st);
+// 2D DFT as tensor-core matrix products (tts_dft_gemm.cu)
+bool dft_gemm_size_ok(int N);
+int launch_dft2d_gemm(const float2* in, float2* out, float2* tmp, int batch, int Nx, int Ny, int inverse,
+                      int split, int* err, cudaStream_t st);
 int launch_init_factors(float2* A, int N, int R, uint64_t seed, uint32_t which, cudaStream_t st);

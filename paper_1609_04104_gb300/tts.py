@@ -20,6 +20,7 @@ TTS_EINVAL, TTS_ENOMEM, TTS_ECUDA, TTS_ERANGE, TTS_ENONFINITE, TTS_ETIMEOUT, TTS
 TTS_EBUSY = -8
 TTS_ENGINE_GRAPH = 1
 TTS_ENGINE_MAX_SLOTS = 4096
+TTS_DFT_BF16X3, TTS_DFT_BF16 = 0, 1
 TTS_DEVICE_PTRS = 1
 TTS_FULL_FRAME = 2
 TTS_POLICY_UNIFORM, TTS_POLICY_VARDENS, TTS_POLICY_INFORMATIVE = 0, 1, 2
@@ -33,7 +34,7 @@ EXPORTS = [
     "tts_launches_per_frame", "tts_ridge_solve", "tts_fft2d", "tts_push_frame_noalloc",
     "tts_stream_footprint", "tts_engine_create", "tts_engine_destroy", "tts_engine_admit", "tts_engine_release",
     "tts_engine_handle", "tts_engine_step", "tts_engine_image", "tts_engine_mask", "tts_engine_synchronize",
-    "tts_engine_info", "tts_engine_autotune", "tts_last_error",
+    "tts_engine_info", "tts_engine_autotune", "tts_dft2d_gemm", "tts_last_error",
 ]
 
 
@@ -111,6 +112,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "tts_ridge_solve": (I, [P, P, I, P]),
         "tts_fft2d": (I, [P, P, I, I, I, I, P]),
         "tts_push_frame_noalloc": (I, [ctypes.POINTER(tts_frame_args), P]),
+        "tts_dft2d_gemm": (I, [P, P, P, I, I, I, I, I, P, P]),
         "tts_stream_footprint": (I, [ctypes.POINTER(tts_config), ctypes.POINTER(ctypes.c_size_t)]),
         "tts_engine_create": (I, [ctypes.c_size_t, I, I, I, P, ctypes.POINTER(H)]),
         "tts_engine_destroy": (None, [H]),
@@ -303,6 +305,18 @@ def tts_fft2d(x, out, inverse=False, stream=None) -> None:
         batch, Nx, Ny = x.shape
     s = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(load().tts_fft2d(x.data_ptr(), out.data_ptr(), batch, Nx, Ny, int(inverse), s))
+
+
+def tts_dft2d_gemm(x, out, tmp, inverse=False, precision=TTS_DFT_BF16X3, status=None, stream=None) -> None:
+    """Unitary 2D DFT of torch CUDA tensors (batch, Nx, Ny) complex64 on the tensor cores."""
+    if x.dim() == 2:
+        batch, (Nx, Ny) = 1, x.shape
+    else:
+        batch, Nx, Ny = x.shape
+    s = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    st = None if status is None else status.data_ptr()
+    _check(load().tts_dft2d_gemm(x.data_ptr(), out.data_ptr(), tmp.data_ptr(), batch, Nx, Ny, int(inverse),
+                                 precision, st, s))
 
 
 def tts_push_frame_noalloc(A, B, stats, gamma, y_rows, line_mask, lambda_forget, mu, mm_iters=1,

@@ -1,0 +1,71 @@
+"""The unitary 2D DFT as tensor-core matrix products (tts_dft2d_gemm), BF16 hi + lo split and
+plain BF16, against the FP64 oracle's DFT: the split form meets the 1e-4 image bound, plain
+BF16 does not (its error is ~2^-8 relative)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import tracker as O
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(64, 64, 2), (128, 128, 2), (192, 192, 2), (256, 256, 2), (96, 160, 3), (32, 224, 5)]
+
+
+def rand_images(b, Nx, Ny, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal((b, Nx, Ny)) + 1j * rng.standard_normal((b, Nx, Ny))).astype(np.complex64)
+
+
+def run(tts, X, inverse, precision, inplace=False):
+    import torch
+    x = torch.from_numpy(X).cuda()
+    out = x if inplace else torch.empty_like(x)
+    tmp = torch.empty_like(x)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    tts.tts_dft2d_gemm(x, out, tmp, inverse=inverse, precision=precision, status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    return out.cpu().numpy()
+
+
+def reference(X, inverse):
+    f = O.ifft2 if inverse else O.fft2
+    return np.stack([f(X[b].astype(np.complex128)) for b in range(X.shape[0])])
+
+
+def nrmse(a, ref):
+    return float(np.linalg.norm(a - ref) / np.linalg.norm(ref))
+
+
+@pytest.mark.parametrize("Nx,Ny,b", SIZES)
+@pytest.mark.parametrize("inverse", [False, True])
+def test_split_bf16_meets_image_bound(tts, Nx, Ny, b, inverse):
+    X = rand_images(b, Nx, Ny, Nx * 1000 + Ny)
+    ref = reference(X, inverse)
+    y = run(tts, X, inverse, tts.TTS_DFT_BF16X3)
+    per_image = [nrmse(y[k], ref[k]) for k in range(b)]
+    assert max(per_image) <= 1e-4, per_image
+
+
+@pytest.mark.parametrize("Nx,Ny,b", [(128, 128, 2), (256, 256, 1)])
+def test_plain_bf16_misses_image_bound(tts, Nx, Ny, b):
+    X = rand_images(b, Nx, Ny, 7)
+    ref = reference(X, False)
+    e = nrmse(run(tts, X, False, tts.TTS_DFT_BF16), ref)
+    assert 1e-4 < e < 2e-2, e
+
+
+def test_in_place_and_errors(tts):
+    import torch
+    X = rand_images(2, 64, 96, 3)
+    ref = reference(X, False)
+    y = run(tts, X, False, tts.TTS_DFT_BF16X3, inplace=True)
+    assert nrmse(y, ref) <= 1e-4
+    x = torch.from_numpy(X).cuda()
+    with pytest.raises(tts.TtsError):
+        tts.tts_dft2d_gemm(x, torch.empty_like(x), x)            # tmp aliases in
+    bad = torch.zeros((1, 48, 64), dtype=torch.complex64, device="cuda")
+    with pytest.raises(tts.TtsError):
+        tts.tts_dft2d_gemm(bad, torch.empty_like(bad), torch.empty_like(bad))   # 48 is not a multiple of 32
