@@ -84,6 +84,13 @@ def parse():
     ap.add_argument("--preload", action="store_true", help="all streams arrive at t = 0")
     ap.add_argument("--arena-mib", type=int, default=4096, help="engine arena (admission budget)")
     ap.add_argument("--fft2d", action="store_true", help="time the batched unitary 2D DFT kernel instead")
+    ap.add_argument("--dft-gemm", action="store_true",
+                    help="time the 2D DFT as tensor-core matrix products (tcgen05, BF16)")
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "bf16"])
+    ap.add_argument("--precision-variant", action="store_true",
+                    help="192x192 R=32 sequence: per-frame image NRMSE vs the FP64 oracle for the FFT, "
+                         "BF16 hi+lo and plain BF16 row transforms")
+    ap.add_argument("--variant-frames", type=int, default=200)
     ap.add_argument("--fft-n", type=int, default=256)
     ap.add_argument("--fft-batch", type=int, default=512)
     return ap.parse_args()
@@ -760,8 +767,158 @@ def run_serve(args):
     }
 
 
+def run_dft_gemm(args):
+    """The unitary 2D DFT as two tensor-core matrix products per image (tts_dft2d_gemm), on a
+    batch larger than L2, against the measured dense BF16 peak; error per image against
+    numpy's FP64 FFT on a sample, with the Stockham FFT path (tts_fft2d) timed beside it."""
+    import torch
+
+    from paper_1609_04104_gb300 import tts
+    tts.load()
+    n, b = args.fft_n, args.fft_batch
+    prec = tts.TTS_DFT_BF16X3 if args.precision == "bf16x3" else tts.TTS_DFT_BF16
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn((b, n, n), dtype=torch.complex64, device="cuda", generator=g)
+    y = torch.empty_like(x)
+    tmp = torch.empty_like(x)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for _ in range(args.steps):
+            e0.record(st)
+            fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        return float(np.median(ts))
+
+    t = timed(lambda: tts.tts_dft2d_gemm(x, y, tmp, precision=prec, status=status, stream=st))
+    assert int(status.item()) == 0, "a bounded wait ran out"
+    t_fft = timed(lambda: tts.tts_fft2d(x, tmp, stream=st))
+    k = min(b, 4)
+    ref = np.fft.fft2(x[:k].cpu().numpy().astype(np.complex128), norm="ortho")
+    tts.tts_dft2d_gemm(x, y, tmp, precision=prec, status=status, stream=st)
+    got = y[:k].cpu().numpy()
+    errs = [float(np.linalg.norm(got[i] - ref[i]) / np.linalg.norm(ref[i])) for i in range(k)]
+    products = 3 if prec == tts.TTS_DFT_BF16X3 else 1
+    flops = 2 * 2 * b * n * (2 * n) * (2 * n) * products   # two passes, M = b n, N' = K' = 2n
+    peak = 1940.8
+    try:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+    except Exception:
+        pass
+    achieved = flops / t / 1e12
+    return {"metric": "2D DFT as tensor-core matrix products", "value": b / t, "unit": "images/s",
+            "config": {"workload": f"dft2d_gemm_{n}x{n}_batch{b}", "precision": args.precision,
+                       "l2": "working set > L2", "products_per_pass": products},
+            "ms_per_call": t * 1e3, "fft_path_ms_per_call": t_fft * 1e3,
+            "nrmse_vs_fp64_per_image": errs,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "flops_per_call": flops,
+                         "peak_note": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)"},
+            "algorithmic_gbs": 16 * n * n * b / t / 1e9}
+
+
+def run_precision_variant(args):
+    """The precision study on the 192 x 192, R = 32 sequence. The FP32-FFT form runs the
+    sequence with its own informative line draws; the tensor-core forms (BF16 hi + lo and
+    plain BF16 products for the acquired rows' transform) run the same frames with those
+    lines. Frames/s per form with the frames resident in HBM. The cpu_baseline leg times the
+    FP64 oracle on the first frames with the same lines and reports each form's per-frame
+    image NRMSE against it."""
+    import torch
+
+    from paper_1609_04104_gb300 import inputs, tts
+    tts.load()
+    w = inputs.CINE192
+    T = args.variant_frames
+    Y = inputs.kspace(w, inputs.phantom(w, T))
+    A0, B0 = inputs.init_factors(w.Nx, w.Ny, w.R, w.seed)
+    Yd = torch.from_numpy(Y).cuda()
+    ones = torch.ones(w.Nx, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    forms = {"fft_fp32": tts.TTS_ROWDFT_FFT, "tc_bf16x3": tts.TTS_ROWDFT_BF16X3, "tc_bf16": tts.TTS_ROWDFT_BF16}
+    masks = None
+    res, images = {}, {}
+    for name, rd in forms.items():
+        trk = tts.Tracker(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, mm_iters=w.mm_iters, central_lines=w.central_lines,
+                          row_dft=rd, cuda_stream=stream)
+        ring = torch.empty((T, w.Nx, w.Ny), dtype=torch.complex64, device="cuda")
+        drawn = torch.zeros((T, w.Nx), dtype=torch.uint8, device="cuda")
+        Md = None if masks is None else torch.from_numpy(masks).cuda()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for rep in range(2):   # warm-up pass, then the timed pass
+            trk.set_factors(A0, B0)
+            trk.set_stats(0.0, 0.0, 0.0, 0)
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                for t in range(T):
+                    if Md is not None:
+                        m = Md[t]
+                    elif t < w.warmup_frames:
+                        m = ones
+                    else:
+                        tts.tts_next_mask(trk.h, w.rate, w.seed, drawn[t])
+                        m = drawn[t]
+                    if Md is None and t < w.warmup_frames:
+                        drawn[t].copy_(ones)
+                    tts.tts_push_frame(trk.h, Yd[t], m, full_frame=True)
+                    tts.tts_image(trk.h, t, ring[t])
+                e1.record(stream)
+            torch.cuda.synchronize()
+        trk.synchronize()
+        if masks is None:
+            masks = drawn.cpu().numpy()
+        res[name] = {"frames_per_s": T / (e0.elapsed_time(e1) / 1e3)}
+        images[name] = ring.cpu().numpy()
+        trk.close()
+    for name in forms:
+        d = [float(np.linalg.norm(images[name][t] - images["fft_fp32"][t]) / np.linalg.norm(images["fft_fp32"][t]))
+             for t in range(T)]
+        res[name]["nrmse_vs_fft_form_max"] = max(d)
+    out = {"metric": "per-frame image NRMSE vs the FP64 oracle, by row-transform precision",
+           "config": {"workload": w.name, "Nx": w.Nx, "Ny": w.Ny, "R": w.R, "T": T, "mm_iters": w.mm_iters,
+                      "k_lines": w.k_lines, "masks": "the FP32-FFT form's informative draws, shared by every form"},
+           "forms": res, "ridge": "FP32 Gauss-Jordan + float-float refinement (FP64 grade)"}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = precision_cpu_baseline(args, w, Y, A0, B0, masks, images)
+    return out
+
+
+def precision_cpu_baseline(args, w, Y, A0, B0, masks, images):
+    """The FP64 oracle on the first frames of the 192 x 192 sequence with the GPU forms'
+    lines (timed on the host cores), and every form's per-frame image NRMSE against it."""
+    from oracle import tracker as O
+    from paper_1609_04104_gb300 import inputs
+    n = min(len(masks), args.cpu_sample_frames * 5)
+    tr = O.Tracker(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, w.mm_iters, A=A0, B=B0)
+    t0 = time.perf_counter()
+    ref = [tr.push_frame(inputs.observed_rows(Y[t], masks[t]), masks[t]) for t in range(n)]
+    el = time.perf_counter() - t0
+    per_form = {}
+    for name, imgs in images.items():
+        e = np.array([O.nrmse(imgs[t], ref[t]) for t in range(n)])
+        per_form[name] = {"nrmse_max": float(e.max()), "nrmse_mean": float(e.mean()), "meets_1e-4": bool(e.max() <= 1e-4)}
+    return {"value": n / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"frames 0-{n - 1} of the 192x192 R=32 sequence with the GPU forms' lines",
+            "image_nrmse_vs_oracle": per_form}
+
+
 def main():
     args = parse()
+    if args.precision_variant:
+        print(json.dumps(run_precision_variant(args)))
+        return
+    if args.dft_gemm:
+        print(json.dumps(run_dft_gemm(args)))
+        return
     if args.serve:
         print(json.dumps(run_serve(args)))
         return

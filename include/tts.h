@@ -81,6 +81,16 @@ enum {
   TTS_LAUNCH_PHASES = 1   /* one kernel launch per phase (same arithmetic, no cluster) */
 };
 
+/* The per-frame inverse DFT of the acquired rows along the readout axis (Yt = y_S conj(F_Ny),
+ * the data side of the separable form of Alg. 3): in the frame kernel by a shared-memory
+ * Stockham FFT in FP32 (default), or by the tensor-core matrix product of tts_dft2d_gemm
+ * before it (Ny a multiple of 32 in [32, 256]; not in an engine). */
+enum {
+  TTS_ROWDFT_FFT = 0,
+  TTS_ROWDFT_BF16X3 = 1,   /* bf16 hi + lo split operands, FP32 accumulation */
+  TTS_ROWDFT_BF16 = 2      /* plain bf16 operands (does not meet the 1e-4 image bound) */
+};
+
 typedef struct tts_handle tts_handle;
 
 typedef struct {
@@ -98,11 +108,12 @@ typedef struct {
   uint64_t init_seed;       /* seed of the default CN(0, 1/N) initial factors */
   uint32_t stream_id;       /* enters the line-draw counter so streams draw independently */
   void* cuda_stream;        /* cudaStream_t to enqueue on; NULL = a stream the handle creates */
+  int row_dft;              /* TTS_ROWDFT_*: how the acquired rows are transformed each frame */
 } tts_config;
 
 /* Fill cfg with defaults: mm_iters 1, central_lines 8, TTS_POLICY_INFORMATIVE, vd_alpha -1,
  * without replacement, Gauss-Seidel, fused launch, cluster_ctas 0, init_seed 0,
- * stream_id 0, cuda_stream NULL. */
+ * stream_id 0, cuda_stream NULL, row_dft TTS_ROWDFT_FFT. */
 void tts_config_init(tts_config* cfg, int Nx, int Ny, int R, double lambda_forget, double mu);
 
 /* Create a tracker (problem (P2) of §III for M = 3: factors A, B of the image-domain
@@ -181,8 +192,9 @@ int tts_sample_lines_from_probs(const double* p, int Nx, int k_lines, int centra
 int tts_save(tts_handle* h, void* buf, size_t* len);
 int tts_load(tts_handle* h, const void* buf, size_t len);
 
-/* Wait for the handle's queued work; returns a deferred device status
- * (TTS_ENONFINITE for a skipped frame) once, then clears it. */
+/* Wait for the handle's queued work; returns a deferred device status once, then clears
+ * it: TTS_ETIMEOUT if a bounded wait of the tensor-core row transform ran out (the frame's
+ * results are invalid), TTS_ENONFINITE for a skipped frame. */
 int tts_synchronize(tts_handle* h);
 
 /* Kernel launches one tts_push_frame enqueues with the handle's settings. */
@@ -310,7 +322,8 @@ void tts_engine_destroy(tts_engine* e);
 
 /* Admission: create a tracker for cfg in a free slot whose footprint fits in the arena
  * (first fit). cfg->cluster_ctas is replaced by the engine's preferred size (or the next
- * larger that fits the stream), cfg->launch and cfg->cuda_stream by the engine's. On success *slot is the stream's slot (0..max_slots-1). TTS_EBUSY when every
+ * larger that fits the stream), cfg->launch and cfg->cuda_stream by the engine's; row_dft
+ * must be TTS_ROWDFT_FFT (TTS_EINVAL otherwise). On success *slot is the stream's slot (0..max_slots-1). TTS_EBUSY when every
  * slot is taken or no free arena block is large enough; TTS_EINVAL for a bad cfg. Does
  * not wait for steps in flight. */
 int tts_engine_admit(tts_engine* e, const tts_config* cfg, int* slot);

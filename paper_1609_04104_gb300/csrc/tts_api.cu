@@ -72,7 +72,7 @@ std::vector<Piece> handle_pieces(tts_handle* h, int Nx, int Ny, int R, int C) {
       {(void**)&p.partMB, sizeof(float2) * C * R * R},  {(void**)&p.partP, sizeof(float2) * C * Nx * R},
       {(void**)&p.sc, sizeof(double) * SC_COUNT},
       {(void**)&p.sf, sizeof(double) * SF_COUNT},       {(void**)&p.gamma, sizeof(float2) * R},
-      {(void**)&p.gamma_d, sizeof(double2) * R},        {(void**)&p.status, sizeof(int) * (1 + TTS_MAX_CLUSTER)},
+      {(void**)&p.gamma_d, sizeof(double2) * R},        {(void**)&p.status, sizeof(int) * (2 + TTS_MAX_CLUSTER)},
       {(void**)&p.Wx, sizeof(float2) * Nx},             {(void**)&p.Wy, sizeof(float2) * Ny},
       {(void**)&h->X, sizeof(float2) * Nx * Ny},        {(void**)&h->dmask_push, (size_t)Nx},
       {(void**)&h->dmask_next, (size_t)Nx},             {(void**)&h->dp, sizeof(double) * Nx},
@@ -99,6 +99,9 @@ int handle_check_config(const tts_config* c) {
   if (c->launch != TTS_LAUNCH_FUSED && c->launch != TTS_LAUNCH_PHASES) return fail(TTS_EINVAL, "unknown launch mode%s");
   if (c->cluster_ctas < 0 || c->cluster_ctas > TTS_MAX_CLUSTER) return fail(TTS_EINVAL, "cluster_ctas must be 0..16%s");
   if (!isfinite(c->vd_alpha)) return fail(TTS_EINVAL, "vd_alpha must be finite%s");
+  if (c->row_dft < TTS_ROWDFT_FFT || c->row_dft > TTS_ROWDFT_BF16) return fail(TTS_EINVAL, "unknown row_dft%s");
+  if (c->row_dft != TTS_ROWDFT_FFT && !dft_gemm_size_ok(c->Ny))
+    return fail(TTS_EINVAL, "the tensor-core row transform needs Ny a multiple of 32 in [32, 256]%s");
   return TTS_OK;
 }
 
@@ -268,6 +271,7 @@ void tts_config_init(tts_config* c, int Nx, int Ny, int R, double lambda_forget,
   c->init_seed = 0;
   c->stream_id = 0;
   c->cuda_stream = nullptr;
+  c->row_dft = TTS_ROWDFT_FFT;
 }
 
 int tts_create(int Nx, int Ny, int R, double lambda_forget, double mu, tts_handle** out) {
@@ -350,6 +354,14 @@ int tts_push_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line_mas
   FrameParams p;
   const int rs = handle_stage_frame(h, y_rows, line_mask, flags, &p);
   if (rs != TTS_OK) return rs;
+  if (h->cfg.row_dft != TTS_ROWDFT_FFT) {
+    // the acquired rows' transform on the tensor cores, straight into Yt
+    const int rr = launch_row_dft(p.yrows, p.Yt, p.mask, h->cfg.Nx, h->cfg.Ny, p.full_frame,
+                                  h->cfg.row_dft == TTS_ROWDFT_BF16X3 ? 1 : 0, p.status + 1 + TTS_MAX_CLUSTER,
+                                  h->stream);
+    if (rr != TTS_OK) return fail(rr, "row transform launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    p.yt_ready = 1;
+  }
   const int rc = launch_frame(p, h->cfg.launch, h->stream);
   if (rc != TTS_OK) return fail(rc, "frame kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
   h->t += 1;
@@ -516,9 +528,15 @@ int tts_load(tts_handle* h, const void* buf, size_t len) {
 
 int tts_synchronize(tts_handle* h) {
   if (!h) return fail(TTS_EINVAL, "NULL handle%s");
-  int st = 0;
+  int st = 0, tmo = 0;
   CK(cudaMemcpyAsync(&st, h->fp.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&tmo, h->fp.status + 1 + TTS_MAX_CLUSTER, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (tmo) {
+    CK(cudaMemsetAsync(h->fp.status + 1 + TTS_MAX_CLUSTER, 0, sizeof(int), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return fail(TTS_ETIMEOUT, "a bounded wait of the tensor-core row transform ran out%s");
+  }
   if (st) {
     CK(cudaMemsetAsync(h->fp.status, 0, sizeof(int), h->stream));
     CK(cudaStreamSynchronize(h->stream));

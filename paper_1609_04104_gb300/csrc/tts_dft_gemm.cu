@@ -36,7 +36,7 @@ namespace {
 
 constexpr int kRows = 128;     // rows per CTA (UMMA M)
 constexpr int kKC = 32;        // K' chunk (bf16 elements) per stage
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;   // 8 warps: warp w and w + 4 share TMEM lanes 32 (w % 4).. in the epilogue
 constexpr int kStages = 2;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -118,6 +118,12 @@ struct GemmArgs {
   int nh;                 // accumulators (1, or 2 when 2N > 256)
   int split;              // 1: hi*hi + hi*lo + lo*hi; 0: hi*hi
   int* err;               // set to 1 when a wait ran out
+  // row mode (the acquired rows of one k-space frame): when mask is set, the rows are the
+  // lines i with mask[i] != 0 (M = their number, one row per "image", so the output is
+  // row-major); with full_frame, row m is x row S[m], else x row m
+  const uint8_t* mask;
+  int mask_n;
+  int full_frame;
 };
 
 // Shared memory of one CTA (bytes): per stage A_hi, A_lo (128 x 32 bf16 = 8 KB each) and
@@ -132,6 +138,26 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm_kernel(GemmArgs g) {
   uint64_t* bars = (uint64_t*)(smem + kStages * SB);   // full[2], empty[2], done
   uint32_t* slot = (uint32_t*)(bars + 8);
   __shared__ int abort_flag;
+  __shared__ int srows[TTS_MAX_N];
+  __shared__ int scount;
+  int M = g.M;
+  if (g.mask) {
+    // compact the line mask into the increasing list S (warp 0)
+    if (warp == 0) {
+      int count = 0;
+      for (int base = 0; base < g.mask_n; base += 32) {
+        const int i = base + lane;
+        const bool on = i < g.mask_n && g.mask[i] != 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, on);
+        if (on) srows[count + __popc(bal & ((1u << lane) - 1u))] = i;
+        count += __popc(bal);
+      }
+      if (lane == 0) scount = count;
+    }
+    __syncthreads();
+    M = scount;
+    if ((int)blockIdx.x * kRows >= M) return;   // uniform: the whole CTA has no rows
+  }
   const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[2]), done = smem_u32(&bars[4]);
   if (tid == 0) {
     abort_flag = 0;
@@ -158,6 +184,22 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm_kernel(GemmArgs g) {
   const int nK = Np / kKC;
   const uint32_t idesc = instr_desc(NT, kRows);
   const size_t bchunk = (size_t)Np * kKC * 2;   // bytes of one K' chunk of the embedding (all N')
+  // A chunk: 128 rows x 32 floats (16 complex), 8 threads per row, one float4 each, four per
+  // thread; the next chunk's values are loaded while the current chunk's products run
+  constexpr int kPer = kRows * kKC / 4 / kThreads;
+  float4 pre[kPer];
+  auto load_chunk = [&](int kc) {
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int idx = tid + kThreads * u;
+      const int r = idx >> 3, q = idx & 7;
+      const int m = m0 + r;
+      const int src = (g.mask && g.full_frame && m < M) ? srows[m] : m;
+      pre[u] = m < M ? *(const float4*)((const float*)(g.x + (size_t)src * N) + kc * kKC + 4 * q)
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  load_chunk(0);
   bool ok = true;
   for (int kc = 0; kc < nK; ++kc) {
     const int s = kc & 1, use = kc >> 1;
@@ -175,14 +217,11 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm_kernel(GemmArgs g) {
       bulk_g2s(smem_u32(bhi), (const char*)g.bhi + kc * bchunk, (uint32_t)bchunk, full0 + 8 * s);
       if (g.split) bulk_g2s(smem_u32(blo), (const char*)g.blo + kc * bchunk, (uint32_t)bchunk, full0 + 8 * s);
     }
-    // A chunk: 128 rows x 32 floats (16 complex), 8 threads per row, float4 each
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < kPer; ++u) {
       const int idx = tid + kThreads * u;
       const int r = idx >> 3, q = idx & 7;
-      const int m = m0 + r;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (m < g.M) v = *(const float4*)((const float*)(g.x + (size_t)m * N) + kc * kKC + 4 * q);
+      const float4 v = pre[u];
       const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
       // byte offset: 8-row group (r / 8) x 512, core matrix along K (q / 2) x 128, row (r % 8) x 16, half (q % 2) x 8
       const int off = (r >> 3) * 512 + (q >> 1) * 128 + (r & 7) * 16 + (q & 1) * 8;
@@ -200,6 +239,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm_kernel(GemmArgs g) {
         *(uint2*)(alo + off) = lv;
       }
     }
+    if (kc + 1 < nK) load_chunk(kc + 1);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
@@ -236,16 +276,18 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm_kernel(GemmArgs g) {
   if (abort_flag || !fin) {
     if (tid == 0) atomicExch(g.err, 1);
   } else {
-    // epilogue: warp w reads TMEM lanes 32w.. (rows), 32 fp32 columns per load
-    const int r = warp * 32 + lane;
+    // epilogue: warp w reads TMEM lanes 32 (w % 4).. (rows), 32 fp32 columns per load; the
+    // warps w and w + 4 take alternate column blocks
+    const int lq = warp & 3, wg = warp >> 2;
+    const int r = lq * 32 + lane;
     const int m = m0 + r;
     const int b = m / g.rows, i = m - b * g.rows;
     float2* ob = g.out + (size_t)b * N * g.rows;
     for (int h = 0; h < g.nh; ++h) {
-      for (int c0 = 0; c0 < NT; c0 += 32) {
+      for (int c0 = 32 * wg; c0 < NT; c0 += 64) {
         uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + h * 256 + c0, v);
-        if (m < g.M) {
+        tmem_ld32(tmem + ((uint32_t)(lq * 32) << 16) + h * 256 + c0, v);
+        if (m < M) {
           const int j0 = (h * NT + c0) >> 1;
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj)
@@ -338,6 +380,20 @@ int embedding(int N, int inverse, const uint4** hi, const uint4** lo) {
   return TTS_OK;
 }
 
+int launch_args(GemmArgs& a, int inverse, int grid, cudaStream_t st) {
+  const uint4 *hi = nullptr, *lo = nullptr;
+  const int rc = embedding(a.N, inverse, &hi, &lo);
+  if (rc != TTS_OK) return rc;
+  a.bhi = hi;
+  a.blo = lo;
+  a.nh = 2 * a.N > 256 ? 2 : 1;
+  const int smem = std::max(kStages * stage_bytes(a.N) + 128, a.nh == 1 ? 80 * 1024 : 120 * 1024);
+  if (cudaFuncSetAttribute(dft_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return TTS_ECUDA;
+  dft_gemm_kernel<<<grid, kThreads, smem, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
+}
+
 int launch_pass(const float2* x, float2* out, int batch, int rows, int N, int inverse, int split, int* err,
                 cudaStream_t st) {
   const uint4 *hi = nullptr, *lo = nullptr;
@@ -354,6 +410,9 @@ int launch_pass(const float2* x, float2* out, int batch, int rows, int N, int in
   a.nh = 2 * N > 256 ? 2 : 1;
   a.split = split;
   a.err = err;
+  a.mask = nullptr;
+  a.mask_n = 0;
+  a.full_frame = 0;
   // TMEM holds 512 columns per SM: ask for enough shared memory that the CTAs resident on
   // one SM never need more (two CTAs of 256 columns, or one of 512), so an allocation never
   // waits on a CTA that cannot finish
@@ -370,6 +429,22 @@ int launch_pass(const float2* x, float2* out, int batch, int rows, int N, int in
 // Sizes the tensor-core form supports: N a multiple of 32 in [32, 256] (K' chunks of 32,
 // at most two accumulators of 256 columns).
 bool dft_gemm_size_ok(int N) { return N >= 32 && N <= 256 && N % 32 == 0; }
+
+int launch_row_dft(const float2* y, float2* yt, const uint8_t* mask, int Nx, int Ny, int full_frame, int split,
+                   int* err, cudaStream_t st) {
+  GemmArgs a;
+  a.x = y;
+  a.out = yt;
+  a.M = Nx;      // upper bound; the kernel counts the mask's lines
+  a.rows = 1;
+  a.N = Ny;
+  a.split = split;
+  a.err = err;
+  a.mask = mask;
+  a.mask_n = Nx;
+  a.full_frame = full_frame;
+  return launch_args(a, 1, (Nx + kRows - 1) / kRows, st);
+}
 
 int launch_dft2d_gemm(const float2* in, float2* out, float2* tmp, int batch, int Nx, int Ny, int inverse,
                       int split, int* err, cudaStream_t st) {

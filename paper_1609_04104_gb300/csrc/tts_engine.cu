@@ -365,6 +365,7 @@ int tts_engine_admit(tts_engine* e, const tts_config* cfg, int* slot_out) {
   c.cuda_stream = e->admin;
   int rc = handle_check_config(&c);
   if (rc) return rc;
+  if (c.row_dft != TTS_ROWDFT_FFT) return tts_fail(TTS_EINVAL, "engine streams transform rows in the frame kernel%s");
   // the preferred cluster size, else the next larger one that holds the stream's layout
   int C = 0;
   const size_t need = engine_footprint(c, e->C, &C);

@@ -459,7 +459,12 @@ __device__ void step_ingest(const FrameParams& p, SM& sm, int cta) {
   const int bsy = fsz(Ny);   // padded row stride of the transform buffers
   const int fft_rows = max(1, p.lay.chunk_f2 / (2 * bsy));
   int bad = 0;
-  for (int m0 = ms.lo; m0 < ms.hi; m0 += fft_rows) {
+  if (p.yt_ready)   // rows already transformed: check them only
+    for (int e = ms.lo * Ny + tid; e < ms.hi * Ny; e += nth) {
+      const float2 v = p.Yt[e];
+      if (!isfinite(v.x) || !isfinite(v.y)) bad = 1;
+    }
+  for (int m0 = ms.lo; m0 < ms.hi && !p.yt_ready; m0 += fft_rows) {
     const int nr = min(fft_rows, ms.hi - m0);
     float2* buf = sm.chunk;
     float2* tmp = sm.chunk + fft_rows * bsy;

@@ -355,6 +355,7 @@ struct FrameParams {
   const uint8_t* mask;            // Nx bytes
   const float2* yrows;            // |S| x Ny acquired rows (or the full Nx x Ny frame)
   int full_frame;                 // yrows is the full frame: row m of S is yrows[rows[m]]
+  int yt_ready;                   // Yt was formed before the launch (tensor-core row transform)
   float2* Yt;                     // |S| x Ny: acquired rows times conj(F_Ny)
   int* rows;                      // S, increasing
   int* nrows;                     // |S|
@@ -434,6 +435,10 @@ int launch_fft2d(const float2* in, float2* out, int batch, int Nx, int Ny, int i
 int launch_ridge(const double2* G, const double2* h, int R, double2* gamma, cudaStream_t st);
 // 2D DFT as tensor-core matrix products (tts_dft_gemm.cu)
 bool dft_gemm_size_ok(int N);
+// Inverse unitary DFT of the acquired rows (mask lines) of a frame, Yt = y_S conj(F_Ny),
+// row-major |S| x Ny, on the tensor cores.
+int launch_row_dft(const float2* y, float2* yt, const uint8_t* mask, int Nx, int Ny, int full_frame, int split,
+                   int* err, cudaStream_t st);
 int launch_dft2d_gemm(const float2* in, float2* out, float2* tmp, int batch, int Nx, int Ny, int inverse,
                       int split, int* err, cudaStream_t st);
 int launch_init_factors(float2* A, int N, int R, uint64_t seed, uint32_t which, cudaStream_t st);

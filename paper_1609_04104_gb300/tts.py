@@ -21,6 +21,7 @@ TTS_EBUSY = -8
 TTS_ENGINE_GRAPH = 1
 TTS_ENGINE_MAX_SLOTS = 4096
 TTS_DFT_BF16X3, TTS_DFT_BF16 = 0, 1
+TTS_ROWDFT_FFT, TTS_ROWDFT_BF16X3, TTS_ROWDFT_BF16 = 0, 1, 2
 TTS_DEVICE_PTRS = 1
 TTS_FULL_FRAME = 2
 TTS_POLICY_UNIFORM, TTS_POLICY_VARDENS, TTS_POLICY_INFORMATIVE = 0, 1, 2
@@ -51,7 +52,7 @@ class tts_config(ctypes.Structure):
         ("mm_iters", ctypes.c_int), ("central_lines", ctypes.c_int), ("policy", ctypes.c_int),
         ("vd_alpha", ctypes.c_double), ("with_replacement", ctypes.c_int), ("update", ctypes.c_int),
         ("launch", ctypes.c_int), ("cluster_ctas", ctypes.c_int), ("init_seed", ctypes.c_uint64),
-        ("stream_id", ctypes.c_uint32), ("cuda_stream", ctypes.c_void_p),
+        ("stream_id", ctypes.c_uint32), ("cuda_stream", ctypes.c_void_p), ("row_dft", ctypes.c_int),
     ]
 
 

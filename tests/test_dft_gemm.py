@@ -69,3 +69,45 @@ def test_in_place_and_errors(tts):
     bad = torch.zeros((1, 48, 64), dtype=torch.complex64, device="cuda")
     with pytest.raises(tts.TtsError):
         tts.tts_dft2d_gemm(bad, torch.empty_like(bad), torch.empty_like(bad))   # 48 is not a multiple of 32
+
+
+@pytest.mark.parametrize("row_dft,bound", [(1, 1e-4), (2, None)])
+def test_tracker_with_tensor_core_row_transform(tts, row_dft, bound):
+    """Small cine through the tracker with the acquired rows transformed on the tensor
+    cores, against the FP64 oracle frame by frame (fixed masks, host rows and a full device
+    frame): the split form meets the image bound; plain BF16 is reported, not bounded."""
+    import torch
+
+    from paper_1609_04104_gb300 import inputs
+    from tests.helpers import nrmse_per_frame, run_oracle
+    w = inputs.scaled(inputs.SMALL_CINE, T=8)
+    Y = inputs.kspace(w, inputs.phantom(w, w.T))
+    A0, B0 = inputs.init_factors(w.Nx, w.Ny, w.R, w.seed)
+    M = inputs.uniform_line_masks(w, w.T)
+    ref, _, _ = run_oracle(w, w.T, Y, A0, B0, masks=M)
+    trk = tts.Tracker(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, mm_iters=w.mm_iters, central_lines=w.central_lines,
+                      row_dft=row_dft)
+    trk.set_factors(A0, B0)
+    out = []
+    for t in range(w.T):
+        if t % 2 == 0:
+            trk.push_frame(inputs.observed_rows(Y[t], M[t]), M[t])
+        else:
+            tts.tts_push_frame(trk.h, torch.from_numpy(Y[t]).cuda(), torch.from_numpy(M[t]).cuda(), full_frame=True)
+        out.append(trk.image(t))
+    trk.synchronize()
+    trk.close()
+    err = nrmse_per_frame(np.array(out), ref)
+    if bound is not None:
+        assert err.max() <= bound, err
+    else:
+        assert err.max() > 1e-4, err   # plain BF16 rows do not meet the image bound
+
+
+def test_row_transform_rejects_bad_sizes(tts):
+    with pytest.raises(tts.TtsError):
+        tts.Tracker(64, 48, 4, 0.9, 1e-2, row_dft=1)   # Ny = 48 is not a multiple of 32
+    eng = tts.Engine(1 << 24, 2)
+    with pytest.raises(tts.TtsError):
+        eng.admit(64, 64, 4, 0.9, 1e-2, row_dft=1)
+    eng.close()
