@@ -571,6 +571,26 @@ int tts_ridge_solve(const double* G, const double* h, int R, double* gamma) {
 
 // ---- standalone batched 2D DFT ----------------------------------------------------
 namespace {
+std::mutex g_status_mu;
+int* g_status[64];
+
+// A device status word per device for the standalone transforms' bounded waits.
+int* device_status(int* rc) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) {
+    *rc = TTS_ECUDA;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_status_mu);
+  if (!g_status[dev]) {
+    if (cudaMalloc(&g_status[dev], sizeof(int)) != cudaSuccess || cudaMemset(g_status[dev], 0, sizeof(int)) != cudaSuccess) {
+      *rc = TTS_ECUDA;
+      return nullptr;
+    }
+  }
+  return g_status[dev];
+}
 std::mutex g_tw_mu;
 struct TwEntry {
   int dev, n;
@@ -607,14 +627,17 @@ int tts_fft2d(const tts_c64* in, tts_c64* out, int batch, int Nx, int Ny, int in
   if (!wx) return rc;
   const float2* wy = device_twiddles(Ny, &rc);
   if (!wy) return rc;
-  rc = launch_fft2d((const float2*)in, (float2*)out, batch, Nx, Ny, inverse, wx, wy, nullptr, (cudaStream_t)cuda_stream);
+  if (fft2d_cluster_ok(Nx, Ny)) {
+    int* st = device_status(&rc);
+    if (!st) return fail(rc, "device status word%s");
+    rc = launch_fft2d_cluster((const float2*)in, (float2*)out, batch, Nx, inverse, wx, st, (cudaStream_t)cuda_stream);
+  } else {
+    rc = launch_fft2d((const float2*)in, (float2*)out, batch, Nx, Ny, inverse, wx, wy, nullptr,
+                      (cudaStream_t)cuda_stream);
+  }
   return rc == TTS_OK ? TTS_OK : fail(rc, "fft kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
 }
 
-namespace {
-std::mutex g_status_mu;
-int* g_status[64];
-}  // namespace
 
 int tts_dft2d_gemm(const tts_c64* in, tts_c64* out, tts_c64* tmp, int batch, int Nx, int Ny, int inverse,
                    int precision, int* dev_status, void* cuda_stream) {
@@ -627,15 +650,9 @@ int tts_dft2d_gemm(const tts_c64* in, tts_c64* out, tts_c64* tmp, int batch, int
   if (batch == 0) return TTS_OK;
   int* st = dev_status;
   if (!st) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) return fail(TTS_ECUDA, "device ordinal out of range%s");
-    std::lock_guard<std::mutex> lk(g_status_mu);
-    if (!g_status[dev]) {
-      CK(cudaMalloc(&g_status[dev], sizeof(int)));
-      CK(cudaMemset(g_status[dev], 0, sizeof(int)));
-    }
-    st = g_status[dev];
+    int rs = TTS_OK;
+    st = device_status(&rs);
+    if (!st) return fail(rs, "device status word%s");
   }
   const int rc = launch_dft2d_gemm((const float2*)in, (float2*)out, (float2*)tmp, batch, Nx, Ny, inverse,
                                    precision == TTS_DFT_BF16X3 ? 1 : 0, st, (cudaStream_t)cuda_stream);

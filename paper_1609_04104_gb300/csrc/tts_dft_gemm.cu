@@ -30,6 +30,7 @@
 #include <mutex>
 #include <vector>
 
+#include "tts_async.cuh"
 #include "tts_internal.cuh"
 
 namespace {
@@ -38,8 +39,6 @@ constexpr int kRows = 128;     // rows per CTA (UMMA M)
 constexpr int kKC = 32;        // K' chunk (bf16 elements) per stage
 constexpr int kThreads = 256;   // 8 warps: warp w and w + 4 share TMEM lanes 32 (w % 4).. in the epilogue
 constexpr int kStages = 2;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Shared-memory matrix descriptor (tcgen05): start address, leading-dimension byte offset
 // (between core matrices along K) and stride byte offset (between 8-row groups), all >> 4;
@@ -58,33 +57,6 @@ __host__ __device__ __forceinline__ uint32_t instr_desc(int n, int m) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(a), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: gives up after ~1 s of SM clock.
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
-  const long long t0 = clock64();
-  while (!mbar_try(a, parity))
-    if (clock64() - t0 > 2000000000LL) return false;
-  return true;
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(mbar)
-               : "memory");
-}
 __device__ __forceinline__ void umma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
