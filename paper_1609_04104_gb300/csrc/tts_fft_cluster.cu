@@ -96,16 +96,28 @@ __global__ void __launch_bounds__(kFftThreads, 2) fft2d_cluster_kernel(const flo
   const int nclusters = gridDim.x / CL, cid = blockIdx.x / CL;
   const int g = tid / T, t = tid % T;
   for (int k = tid; k < N; k += kFftThreads) W[fpad(k)] = Wg[k];
+  // the first row of each group for the next image, loaded while the current image's
+  // columns are written out and the cluster synchronises
+  float2 pv[R];
+  auto load_row = [&](float2* v, int img, int r) {
+    const float2* src = in + ((size_t)img * N + rank * RW + r) * N;
+#pragma unroll
+    for (int n2 = 0; n2 < R; ++n2) v[n2] = src[t + T * n2];
+  };
+  if (cid < batch && g < RW) load_row(pv, cid, g);
   __syncthreads();
   for (int img = cid; img < batch; img += nclusters) {
     cluster.sync();   // every column buffer is free (and every peer has started)
     // rows, straight from global memory
     for (int r = g; r < RW; r += GROUPS) {
       const int gr = rank * RW + r;
-      const float2* src = in + ((size_t)img * N + gr) * N;
       float2 v[R];
+      if (r == g) {
 #pragma unroll
-      for (int n2 = 0; n2 < R; ++n2) v[n2] = src[t + T * n2];
+        for (int n2 = 0; n2 < R; ++n2) v[n2] = pv[n2];
+      } else {
+        load_row(v, img, r);
+      }
       fft_line<N>(v, scr + g * N, 1, W, sign, t, [&](int k, float2 x) {
         float2* dst = cluster.map_shared_rank(G, k / CW);
         dst[gr * GS + (k % CW)] = x;
@@ -120,6 +132,7 @@ __global__ void __launch_bounds__(kFftThreads, 2) fft2d_cluster_kernel(const flo
       for (int n2 = 0; n2 < R; ++n2) v[n2] = col[(t + T * n2) * GS];
       fft_line<N>(v, col, GS, W, sign, t, [&](int k, float2 x) { col[k * GS] = x; });
     }
+    if (img + nclusters < batch && g < RW) load_row(pv, img + nclusters, g);
     __syncthreads();
     // write: one row segment of CW values (CW * 8 bytes) per warp instruction
     float2* ob = out + (size_t)img * N * N + rank * CW;
