@@ -247,3 +247,37 @@ def serving_arrivals(n: int = 256, rate_per_s: float = 4.0, lifetime: int = 300,
                                 rate=1.0 / 8.0, seed=seed * 100003 + k)
         out.append(Arrival(t_open=t, fps=fps, frames=lifetime, work=w))
     return out
+
+
+# ---- several receive coils ----------------------------------------------------------
+
+def coil_maps(Nx: int, Ny: int, C: int, seed: int = 0) -> np.ndarray:
+    """Synthetic coil sensitivities H_c (C x Nx x Ny, complex64): coil c sits at angle
+    2 pi c / C on a circle of radius 1.3 around the field of view [-1, 1]^2, with a
+    Gaussian magnitude profile (width 0.9) and a smooth linear phase of random slope;
+    the maps are normalised so that sum_c |H_c|^2 = 1 at every pixel (SENSE-style)."""
+    rng = np.random.default_rng([seed, 0xC011])
+    x = (np.arange(Nx) + 0.5) / Nx * 2.0 - 1.0
+    y = (np.arange(Ny) + 0.5) / Ny * 2.0 - 1.0
+    X, Yg = np.meshgrid(x, y, indexing="ij")
+    maps = []
+    for c in range(C):
+        th = 2.0 * math.pi * c / C
+        cx, cy = 1.3 * math.cos(th), 1.3 * math.sin(th)
+        mag = np.exp(-((X - cx) ** 2 + (Yg - cy) ** 2) / (2.0 * 0.9 ** 2))
+        kx, ky = rng.uniform(-1.5, 1.5, size=2)
+        maps.append(mag * np.exp(1j * (kx * X + ky * Yg + rng.uniform(0, 2 * math.pi))))
+    H = np.stack(maps)
+    H /= np.sqrt(np.sum(np.abs(H) ** 2, axis=0, keepdims=True))
+    return H.astype(np.complex64)
+
+
+def multicoil_kspace(w: Workload, frames: np.ndarray, H: np.ndarray) -> np.ndarray:
+    """Each coil's fully sampled noisy k-space, Y_c,t = DFT2(H_c .* L_t) + v with
+    v ~ CN(0, sigma^2); complex64, shape (T, C, Nx, Ny)."""
+    rng = np.random.default_rng([w.seed, 0x5B])
+    img = H[None, :, :, :].astype(np.complex128) * frames[:, None, :, :].astype(np.complex128)
+    Y = np.fft.fft2(img, axes=(-2, -1), norm="ortho")
+    s = w.sigma / math.sqrt(2.0)
+    Y = Y + s * (rng.standard_normal(Y.shape) + 1j * rng.standard_normal(Y.shape))
+    return Y.astype(np.complex64)
