@@ -159,6 +159,20 @@ int tts_push_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line_mas
  * the call waits for the image. */
 int tts_image(tts_handle* h, int64_t t, tts_c64* out, int flags);
 
+/* Several receive coils (Alg. 3 with C coils, §IV-B tomographic parallel MRI): coil c sees
+ * y_c = P_Omega F(H_c .* L_t) + v with known sensitivity H_c. maps: C x Nx x Ny complex64
+ * (host, or device with TTS_DEVICE_PTRS), copied; C in 1..TTS_MAX_COILS; NULL or C = 0
+ * returns the handle to the single-coil tracker. Afterwards tts_push_frame takes the
+ * coils' acquired rows stacked, C x |S| x Ny (or C x Nx x Ny with TTS_FULL_FRAME), and
+ * each MM iteration transforms the C R sensitivity-weighted rank-one images explicitly
+ * (batched 2D DFTs): Phi stacks the coils' masked DFTs, Theta = sum_c conj(H_c) .*
+ * F^{-1}(Xi_c), and the majoriser weights carry h_max = max_ij sum_c |H_c[i,j]|^2.
+ * Requires Gauss-Seidel updates, the FFT row transform and R (Ny + 1) <= 16384; not for
+ * engine streams. tts_image and tts_next_mask are unchanged; tts_save does not store the
+ * maps. A multi-coil frame waits for the line count and the input check on the host. */
+#define TTS_MAX_COILS 64
+int tts_set_coil_maps(tts_handle* h, const tts_c64* maps, int C, int flags);
+
 /* S0 of Alg. 5 for the next frame: draw its phase-encode lines under the handle's
  * policy (informative: scores of §V-B marginalised over readout as in §VI-C,
  * s_i = (Ny ||abar_i||^2 + R) / (R (Nx + Ny)) with abar the rows of the

@@ -285,6 +285,7 @@ int tts_create_ex(const tts_config* cfg, tts_handle** out) { return handle_creat
 void tts_destroy(tts_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  mc_detach(h);
   if (h->own_mem) cudaFree(h->dmem);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -349,8 +350,27 @@ int tts_get_config(tts_handle* h, tts_config* cfg) {
   return TTS_OK;
 }
 
+int tts_set_coil_maps(tts_handle* h, const tts_c64* maps, int C, int flags) {
+  if (!h) return fail(TTS_EINVAL, "NULL handle%s");
+  if (h->in_engine) return fail(TTS_EINVAL, "engine streams are single-coil%s");
+  if (flags & ~TTS_DEVICE_PTRS) return fail(TTS_EINVAL, "unknown flags%s");
+  if (!maps || C == 0) {
+    CK(cudaStreamSynchronize(h->stream));
+    mc_detach(h);
+    return TTS_OK;
+  }
+  if (C < 1 || C > TTS_MAX_COILS) return fail(TTS_EINVAL, "C must be 1..64%s");
+  if (h->cfg.update != TTS_UPDATE_GAUSS_SEIDEL || h->cfg.row_dft != TTS_ROWDFT_FFT)
+    return fail(TTS_EINVAL, "the multi-coil tracker runs Gauss-Seidel iterations with the FFT row transform%s");
+  if ((size_t)h->cfg.R * (h->cfg.Ny + 1) + h->cfg.Ny > 16384 + 512)
+    return fail(TTS_EINVAL, "the multi-coil tracker needs R (Ny + 1) <= 16384%s");
+  CK(cudaStreamSynchronize(h->stream));
+  return mc_attach(h, (const float2*)maps, C, (flags & TTS_DEVICE_PTRS) != 0);
+}
+
 int tts_push_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line_mask, int flags) {
   if (!h || !y_rows) return fail(TTS_EINVAL, "NULL argument%s");
+  if (h->mc) return mc_push(h, y_rows, line_mask, flags);
   FrameParams p;
   const int rs = handle_stage_frame(h, y_rows, line_mask, flags, &p);
   if (rs != TTS_OK) return rs;

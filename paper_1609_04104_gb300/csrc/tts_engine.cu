@@ -387,6 +387,7 @@ int tts_engine_admit(tts_engine* e, const tts_config* cfg, int* slot_out) {
     return rc;
   }
   // from now on the slot's work is ordered on the engine stream
+  h->in_engine = true;
   h->stream = e->stream;
   h->cfg.cuda_stream = e->stream;
   e->slot[s] = h;

@@ -8,6 +8,8 @@
 
 #include "tts_internal.cuh"
 
+struct MultiCoil;   // coil maps and workspace of the multi-coil tracker (tts_multicoil.cu)
+
 struct tts_handle {
   tts_config cfg;
   int dev = 0;
@@ -25,7 +27,9 @@ struct tts_handle {
   int64_t t = 0;                // frames processed
   bool have_next = false;
   bool next_on_host = false;
+  bool in_engine = false;       // a slot of an engine (no coil maps)
   std::vector<uint8_t> next_host;
+  MultiCoil* mc = nullptr;      // set by tts_set_coil_maps
 };
 
 // Validates a configuration (message through tts_last_error on failure).
@@ -45,4 +49,8 @@ uint64_t handle_draw_counter(const tts_handle* h);
 // Lines a draw at this rate keeps: max(central, round(rate Nx)).
 int handle_k_lines(const tts_handle* h, double rate);
 int tts_fail(int code, const char* fmt, const char* detail = nullptr);
+// multi-coil tracker (tts_multicoil.cu)
+int mc_attach(tts_handle* h, const float2* maps, int C, bool device);
+void mc_detach(tts_handle* h);
+int mc_push(tts_handle* h, const tts_c64* y, const uint8_t* mask, int flags);
 int tts_cuda_fail(cudaError_t e, const char* where);

@@ -35,7 +35,7 @@ EXPORTS = [
     "tts_launches_per_frame", "tts_ridge_solve", "tts_fft2d", "tts_push_frame_noalloc",
     "tts_stream_footprint", "tts_engine_create", "tts_engine_destroy", "tts_engine_admit", "tts_engine_release",
     "tts_engine_handle", "tts_engine_step", "tts_engine_image", "tts_engine_mask", "tts_engine_synchronize",
-    "tts_engine_info", "tts_engine_autotune", "tts_dft2d_gemm", "tts_last_error",
+    "tts_engine_info", "tts_engine_autotune", "tts_dft2d_gemm", "tts_set_coil_maps", "tts_last_error",
 ]
 
 
@@ -114,6 +114,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "tts_fft2d": (I, [P, P, I, I, I, I, P]),
         "tts_push_frame_noalloc": (I, [ctypes.POINTER(tts_frame_args), P]),
         "tts_dft2d_gemm": (I, [P, P, P, I, I, I, I, I, P, P]),
+        "tts_set_coil_maps": (I, [H, P, I, I]),
         "tts_stream_footprint": (I, [ctypes.POINTER(tts_config), ctypes.POINTER(ctypes.c_size_t)]),
         "tts_engine_create": (I, [ctypes.c_size_t, I, I, I, P, ctypes.POINTER(H)]),
         "tts_engine_destroy": (None, [H]),
@@ -234,6 +235,15 @@ def tts_get_config(h) -> tts_config:
     cfg = tts_config()
     _check(load().tts_get_config(h, ctypes.byref(cfg)))
     return cfg
+
+
+def tts_set_coil_maps(h, maps) -> None:
+    """Coil sensitivities (C x Nx x Ny complex64, numpy or CUDA tensor); None = single coil."""
+    if maps is None:
+        _check(load().tts_set_coil_maps(h, None, 0, 0))
+        return
+    pm, fm = _ptr(maps, np.complex64)
+    _check(load().tts_set_coil_maps(h, pm, maps.shape[0], fm))
 
 
 def tts_push_frame(h, y_rows, line_mask=None, full_frame=False) -> None:
@@ -528,6 +538,9 @@ class Tracker:
 
     def gamma(self):
         return tts_get_gamma(self.h, self.R)
+
+    def set_coil_maps(self, maps):
+        tts_set_coil_maps(self.h, np.ascontiguousarray(maps, np.complex64) if isinstance(maps, np.ndarray) else maps)
 
     def push_frame(self, y_rows, line_mask=None):
         if isinstance(y_rows, np.ndarray):
