@@ -78,22 +78,30 @@ __global__ void __launch_bounds__(kT) mc_gram_kernel(const float2* __restrict__ 
   }
 }
 
-// G = sum of the partials + mu I, h = sum of the partials (FP64, fixed order)
+// G = sum of the partials + mu I, h = sum of the partials (FP64): one warp per entry, lane l
+// summing partials l, l + 32, ..., then a fixed shuffle tree (the order never changes)
 __global__ void mc_gram_reduce_kernel(const double2* __restrict__ part, int nparts, int R, double mu,
                                       double2* __restrict__ G, double2* __restrict__ h) {
   const int E = R * R + R;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
-    double2 acc = make_double2(0.0, 0.0);
-    for (int p = 0; p < nparts; ++p) {
-      const double2 v = part[(size_t)p * E + e];
-      acc.x += v.x;
-      acc.y += v.y;
-    }
+  const int lane = threadIdx.x & 31;
+  const int e = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (e >= E) return;   // whole warps
+  double ax = 0.0, ay = 0.0;
+  for (int p = lane; p < nparts; p += 32) {
+    const double2 v = part[(size_t)p * E + e];
+    ax += v.x;
+    ay += v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ax += __shfl_xor_sync(0xffffffffu, ax, o);
+    ay += __shfl_xor_sync(0xffffffffu, ay, o);
+  }
+  if (lane == 0) {
     if (e < R * R) {
-      if (e / R == e % R) acc.x += mu;
-      G[e] = acc;
+      if (e / R == e % R) ax += mu;
+      G[e] = make_double2(ax, ay);
     } else {
-      h[e - R * R] = acc;
+      h[e - R * R] = make_double2(ax, ay);
     }
   }
 }
@@ -175,14 +183,13 @@ __global__ void mc_coeff_kernel(const float2* __restrict__ F, int n, int R, cons
                                 double hmax, double lf, double* sf, int abar_slot, int alpha_slot,
                                 float* __restrict__ coef) {
   __shared__ double red[kT];
-  double acc = 0.0;
+  float acc = 0.f;   // per-thread sums in FP32 (as the single-coil frame kernel), the tree in FP64
   for (int e = threadIdx.x; e < n * R; e += blockDim.x) {
     const int r = e % R;
-    const float2 v = F[e];
     const double2 g = gamma_d[r];
-    acc += ((double)v.x * v.x + (double)v.y * v.y) * (g.x * g.x + g.y * g.y);
+    acc = fmaf(cabs2(F[e]), (float)(g.x * g.x + g.y * g.y), acc);
   }
-  red[threadIdx.x] = acc;
+  red[threadIdx.x] = (double)acc;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
@@ -456,7 +463,7 @@ int mc_push(tts_handle* h, const tts_c64* y_in, const uint8_t* mask_in, int flag
     rc = tts_fft2d((const tts_c64*)m->Z, (tts_c64*)m->Z, C * R, Nx, Ny, 0, st);
     if (rc != TTS_OK) break;
     mc_gram_kernel<<<C * s, kT, gram_smem, st>>>(m->Z, m->y, p.rows, C, R, Nx, Ny, s, m->part);
-    mc_gram_reduce_kernel<<<(R * R + R + kT - 1) / kT, kT, 0, st>>>(m->part, C * s, R, p.mu, m->G, m->h);
+    mc_gram_reduce_kernel<<<((R * R + R) * 32 + kT - 1) / kT, kT, 0, st>>>(m->part, C * s, R, p.mu, m->G, m->h);
     rc = launch_ridge(m->G, m->h, R, p.gamma_d, st);
     if (rc != TTS_OK) break;
     // (S2) A block
