@@ -109,11 +109,19 @@ typedef struct {
   uint32_t stream_id;       /* enters the line-draw counter so streams draw independently */
   void* cuda_stream;        /* cudaStream_t to enqueue on; NULL = a stream the handle creates */
   int row_dft;              /* TTS_ROWDFT_*: how the acquired rows are transformed each frame */
+  int kspace;               /* 0: image-domain factors (Alg. 3); 1: k-space factors (Alg. 2) */
 } tts_config;
 
 /* Fill cfg with defaults: mm_iters 1, central_lines 8, TTS_POLICY_INFORMATIVE, vd_alpha -1,
  * without replacement, Gauss-Seidel, fused launch, cluster_ctas 0, init_seed 0,
- * stream_id 0, cuda_stream NULL, row_dft TTS_ROWDFT_FFT. */
+ * stream_id 0, cuda_stream NULL, row_dft TTS_ROWDFT_FFT, kspace 0.
+ *
+ * kspace = 1 runs the k-space interpolation tracker of Alg. 2 (§IV-A): the factors are
+ * k-space factors A1 (Nx x R), A2 (Ny x R) with x^(i,j) = <a1_i, a2_j, gamma_t>, each MM
+ * iteration works on the acquired rows directly (no transform in the loop), the line
+ * scores are taken on the rows of A1, and tts_image returns F^{-1}(A1 diag(gamma) A2^T)
+ * (the paper's image is its magnitude). Requires TTS_ROWDFT_FFT and no coil maps; not in
+ * an engine. tts_get_factors / tts_set_factors then read and write A1, A2. */
 void tts_config_init(tts_config* cfg, int Nx, int Ny, int R, double lambda_forget, double mu);
 
 /* Create a tracker (problem (P2) of §III for M = 3: factors A, B of the image-domain

@@ -100,6 +100,8 @@ int handle_check_config(const tts_config* c) {
   if (c->cluster_ctas < 0 || c->cluster_ctas > TTS_MAX_CLUSTER) return fail(TTS_EINVAL, "cluster_ctas must be 0..16%s");
   if (!isfinite(c->vd_alpha)) return fail(TTS_EINVAL, "vd_alpha must be finite%s");
   if (c->row_dft < TTS_ROWDFT_FFT || c->row_dft > TTS_ROWDFT_BF16) return fail(TTS_EINVAL, "unknown row_dft%s");
+  if (c->kspace != 0 && c->kspace != 1) return fail(TTS_EINVAL, "kspace must be 0 or 1%s");
+  if (c->kspace && c->row_dft != TTS_ROWDFT_FFT) return fail(TTS_EINVAL, "the k-space tracker transforms no rows%s");
   if (c->row_dft != TTS_ROWDFT_FFT && !dft_gemm_size_ok(c->Ny))
     return fail(TTS_EINVAL, "the tensor-core row transform needs Ny a multiple of 32 in [32, 256]%s");
   return TTS_OK;
@@ -175,8 +177,9 @@ int handle_create(const tts_config* cfg, void* mem, tts_handle** out) {
   p.jacobi = cfg->update == TTS_UPDATE_JACOBI;
   p.lf = cfg->lambda_forget;
   p.mu = cfg->mu;
-  p.isx = (float)(1.0 / sqrt((double)Nx));
-  p.isy = (float)(1.0 / sqrt((double)Ny));
+  p.kspace = cfg->kspace;
+  p.isx = cfg->kspace ? 1.f : (float)(1.0 / sqrt((double)Nx));
+  p.isy = cfg->kspace ? 1.f : (float)(1.0 / sqrt((double)Ny));
   p.plan_y = fft_plan(Ny);
   std::vector<float2> wx = twiddles(Nx), wy = twiddles(Ny);
   rc = TTS_OK;
@@ -272,6 +275,7 @@ void tts_config_init(tts_config* c, int Nx, int Ny, int R, double lambda_forget,
   c->stream_id = 0;
   c->cuda_stream = nullptr;
   c->row_dft = TTS_ROWDFT_FFT;
+  c->kspace = 0;
 }
 
 int tts_create(int Nx, int Ny, int R, double lambda_forget, double mu, tts_handle** out) {
@@ -353,6 +357,7 @@ int tts_get_config(tts_handle* h, tts_config* cfg) {
 int tts_set_coil_maps(tts_handle* h, const tts_c64* maps, int C, int flags) {
   if (!h) return fail(TTS_EINVAL, "NULL handle%s");
   if (h->in_engine) return fail(TTS_EINVAL, "engine streams are single-coil%s");
+  if (h->cfg.kspace) return fail(TTS_EINVAL, "the k-space tracker is single-coil%s");
   if (flags & ~TTS_DEVICE_PTRS) return fail(TTS_EINVAL, "unknown flags%s");
   if (!maps || C == 0) {
     CK(cudaStreamSynchronize(h->stream));
@@ -395,6 +400,11 @@ int tts_image(tts_handle* h, int64_t t, tts_c64* out, int flags) {
   float2* dst = (flags & TTS_DEVICE_PTRS) ? (float2*)out : h->X;
   int rc = launch_image(h->fp.A, h->fp.B, h->fp.gamma, dst, Nx, Ny, h->cfg.R, h->stream);
   if (rc != TTS_OK) return fail(rc, "image kernel launch failed%s");
+  if (h->cfg.kspace) {
+    // Alg. 2: the interpolated k-space frame back to the image domain
+    rc = tts_fft2d((const tts_c64*)dst, (tts_c64*)dst, 1, Nx, Ny, 1, h->stream);
+    if (rc != TTS_OK) return rc;
+  }
   if (!(flags & TTS_DEVICE_PTRS)) {
     CK(cudaMemcpyAsync(out, h->X, sizeof(float2) * (size_t)Nx * Ny, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -410,7 +420,7 @@ int tts_next_mask(tts_handle* h, double rate, uint64_t seed, uint8_t* line_mask_
   uint8_t* out2 = (flags & TTS_DEVICE_PTRS) ? line_mask_out : nullptr;
   int rc = launch_sampler(h->fp.A, Nx, h->cfg.Ny, h->cfg.R, nullptr, h->dp, h->cfg.policy, h->cfg.vd_alpha, k_lines,
                           h->cfg.central_lines, seed, handle_draw_counter(h), h->cfg.with_replacement, h->fp.Wx,
-                          h->dmask_next, out2, h->stream);
+                          h->dmask_next, out2, h->stream, h->cfg.kspace);
   if (rc != TTS_OK) return fail(rc, "sampler kernel launch failed%s");
   h->have_next = true;
   if (flags & TTS_DEVICE_PTRS) {
@@ -429,7 +439,7 @@ int tts_line_probs(tts_handle* h, double* p, int flags) {
   const int Nx = h->cfg.Nx;
   double* dst = (flags & TTS_DEVICE_PTRS) ? p : h->dp;
   int rc = launch_sampler(h->fp.A, Nx, h->cfg.Ny, h->cfg.R, nullptr, dst, h->cfg.policy, h->cfg.vd_alpha, 0,
-                          h->cfg.central_lines, 0, 0, 0, h->fp.Wx, h->dmask_next, nullptr, h->stream);
+                          h->cfg.central_lines, 0, 0, 0, h->fp.Wx, h->dmask_next, nullptr, h->stream, h->cfg.kspace);
   if (rc != TTS_OK) return fail(rc, "sampler kernel launch failed%s");
   if (!(flags & TTS_DEVICE_PTRS)) {
     CK(cudaMemcpyAsync(p, h->dp, sizeof(double) * Nx, cudaMemcpyDeviceToHost, h->stream));

@@ -366,6 +366,7 @@ int tts_engine_admit(tts_engine* e, const tts_config* cfg, int* slot_out) {
   int rc = handle_check_config(&c);
   if (rc) return rc;
   if (c.row_dft != TTS_ROWDFT_FFT) return tts_fail(TTS_EINVAL, "engine streams transform rows in the frame kernel%s");
+  if (c.kspace) return tts_fail(TTS_EINVAL, "engine streams track image-domain factors%s");
   // the preferred cluster size, else the next larger one that holds the stream's layout
   int C = 0;
   const size_t need = engine_footprint(c, e->C, &C);

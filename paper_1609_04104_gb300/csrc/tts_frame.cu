@@ -331,8 +331,13 @@ __device__ __forceinline__ void fill_twiddles(const FrameParams& p, SM& sm, floa
                                               int nrows) {
   for (int e = threadIdx.x; e < mc * nrows; e += blockDim.x) {
     const int mm = e / nrows, nl = e - mm * nrows;
-    const int idx = (sm.rows[m0 + mm] * (lo + nl)) % p.Nx;
-    TW[e] = sm.Wx[idx];
+    if (p.kspace) {
+      // k-space factors: F_Nx[S, :] becomes the row selection of S
+      TW[e] = make_float2(sm.rows[m0 + mm] == lo + nl ? 1.f : 0.f, 0.f);
+    } else {
+      const int idx = (sm.rows[m0 + mm] * (lo + nl)) % p.Nx;
+      TW[e] = sm.Wx[idx];
+    }
   }
 }
 
@@ -490,7 +495,7 @@ __device__ void step_ingest(const FrameParams& p, SM& sm, int cta) {
       }
     }
     __syncthreads();
-    float2* res = fft_smem(buf, tmp, p.plan_y, nr, bsy, sm.Wy, +1, tid, nth);
+    float2* res = p.kspace ? buf : fft_smem(buf, tmp, p.plan_y, nr, bsy, sm.Wy, +1, tid, nth);
     for (int e = tid; e < nr * Ny; e += nth) {
       const int mr = e / Ny;
       p.Yt[(size_t)m0 * Ny + e] = cscale(res[mr * bsy + fpad(e - mr * Ny)], p.isy);

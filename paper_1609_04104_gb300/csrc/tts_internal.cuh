@@ -356,6 +356,7 @@ struct FrameParams {
   const float2* yrows;            // |S| x Ny acquired rows (or the full Nx x Ny frame)
   int full_frame;                 // yrows is the full frame: row m of S is yrows[rows[m]]
   int yt_ready;                   // Yt was formed before the launch (tensor-core row transform)
+  int kspace;                     // k-space factors (Alg. 2): selection instead of F_Nx[S,:], rows untransformed
   float2* Yt;                     // |S| x Ny: acquired rows times conj(F_Ny)
   int* rows;                      // S, increasing
   int* nrows;                     // |S|
@@ -397,6 +398,7 @@ struct SamplerJob {
   uint8_t* mask_out;
   uint8_t* mask_out2;   // optional second copy, or NULL
   int fft_cols;         // columns of A transformed together
+  int no_fft;           // scores on the rows of A itself (k-space factor)
 };
 
 // One image X = A diag(gamma) B^T as a job of a batched launch: tiles [tile0, tile0 + tiles).
@@ -428,7 +430,7 @@ int launch_image(const float2* A, const float2* B, const float2* gamma, float2* 
                  cudaStream_t st);
 int launch_sampler(const float2* A, int Nx, int Ny, int R, const double* p_in, double* p_out, int policy,
                    double vd_alpha, int k_lines, int central, uint64_t seed, uint64_t ctr, int with_replacement,
-                   const float2* Wx, uint8_t* mask_out, uint8_t* mask_out2, cudaStream_t st);
+                   const float2* Wx, uint8_t* mask_out, uint8_t* mask_out2, cudaStream_t st, int no_fft = 0);
 void tts_internal_set_error(const char* msg);   // message returned by tts_last_error
 int launch_fft2d(const float2* in, float2* out, int batch, int Nx, int Ny, int inverse, const float2* Wx,
                  const float2* Wy, float2* scratch, cudaStream_t st);

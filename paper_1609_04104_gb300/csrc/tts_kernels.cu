@@ -165,7 +165,7 @@ __device__ __forceinline__ void sampler_run(const SamplerJob& job, unsigned char
         }
       }
       __syncthreads();
-      float2* res = fft_smem(buf, buf + fft_cols * ld, plan, nc, ld, W, -1, tid, blockDim.x);
+      float2* res = job.no_fft ? buf : fft_smem(buf, buf + fft_cols * ld, plan, nc, ld, W, -1, tid, blockDim.x);
       for (int c = warp; c < nc; c += nwarp) {
         float acc = 0.f;
         for (int n = lane; n < Nx; n += 32) acc += cabs2(res[c * ld + fpad(n)]);
@@ -469,6 +469,7 @@ SamplerJob sampler_job(const float2* A, int Nx, int Ny, int R, const double* p_i
   j.mask_out = mask_out;
   j.mask_out2 = mask_out2;
   j.fft_cols = max(1, min(min(R, 64), 8192 / max(Nx, 1)));
+  j.no_fft = 0;
   return j;
 }
 
@@ -491,9 +492,10 @@ int launch_image_batch(const ImageJob* jobs, const int* n, int grid, cudaStream_
 
 int launch_sampler(const float2* A, int Nx, int Ny, int R, const double* p_in, double* p_out, int policy,
                    double vd_alpha, int k_lines, int central, uint64_t seed, uint64_t ctr, int with_replacement,
-                   const float2* Wx, uint8_t* mask_out, uint8_t* mask_out2, cudaStream_t st) {
-  const SamplerJob j = sampler_job(A, Nx, Ny, R, p_in, p_out, policy, vd_alpha, k_lines, central, seed, ctr,
-                                   with_replacement, Wx, mask_out, mask_out2);
+                   const float2* Wx, uint8_t* mask_out, uint8_t* mask_out2, cudaStream_t st, int no_fft) {
+  SamplerJob j = sampler_job(A, Nx, Ny, R, p_in, p_out, policy, vd_alpha, k_lines, central, seed, ctr,
+                             with_replacement, Wx, mask_out, mask_out2);
+  j.no_fft = no_fft;
   const size_t smem = sampler_smem(Nx, j.fft_cols);
   cudaError_t e = cudaFuncSetAttribute(sampler_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return TTS_ECUDA;

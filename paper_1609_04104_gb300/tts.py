@@ -53,6 +53,7 @@ class tts_config(ctypes.Structure):
         ("vd_alpha", ctypes.c_double), ("with_replacement", ctypes.c_int), ("update", ctypes.c_int),
         ("launch", ctypes.c_int), ("cluster_ctas", ctypes.c_int), ("init_seed", ctypes.c_uint64),
         ("stream_id", ctypes.c_uint32), ("cuda_stream", ctypes.c_void_p), ("row_dft", ctypes.c_int),
+        ("kspace", ctypes.c_int),
     ]
 
 
