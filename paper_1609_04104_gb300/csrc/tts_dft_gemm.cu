@@ -11,17 +11,20 @@
 // hi + lo with hi = bf16(v), lo = bf16(v - hi) and accumulates hi*hi + hi*lo + lo*hi in FP32
 // (the lo*lo term, ~2^-16 relative, is dropped); plain precision uses hi*hi only.
 //
-// Kernel: one CTA of 128 threads per 128 rows. K' is consumed in chunks of 32 through two
-// shared-memory stages: the threads load the fp32 rows (coalesced), split them to bf16 and
-// store them in the canonical K-major no-swizzle layout (8 x 16-byte core matrices, 128 B
-// each); the DFT-matrix chunk, pre-arranged in that layout in global memory, arrives by one
-// bulk copy per operand on an mbarrier. One thread issues the tcgen05.mma instructions
-// (M = 128, N' up to 256 per accumulator, two accumulators for N' = 2N > 256, K = 16 each)
-// into tensor memory and commits them to the stage's mbarrier, which frees the stage for
-// the chunk after next. The epilogue reads the accumulators with tcgen05.ld (warp w owns
-// TMEM lanes 32w..32w+31 = rows) and writes complex outputs transposed, 256 contiguous
-// bytes per warp and output column. Every mbarrier wait is bounded; on timeout the CTA
-// records an error and stops issuing work.
+// Kernel: one CTA of 8 warps per 128 rows, warp-specialised on mbarriers. K' is consumed in
+// chunks of 16 (one MMA K step) through four shared-memory stages:
+//   - producer warp w (w < 4) fills stage w with chunks w, w + 4, ...: it loads the chunk's
+//     fp32 rows (16 float4 per lane at once, so four chunks are in flight), splits them to
+//     bf16 and stores them in the canonical K-major no-swizzle layout (8 x 16-byte core
+//     matrices, 128 B each); its lane 0 bulk-copies the DFT-matrix chunk (pre-arranged in
+//     that layout in global memory) on the stage's "full" barrier; the warp then arrives;
+//   - lane 0 of warp 4 waits for a full stage, issues the tcgen05.mma instructions (M = 128,
+//     N' up to 256 per accumulator, two accumulators for N' = 2N > 256) into tensor memory
+//     and commits them to the stage's "empty" barrier, which lets the producer refill it;
+//   - after the last commit all warps read the accumulators with tcgen05.ld (warp w owns
+//     TMEM lanes 32 (w mod 4)..) and write complex outputs transposed, 256 contiguous bytes
+//     per warp and output column.
+// Every mbarrier wait is bounded; on timeout the CTA records an error and every role stops.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
@@ -36,9 +39,11 @@
 namespace {
 
 constexpr int kRows = 128;     // rows per CTA (UMMA M)
-constexpr int kKC = 32;        // K' chunk (bf16 elements) per stage
+constexpr int kKC = 16;        // K' chunk (bf16 elements) per stage: one MMA K step
 constexpr int kThreads = 256;   // 8 warps: warp w and w + 4 share TMEM lanes 32 (w % 4).. in the epilogue
-constexpr int kStages = 2;
+constexpr int kStages = 4;     // one per producer warp
+constexpr int kProducers = 4;  // warps 0..3 load and split the A rows; warp w fills stage w
+constexpr int kIssuer = 4;     // lane 0 of warp 4 issues the MMAs
 
 // Shared-memory matrix descriptor (tcgen05): start address, leading-dimension byte offset
 // (between core matrices along K) and stride byte offset (between 8-row groups), all >> 4;
@@ -98,20 +103,27 @@ struct GemmArgs {
   int full_frame;
 };
 
-// Shared memory of one CTA (bytes): per stage A_hi, A_lo (128 x 32 bf16 = 8 KB each) and
-// B_hi, B_lo (N' x 32 bf16 each); then the mbarriers and the TMEM address slot.
-__host__ __device__ inline int stage_bytes(int N) { return 2 * (kRows * kKC * 2) + 2 * (2 * N * kKC * 2); }
+// Shared memory of one CTA (bytes): per stage A_hi, A_lo (128 x 16 bf16 = 4 KB each) and
+// B_hi, B_lo (N' x 16 bf16 each); then the mbarriers and the TMEM address slot.
+__host__ __device__ inline int a_bytes() { return kRows * kKC * 2; }
+__host__ __device__ inline int b_bytes(int N) { return 2 * N * kKC * 2; }
+__host__ __device__ inline int stage_bytes(int N) { return 2 * a_bytes() + 2 * b_bytes(N); }
+
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
 
 __global__ void __launch_bounds__(kThreads, 1) dft_gemm_kernel(GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int N = g.N, Np = 2 * N, NT = Np / g.nh;
   const int SB = stage_bytes(N);
-  uint64_t* bars = (uint64_t*)(smem + kStages * SB);   // full[2], empty[2], done
-  uint32_t* slot = (uint32_t*)(bars + 8);
+  uint64_t* bars = (uint64_t*)(smem + kStages * SB);   // full[S], empty[S], done
+  uint32_t* slot = (uint32_t*)(bars + 2 * kStages + 2);
   __shared__ int abort_flag;
   __shared__ int srows[TTS_MAX_N];
   __shared__ int scount;
+  volatile int* abort_v = &abort_flag;
   int M = g.M;
   if (g.mask) {
     // compact the line mask into the increasing list S (warp 0)
@@ -130,15 +142,15 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm_kernel(GemmArgs g) {
     M = scount;
     if ((int)blockIdx.x * kRows >= M) return;   // uniform: the whole CTA has no rows
   }
-  const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[2]), done = smem_u32(&bars[4]);
+  const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[kStages]), done = smem_u32(&bars[2 * kStages]);
   if (tid == 0) {
     abort_flag = 0;
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, 1);
+      mbar_init(full0 + 8 * s, 2);    // the producer warp, and the B copy's arrival with its bytes
+      mbar_init(empty0 + 8 * s, 1);   // the MMA commit
     }
     mbar_init(done, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_mbar_init();
   }
   const uint32_t ncols = g.nh == 1 ? 256u : 512u;
   if (warp == 0) {
@@ -155,93 +167,92 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm_kernel(GemmArgs g) {
   const int m0 = blockIdx.x * kRows;
   const int nK = Np / kKC;
   const uint32_t idesc = instr_desc(NT, kRows);
-  const size_t bchunk = (size_t)Np * kKC * 2;   // bytes of one K' chunk of the embedding (all N')
-  // A chunk: 128 rows x 32 floats (16 complex), 8 threads per row, one float4 each, four per
-  // thread; the next chunk's values are loaded while the current chunk's products run
-  constexpr int kPer = kRows * kKC / 4 / kThreads;
-  float4 pre[kPer];
-  auto load_chunk = [&](int kc) {
-#pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-      const int idx = tid + kThreads * u;
-      const int r = idx >> 3, q = idx & 7;
-      const int m = m0 + r;
-      const int src = (g.mask && g.full_frame && m < M) ? srows[m] : m;
-      pre[u] = m < M ? *(const float4*)((const float*)(g.x + (size_t)src * N) + kc * kKC + 4 * q)
-                     : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-  };
-  load_chunk(0);
-  bool ok = true;
-  for (int kc = 0; kc < nK; ++kc) {
-    const int s = kc & 1, use = kc >> 1;
+  const uint32_t bchunk = (uint32_t)b_bytes(N);   // bytes of one K' chunk of the embedding (all N')
+  if (warp < kProducers) {
+    // producer warp w: chunks w, w + 4, ... into stage w (128 rows x 16 floats; a lane
+    // loads 16 float4 at once, so four chunks are in flight across the producer warps)
+    const int s = warp;
     unsigned char* st = smem + s * SB;
     unsigned char* ahi = st;
-    unsigned char* alo = st + kRows * kKC * 2;
-    unsigned char* bhi = st + 2 * kRows * kKC * 2;
-    unsigned char* blo = bhi + Np * kKC * 2;
-    if (kc >= kStages && ok) ok = mbar_wait(empty0 + 8 * s, (use - 1) & 1);
-    if (!ok) abort_flag = 1;
-    __syncthreads();
-    if (abort_flag) break;
-    if (tid == 0) {
-      mbar_expect_tx(full0 + 8 * s, (uint32_t)(g.split ? 2 * bchunk : bchunk));
-      bulk_g2s(smem_u32(bhi), (const char*)g.bhi + kc * bchunk, (uint32_t)bchunk, full0 + 8 * s);
-      if (g.split) bulk_g2s(smem_u32(blo), (const char*)g.blo + kc * bchunk, (uint32_t)bchunk, full0 + 8 * s);
-    }
-#pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-      const int idx = tid + kThreads * u;
-      const int r = idx >> 3, q = idx & 7;
-      const float4 v = pre[u];
-      const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
-      // byte offset: 8-row group (r / 8) x 512, core matrix along K (q / 2) x 128, row (r % 8) x 16, half (q % 2) x 8
-      const int off = (r >> 3) * 512 + (q >> 1) * 128 + (r & 7) * 16 + (q & 1) * 8;
-      uint2 hv;
-      hv.x = *(const uint32_t*)&h01;
-      hv.y = *(const uint32_t*)&h23;
-      *(uint2*)(ahi + off) = hv;
-      if (g.split) {
-        const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
-        const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
-        const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
-        uint2 lv;
-        lv.x = *(const uint32_t*)&l01;
-        lv.y = *(const uint32_t*)&l23;
-        *(uint2*)(alo + off) = lv;
-      }
-    }
-    if (kc + 1 < nK) load_chunk(kc + 1);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      if (!mbar_wait(full0 + 8 * s, use & 1)) {
+    unsigned char* alo = st + a_bytes();
+    unsigned char* bhi = st + 2 * a_bytes();
+    unsigned char* blo = bhi + b_bytes(N);
+    for (int kc = s, use = 0; kc < nK; kc += kStages, ++use) {
+      if (use > 0 && (*abort_v || !mbar_wait(empty0 + 8 * s, (use - 1) & 1))) {
         abort_flag = 1;
-      } else {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a_hi = smem_u32(ahi), a_lo = smem_u32(alo);
-        const uint32_t b_hi = smem_u32(bhi), b_lo = smem_u32(blo);
+        break;
+      }
+      if (lane == 0) {
+        mbar_expect_tx(full0 + 8 * s, g.split ? 2 * bchunk : bchunk);
+        bulk_g2s(smem_u32(bhi), (const char*)g.bhi + (size_t)kc * bchunk, bchunk, full0 + 8 * s);
+        if (g.split) bulk_g2s(smem_u32(blo), (const char*)g.blo + (size_t)kc * bchunk, bchunk, full0 + 8 * s);
+      }
+      float4 v[16];
 #pragma unroll
-        for (int ks = 0; ks < kKC / 16; ++ks) {
-          const uint64_t dah = smem_desc(a_hi + ks * 256, 128, 512);
-          const uint64_t dal = smem_desc(a_lo + ks * 256, 128, 512);
-          for (int h = 0; h < g.nh; ++h) {
-            const uint32_t boff = h * NT * kKC * 2 + ks * 256;
-            const uint64_t dbh = smem_desc(b_hi + boff, 128, 512);
-            const uint32_t d = tmem + h * 256;
-            umma(d, dah, dbh, idesc, (kc | ks) != 0);
-            if (g.split) {
-              const uint64_t dbl = smem_desc(b_lo + boff, 128, 512);
-              umma(d, dah, dbl, idesc, 1);
-              umma(d, dal, dbh, idesc, 1);
-            }
+      for (int u = 0; u < 16; ++u) {
+        const int idx = lane + 32 * u;
+        const int r = idx >> 2, q = idx & 3;
+        const int m = m0 + r;
+        const int src = (g.mask && g.full_frame && m < M) ? srows[m] : m;
+        v[u] = m < M ? *(const float4*)((const float*)(g.x + (size_t)src * N) + kc * kKC + 4 * q)
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int idx = lane + 32 * u;
+        const int r = idx >> 2, q = idx & 3;
+        // byte offset: 8-row group (r / 8) x 256, core matrix along K (q / 2) x 128, row (r % 8) x 16, half (q % 2) x 8
+        const int off = (r >> 3) * 256 + (q >> 1) * 128 + (r & 7) * 16 + (q & 1) * 8;
+        const __nv_bfloat162 h01 = __floats2bfloat162_rn(v[u].x, v[u].y), h23 = __floats2bfloat162_rn(v[u].z, v[u].w);
+        uint2 hv;
+        hv.x = *(const uint32_t*)&h01;
+        hv.y = *(const uint32_t*)&h23;
+        *(uint2*)(ahi + off) = hv;
+        if (g.split) {
+          const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+          const __nv_bfloat162 l01 = __floats2bfloat162_rn(v[u].x - f01.x, v[u].y - f01.y);
+          const __nv_bfloat162 l23 = __floats2bfloat162_rn(v[u].z - f23.x, v[u].w - f23.y);
+          uint2 lv;
+          lv.x = *(const uint32_t*)&l01;
+          lv.y = *(const uint32_t*)&l23;
+          *(uint2*)(alo + off) = lv;
+        }
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(full0 + 8 * s);
+    }
+  } else if (warp == kIssuer) {
+    if (lane == 0) {
+      for (int kc = 0; kc < nK; ++kc) {
+        const int s = kc % kStages, use = kc / kStages;
+        if (*abort_v || !mbar_wait(full0 + 8 * s, use & 1)) {
+          abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        unsigned char* st = smem + s * SB;
+        const uint32_t a_hi = smem_u32(st), a_lo = a_hi + a_bytes();
+        const uint32_t b_hi = a_hi + 2 * a_bytes(), b_lo = b_hi + b_bytes(N);
+        const uint64_t dah = smem_desc(a_hi, 128, 256);
+        const uint64_t dal = smem_desc(a_lo, 128, 256);
+        for (int h = 0; h < g.nh; ++h) {
+          const uint32_t boff = h * NT * kKC * 2;
+          const uint64_t dbh = smem_desc(b_hi + boff, 128, 256);
+          const uint32_t d = tmem + h * 256;
+          umma(d, dah, dbh, idesc, kc != 0);
+          if (g.split) {
+            const uint64_t dbl = smem_desc(b_lo + boff, 128, 256);
+            umma(d, dah, dbl, idesc, 1);
+            umma(d, dal, dbh, idesc, 1);
           }
         }
         umma_commit(empty0 + 8 * s);
       }
+      umma_commit(done);   // arrives once every MMA issued above has completed
     }
+    __syncwarp();
   }
-  if (tid == 0) umma_commit(done);   // arrives once every MMA issued above has completed
   const bool fin = mbar_wait(done, 0);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncthreads();
@@ -297,8 +308,8 @@ float bf16_float(uint16_t b) {
 }
 
 // The real 2N x 2N embedding of W = N^{-1/2} exp(-+2 pi i jk / N), as rows c (output,
-// N' = 2N) and columns k' (input, K' = 2N), laid out chunk by chunk (32 columns k') in the
-// canonical K-major no-swizzle layout: byte (c / 8) * 512 + (k'_in_chunk / 8) * 128 +
+// N' = 2N) and columns k' (input, K' = 2N), laid out chunk by chunk (16 columns k') in the
+// canonical K-major no-swizzle layout: byte (c / 8) * 256 + (k'_in_chunk / 8) * 128 +
 // (c % 8) * 16 + (k'_in_chunk % 8) * 2 within the chunk.
 int embedding(int N, int inverse, const uint4** hi, const uint4** lo) {
   int dev = 0;
@@ -327,7 +338,7 @@ int embedding(int N, int inverse, const uint4** hi, const uint4** lo) {
       const uint16_t h = bf16_bits(f);
       const uint16_t l = bf16_bits(f - bf16_float(h));
       const int kc = kp / kKC, kk = kp % kKC;
-      const size_t idx = (size_t)kc * chunk + (size_t)(c >> 3) * 256 + (kk >> 3) * 64 + (c & 7) * 8 + (kk & 7);
+      const size_t idx = (size_t)kc * chunk + (size_t)(c >> 3) * (8 * kKC) + (kk >> 3) * 64 + (c & 7) * 8 + (kk & 7);
       H[idx] = h;
       L[idx] = l;
     }
