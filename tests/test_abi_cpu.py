@@ -57,6 +57,13 @@ def test_no_cpu_fallback_without_a_gpu():
         tts.tts_create(64, 64, 8, 0.9, 1e-2)
     assert e.value.code == tts.TTS_ECUDA
     assert "no CPU fallback" in tts.tts_last_error() or "CUDA" in tts.tts_last_error()
+    with pytest.raises(tts.TtsError) as e:
+        tts.tts_engine_create(1 << 24, 4)
+    assert e.value.code == tts.TTS_ECUDA
+    cfg = tts.tts_config_init(64, 64, 8, 0.9, 1e-2)
+    with pytest.raises(tts.TtsError) as e:
+        tts.tts_engine_autotune([cfg], steps=1)
+    assert e.value.code in (tts.TTS_ECUDA, tts.TTS_EINVAL)
 
 
 def test_input_recipe_shapes_and_masks():
