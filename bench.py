@@ -267,12 +267,16 @@ def run_tts(args, rank, world):
         nrmse_plain = worst
         plain.close()
 
-    # end to end through the C ABI with host buffers (pinned)
+    # end to end through the C ABI with host buffers (pinned): per frame the drawn lines come
+    # back to the host (the scanner needs them before it acquires the frame), the acquired
+    # rows go to the device, and the image comes back to the host asynchronously (its copy
+    # overlaps the next frame; every image is on the host when the step ends)
     e2e = None
     if not args.no_e2e:
         Yp = torch.from_numpy(Yh).pin_memory().numpy()
-        stage = torch.empty((w.Nx, w.Ny), dtype=torch.complex64).pin_memory().numpy()
-        out = torch.empty((w.Nx, w.Ny), dtype=torch.complex64).pin_memory().numpy()
+        stage = torch.empty((T, w.Nx, w.Ny), dtype=torch.complex64).pin_memory().numpy()
+        himg = torch.empty((T, w.Nx, w.Ny), dtype=torch.complex64).pin_memory()
+        dimg = torch.empty((T, w.Nx, w.Ny), dtype=torch.complex64, device=f"cuda:{dev}")
         mh = torch.empty(w.Nx, dtype=torch.uint8).pin_memory().numpy()
         full = np.ones(w.Nx, np.uint8)
         e2e_s, h2d, d2h = [], 0, 0
@@ -281,26 +285,29 @@ def run_tts(args, rank, world):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             hb = db = 0
-            for t in range(T):
-                if t < w.warmup_frames:
-                    m = full
-                else:
-                    trk.next_mask(w.rate, seed, out=mh)
-                    m = mh
-                    db += w.Nx
-                rows = np.flatnonzero(m)
-                s = len(rows)
-                np.take(Yp[t], rows, axis=0, out=stage[:s])
-                trk.push_frame(stage[:s], m)
-                hb += s * w.Ny * 8 + w.Nx
-                trk.image(t, out=out)
-                db += w.Nx * w.Ny * 8
+            with torch.cuda.stream(stream):
+                for t in range(T):
+                    if t < w.warmup_frames:
+                        m = full
+                    else:
+                        trk.next_mask(w.rate, seed, out=mh)
+                        m = mh
+                        db += w.Nx
+                    rows = np.flatnonzero(m)
+                    s = len(rows)
+                    np.take(Yp[t], rows, axis=0, out=stage[t, :s])
+                    trk.push_frame(stage[t, :s], m)
+                    hb += s * w.Ny * 8 + w.Nx
+                    tts.tts_image(trk.h, t, dimg[t])
+                    himg[t].copy_(dimg[t], non_blocking=True)
+                    db += w.Nx * w.Ny * 8
             torch.cuda.synchronize()
             if it >= args.warmup:
                 e2e_s.append(time.perf_counter() - t0)
                 h2d, d2h = hb, db
         e2e = {"value": T * world / float(np.mean(e2e_s)), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
+               "d2h_bytes_per_step": d2h,
+               "note": "host lines back every frame (synchronous), rows in, images out asynchronously"}
 
     # roofline of the dominant kernel (the frame kernel), FP32 ALU bound
     kmean = float(np.mean(kern_ms)) * 1e-3
@@ -612,6 +619,9 @@ def run_batched(args):
         e2e = {"value": n * T / el, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "note": "one step = one frame of every stream; full host frames in, every image out"}
     eng.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = batched_cpu_baseline(ws, cfgs, slot_C, banks, F, stream)
 
     flops_step = float(np.mean([sum(frame_flops(w.Nx, w.Ny, w.R, w.mm_iters, w.Nx if t < w.warmup_frames else
                                                 w.k_lines) for w in ws) for t in range(T)]))
@@ -639,12 +649,51 @@ def run_batched(args):
         "engine": info,
         "e2e": e2e,
         "gpu_launches": 3 * T,
+        "cpu_baseline": cpu,
         "roofline": {"bound": "alu", "kernel": "engine step (frame_batch_kernel + image + sampler)",
                      "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                      "traffic": None, "flops_per_step": flops_step,
                      "peak_note": "FP32 SIMT peak 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived)"},
         "clocks": clk,
     }
+
+
+def batched_cpu_baseline(ws, cfgs, slot_C, banks, F, stream):
+    """Oracle spot check on sampled streams of the uneven mix: a stream runs alone through
+    its handle at its engine cluster size (bit-identical to its engine run), recording its
+    lines; the FP64 oracle (timed on the host cores) runs the same frames with the same
+    lines from the same initial factors; per-frame image NRMSE."""
+    import torch
+
+    from oracle import tracker as O
+    from paper_1609_04104_gb300 import tts
+    picks = [0, len(ws) // 2]
+    n_frames = 6
+    worst, el, frames = 0.0, 0.0, 0
+    for k in picks:
+        w = ws[k]
+        trk = tts.Tracker(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, cluster_ctas=slot_C[k], cuda_stream=stream,
+                          **cfgs[k])
+        A0 = np.zeros((w.Nx, w.R), np.complex64)
+        B0 = np.zeros((w.Ny, w.R), np.complex64)
+        tts.tts_get_factors(trk.h, A0, B0)
+        ora = O.Tracker(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, w.mm_iters, A=A0, B=B0)
+        bank = banks[(w.Nx, w.Ny)].cpu().numpy()
+        for t in range(n_frames):
+            m = np.ones(w.Nx, np.uint8) if t < w.warmup_frames else trk.next_mask(w.rate, w.seed + 1000)
+            rows = np.ascontiguousarray(bank[t % F][np.flatnonzero(m)])
+            trk.push_frame(rows, m)
+            x = trk.image(t)
+            t0 = time.perf_counter()
+            ref = ora.push_frame(rows, m)
+            el += time.perf_counter() - t0
+            frames += 1
+            worst = max(worst, O.nrmse(x, ref))
+        trk.close()
+    return {"value": frames / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"frames 0-{n_frames - 1} of streams {picks} "
+                      f"({', '.join(ws[k].name for k in picks)}), the GPU's lines",
+            "image_nrmse_vs_oracle": worst}
 
 
 def run_serve(args):
