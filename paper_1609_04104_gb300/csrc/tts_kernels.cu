@@ -10,10 +10,13 @@ namespace {
 // X = A diag(gamma) B^T  (the image of the most recent frame, cf. §IV-A X_t)
 // 32 x 32 output tile per CTA; A and B rows of the tile staged in shared memory.
 // ------------------------------------------------------------------------------------
+// One TR x 32 tile of X (TR in {8, 32}) by 256 threads. Every output sums its R terms in
+// the order r = 0 .. R - 1, so the tile shape does not change a single bit of X.
+template <int TR>
 __device__ __forceinline__ void image_tile(const float2* __restrict__ A, const float2* __restrict__ B,
                                            const float2* __restrict__ gamma, float2* __restrict__ X, int Nx, int Ny,
                                            int R, int i0, int j0, unsigned char* smem_raw) {
-  float2* sA = (float2*)smem_raw;     // 32 x (R+1), A[i][r] gamma_r
+  float2* sA = (float2*)smem_raw;     // TR x (R+1), A[i][r] gamma_r
   float2* sB = sA + 32 * (R + 1);     // 32 x (R+1)
   const int tid = threadIdx.x;
   for (int base = tid; base < 32 * R; base += 4 * blockDim.x) {
@@ -24,7 +27,7 @@ __device__ __forceinline__ void image_tile(const float2* __restrict__ A, const f
       if (e < 32 * R) {
         const int ii = e / R, r = e - ii * R;
         const int i = i0 + ii, j = j0 + ii;
-        va[u] = i < Nx ? A[i * R + r] : make_float2(0.f, 0.f);
+        va[u] = (ii < TR && i < Nx) ? A[i * R + r] : make_float2(0.f, 0.f);
         vb[u] = j < Ny ? B[j * R + r] : make_float2(0.f, 0.f);
         vg[u] = gamma[r];
       }
@@ -34,30 +37,35 @@ __device__ __forceinline__ void image_tile(const float2* __restrict__ A, const f
       const int e = base + u * blockDim.x;
       if (e < 32 * R) {
         const int ii = e / R, r = e - ii * R;
-        sA[ii * (R + 1) + r] = cmul(va[u], vg[u]);
+        if (ii < TR) sA[ii * (R + 1) + r] = cmul(va[u], vg[u]);
         sB[ii * (R + 1) + r] = vb[u];
       }
     }
   }
   __syncthreads();
-  const int jj = tid & 31, ib = tid >> 5;  // each thread: column jj, rows ib, ib+8, ib+16, ib+24
-  float2 acc[4];
-  for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
+  constexpr int Q = TR / 8;
+  const int jj = tid & 31, ib = tid >> 5;  // each thread: column jj, rows ib, ib+8, ... (Q rows)
+  float2 acc[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) acc[q] = make_float2(0.f, 0.f);
   for (int r = 0; r < R; ++r) {
     const float2 b = sB[jj * (R + 1) + r];
-    for (int q = 0; q < 4; ++q) cfma(acc[q], sA[(ib + 8 * q) * (R + 1) + r], b);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) cfma(acc[q], sA[(ib + 8 * q) * (R + 1) + r], b);
   }
-  for (int q = 0; q < 4; ++q) {
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
     const int i = i0 + ib + 8 * q, j = j0 + jj;
     if (i < Nx && j < Ny) X[(size_t)i * Ny + j] = acc[q];
   }
 }
 
+template <int TR>
 __global__ void __launch_bounds__(256) image_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
                                                     const float2* __restrict__ gamma, float2* __restrict__ X,
                                                     int Nx, int Ny, int R) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  image_tile(A, B, gamma, X, Nx, Ny, R, blockIdx.y * 32, blockIdx.x * 32, smem_raw);
+  image_tile<TR>(A, B, gamma, X, Nx, Ny, R, blockIdx.y * TR, blockIdx.x * 32, smem_raw);
 }
 
 // Images of many trackers: the 32 x 32 tiles of all jobs form one list (job k owns tiles
@@ -78,7 +86,7 @@ __global__ void __launch_bounds__(256) image_batch_kernel(const ImageJob* __rest
     const ImageJob& j = jobs[lo];
     const int tl = t - j.tile0, tx = (j.Ny + 31) / 32;
     const int ti = tl / tx, tj = tl - ti * tx;
-    image_tile(j.A, j.B, j.gamma, j.X, j.Nx, j.Ny, j.R, ti * 32, tj * 32, smem_raw);
+    image_tile<32>(j.A, j.B, j.gamma, j.X, j.Nx, j.Ny, j.R, ti * 32, tj * 32, smem_raw);
     __syncthreads();
   }
 }
@@ -442,9 +450,23 @@ __global__ void __launch_bounds__(256) fft_cols_kernel(float2* data, int Nx, int
 
 int launch_image(const float2* A, const float2* B, const float2* gamma, float2* X, int Nx, int Ny, int R,
                  cudaStream_t st) {
+  // 32-row tiles while they fill every SM, else 8-row tiles (four times the CTAs)
   const int smem = 2 * 32 * (R + 1) * (int)sizeof(float2);
-  dim3 grid((Ny + 31) / 32, (Nx + 31) / 32);
-  image_kernel<<<grid, 256, smem, st>>>(A, B, gamma, X, Nx, Ny, R);
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return TTS_ECUDA;
+  }
+  const int tiles32 = ((Ny + 31) / 32) * ((Nx + 31) / 32);
+  if (tiles32 >= sms) {
+    dim3 grid((Ny + 31) / 32, (Nx + 31) / 32);
+    image_kernel<32><<<grid, 256, smem, st>>>(A, B, gamma, X, Nx, Ny, R);
+  } else {
+    dim3 grid((Ny + 31) / 32, (Nx + 7) / 8);
+    image_kernel<8><<<grid, 256, smem, st>>>(A, B, gamma, X, Nx, Ny, R);
+  }
   return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
 }
 
