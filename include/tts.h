@@ -84,7 +84,8 @@ enum {
 /* The per-frame inverse DFT of the acquired rows along the readout axis (Yt = y_S conj(F_Ny),
  * the data side of the separable form of Alg. 3): in the frame kernel by a shared-memory
  * Stockham FFT in FP32 (default), or by the tensor-core matrix product of tts_dft2d_gemm
- * before it (Ny a multiple of 32 in [32, 256]; not in an engine). */
+ * before it (Ny a multiple of 32 in [32, 256]; not in an engine; device frames passed to
+ * tts_push_frame then 16-byte aligned, TTS_EINVAL otherwise). */
 enum {
   TTS_ROWDFT_FFT = 0,
   TTS_ROWDFT_BF16X3 = 1,   /* bf16 hi + lo split operands, FP32 accumulation */
@@ -232,8 +233,8 @@ int tts_ridge_solve(const double* G, const double* h, int R, double* gamma);
 
 /* Batched unitary 2D DFT (forward: F_Nx X F_Ny; inverse: conj(F_Nx) X conj(F_Ny))
  * of `batch` row-major Nx x Ny complex images, device pointers, on `cuda_stream`
- * (NULL = default stream). in == out is allowed. Nx, Ny in [1, 512] with prime factors
- * in {2, 3, 5}. Asynchronous. */
+ * (NULL = default stream). in == out is allowed; any float2-aligned pointers. Nx, Ny in
+ * [1, 512] with prime factors in {2, 3, 5}. Asynchronous. */
 int tts_fft2d(const tts_c64* in, tts_c64* out, int batch, int Nx, int Ny, int inverse, void* cuda_stream);
 
 /* The same unitary 2D DFT as dense complex matrix products on the tensor cores (tcgen05,
@@ -243,8 +244,8 @@ int tts_fft2d(const tts_c64* in, tts_c64* out, int batch, int Nx, int Ny, int in
  * bf16 hi + lo parts and accumulates hi*hi + hi*lo + lo*hi (relative error ~1e-5, within
  * the 1e-4 image bound); TTS_DFT_BF16 uses hi*hi only (~4e-3: plain BF16 does not meet the
  * bound). in, out, tmp: device, batch x Nx x Ny complex64, row-major; tmp (same size) holds
- * the intermediate transposes and must not alias in or out (in == out is allowed). Nx, Ny
- * multiples of 32 in [32, 256]. dev_status: NULL, or a device int the kernel sets to 1 if
+ * the intermediate transposes and must not alias in or out (in == out is allowed); all
+ * three 16-byte aligned (TTS_EINVAL otherwise). Nx, Ny multiples of 32 in [32, 256]. dev_status: NULL, or a device int the kernel sets to 1 if
  * one of its bounded waits ran out (the results are then invalid). Asynchronous on
  * cuda_stream (NULL = default stream). */
 #define TTS_DFT_BF16X3 0

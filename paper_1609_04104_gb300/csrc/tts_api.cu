@@ -376,6 +376,8 @@ int tts_set_coil_maps(tts_handle* h, const tts_c64* maps, int C, int flags) {
 int tts_push_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line_mask, int flags) {
   if (!h || !y_rows) return fail(TTS_EINVAL, "NULL argument%s");
   if (h->mc) return mc_push(h, y_rows, line_mask, flags);
+  if (h->cfg.row_dft != TTS_ROWDFT_FFT && (flags & TTS_DEVICE_PTRS) && (uintptr_t)y_rows % 16 != 0)
+    return fail(TTS_EINVAL, "the tensor-core row transform reads 16-byte aligned device rows%s");
   FrameParams p;
   const int rs = handle_stage_frame(h, y_rows, line_mask, flags, &p);
   if (rs != TTS_OK) return rs;
@@ -657,10 +659,10 @@ int tts_fft2d(const tts_c64* in, tts_c64* out, int batch, int Nx, int Ny, int in
   if (!wx) return rc;
   const float2* wy = device_twiddles(Ny, &rc);
   if (!wy) return rc;
-  if (fft2d_cluster_ok(Nx, Ny)) {
+  if (fft2d_square_ok(Nx, Ny)) {
     int* st = device_status(&rc);
     if (!st) return fail(rc, "device status word%s");
-    rc = launch_fft2d_cluster((const float2*)in, (float2*)out, batch, Nx, inverse, wx, st, (cudaStream_t)cuda_stream);
+    rc = launch_fft2d_square((const float2*)in, (float2*)out, batch, Nx, inverse, wx, st, (cudaStream_t)cuda_stream);
   } else {
     rc = launch_fft2d((const float2*)in, (float2*)out, batch, Nx, Ny, inverse, wx, wy, nullptr,
                       (cudaStream_t)cuda_stream);
@@ -677,6 +679,8 @@ int tts_dft2d_gemm(const tts_c64* in, tts_c64* out, tts_c64* tmp, int batch, int
   if (precision != TTS_DFT_BF16X3 && precision != TTS_DFT_BF16) return fail(TTS_EINVAL, "unknown precision%s");
   if ((const void*)tmp == (const void*)in || (const void*)tmp == (const void*)out)
     return fail(TTS_EINVAL, "tmp must not alias in or out%s");
+  if (((uintptr_t)in | (uintptr_t)out | (uintptr_t)tmp) % 16 != 0)
+    return fail(TTS_EINVAL, "in, out and tmp must be 16-byte aligned%s");
   if (batch == 0) return TTS_OK;
   int* st = dev_status;
   if (!st) {

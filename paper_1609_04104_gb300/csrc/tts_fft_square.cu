@@ -1,0 +1,340 @@
+// Batched unitary 2D DFT for square N in {64, 128, 256} as one persistent launch over band
+// tasks, with the intermediate image kept in L2, so that HBM sees about one read and one
+// write of every image.
+//
+// The image splits into NB = N / 32 bands of 32 rows and NB bands of 32 columns. A row task
+// (image i, band b) transforms rows [32 b, 32 b + 32) of in[i] and writes them, unscaled, to
+// out[i]; a column task transforms columns [32 b, 32 b + 32) of out[i] in place and scales
+// by 1 / N (the two unitary 1 / sqrt N factors). Tasks are taken in a fixed order from one
+// counter: the row tasks of image i come L images ahead of its column tasks (L about the
+// number of resident CTAs over 2 NB), so a column task almost never waits, and the L images
+// between the two passes (a few MB) stay in L2. A column task waits until the NB row tasks
+// of its image have published (a per-image counter, release / acquire at GPU scope; the
+// wait is bounded). A row task never waits, and every task waits only on tasks taken
+// before it, so the launch cannot deadlock.
+//
+// Both task kinds run the four-step FFT N = T x R per line: a length-R DFT in registers over
+// the elements t + T n2, twiddles w_N^(t k2), a transpose through shared memory, length-T
+// DFTs.
+//   rows:    T threads per row (a half-warp or a quarter-warp), loads and stores of T
+//            consecutive values; the transpose through the row's own 2N-byte region;
+//   columns: lane = column of the band, warp = the four-step index t; every load and store
+//            of a warp moves 32 consecutive values (256 bytes) of one row, the transpose
+//            through the band's N x 32 buffer.
+// Global loads bypass L1 (the data of a column task was written by other SMs).
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+
+#include "tts_internal.cuh"
+
+namespace {
+
+constexpr int kBand = 32;      // rows or columns per task
+
+// T x R = N; NT threads, one line of the band each (32 T = NT); MINB CTAs per SM
+template <int N>
+struct Shape;
+template <>
+struct Shape<256> {
+  static constexpr int T = 16, R = 16, NT = 512, MINB = 2;
+};
+template <>
+struct Shape<128> {
+  static constexpr int T = 8, R = 16, NT = 256, MINB = 4;
+};
+template <>
+struct Shape<64> {
+  static constexpr int T = 8, R = 8, NT = 256, MINB = 4;
+};
+
+// w_16^k = exp(-2 pi i k / 16) for the k the small DFTs use (conjugated for the inverse)
+constexpr float kC1 = 0.92387953251128675613f;   // cos(pi / 8)
+constexpr float kS1 = 0.38268343236508977173f;   // sin(pi / 8)
+constexpr float kH = 0.70710678118654752440f;    // cos(pi / 4)
+
+template <bool INV>
+__device__ __forceinline__ float2 w16(int k) {
+  float2 w;
+  switch (k & 15) {
+    case 1: w = make_float2(kC1, -kS1); break;
+    case 2: w = make_float2(kH, -kH); break;
+    case 3: w = make_float2(kS1, -kC1); break;
+    case 4: w = make_float2(0.f, -1.f); break;
+    case 6: w = make_float2(-kH, -kH); break;
+    default: w = make_float2(-kC1, kS1); break;   // k = 9
+  }
+  return INV ? make_float2(w.x, -w.y) : w;
+}
+
+// 16-point DFT in registers: n = 4 n1 + n2, k = k1 + 4 k2, inner twiddles w_16^(n2 k1)
+template <bool INV>
+__device__ __forceinline__ void dft16c(float2* v) {
+  constexpr int sg = INV ? 1 : -1;
+  float2 t[16];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    float2 r0, r1, r2, r3;
+    bfly4(v[n2], v[4 + n2], v[8 + n2], v[12 + n2], sg, r0, r1, r2, r3);
+    t[n2 * 4 + 0] = r0;
+    t[n2 * 4 + 1] = n2 == 0 ? r1 : cmul(r1, w16<INV>(n2));
+    t[n2 * 4 + 2] = n2 == 0 ? r2 : cmul(r2, w16<INV>(2 * n2));
+    t[n2 * 4 + 3] = n2 == 0 ? r3 : cmul(r3, w16<INV>(3 * n2));
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+    bfly4(t[k1], t[4 + k1], t[8 + k1], t[12 + k1], sg, v[k1], v[k1 + 4], v[k1 + 8], v[k1 + 12]);
+}
+
+// 8-point DFT in registers: n = 4 n1 + n2 (n1 < 2), k = k1 + 2 k2, inner twiddles w_8^(n2)
+template <bool INV>
+__device__ __forceinline__ void dft8c(float2* v) {
+  constexpr int sg = INV ? 1 : -1;
+  float2 t0[4], t1[4];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    t0[n2] = cadd(v[n2], v[4 + n2]);
+    const float2 d = csub(v[n2], v[4 + n2]);
+    t1[n2] = n2 == 0 ? d : cmul(d, w16<INV>(2 * n2));
+  }
+  bfly4(t0[0], t0[1], t0[2], t0[3], sg, v[0], v[2], v[4], v[6]);
+  bfly4(t1[0], t1[1], t1[2], t1[3], sg, v[1], v[3], v[5], v[7]);
+}
+
+template <int L, bool INV>
+__device__ __forceinline__ void dft_small(float2* v) {
+  if constexpr (L == 16) dft16c<INV>(v);
+  else dft8c<INV>(v);
+}
+
+// w_N^idx from the padded table of exp(-2 pi i k / N)
+template <bool INV>
+__device__ __forceinline__ float2 twn(const float2* W, int idx) {
+  const float2 w = W[fpad(idx)];
+  return INV ? make_float2(w.x, -w.y) : w;
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Task q of the fixed order: row tasks of images [0, L) first, then per image i >= L the
+// column tasks of image i - L followed by the row tasks of image i, then the column tasks
+// of the last L images. Returns the image; *band the band, *col whether a column task.
+__device__ __forceinline__ int decode(int q, int NB, int L, int batch, int* band, bool* col) {
+  const int Lb = min(L, batch);
+  const int head = NB * Lb;
+  const int mid_imgs = batch - Lb;
+  const int mid = 2 * NB * mid_imgs;
+  if (q < head) {
+    *col = false;
+    *band = q % NB;
+    return q / NB;
+  }
+  if (q < head + mid) {
+    const int qq = q - head, pair = qq / (2 * NB), r = qq - pair * 2 * NB;
+    *col = r < NB;
+    *band = *col ? r : r - NB;
+    return *col ? pair : pair + Lb;
+  }
+  const int qq = q - head - mid;
+  *col = true;
+  *band = qq % NB;
+  return mid_imgs + qq / NB;
+}
+
+// Row regions of a row task: with quarter-warp rows (T = 8) a pad of 64 bytes puts the two
+// rows of a half-warp on different banks.
+template <int N>
+__host__ __device__ constexpr int row_stride() {
+  return N + (Shape<N>::T == 8 ? 8 : 0);
+}
+
+template <int N, bool INV>
+__global__ void __launch_bounds__(Shape<N>::NT, Shape<N>::MINB)
+    fft2d_square_kernel(const float2* in, float2* out, int batch, int L, const float2* __restrict__ Wg, float scale,
+                        int* ctrl, int* err) {
+  constexpr int T = Shape<N>::T, R = Shape<N>::R, NT = Shape<N>::NT, J = R / T, NB = N / kBand;
+  static_assert(kBand * T == NT, "one line of the band per thread");
+  constexpr int RS = row_stride<N>();       // row regions of a row task in S
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* S = (float2*)smem;                // transposes: kBand x RS (rows), N x kBand (columns)
+  float2* W = S + kBand * RS;               // fsz(N), padded
+  __shared__ int s_task[2];
+  int* next = ctrl;                         // task counter
+  int* done = ctrl + 1;                     // row tasks published, per image
+  const int tid = threadIdx.x;
+  const int total = 2 * NB * batch;
+  for (int k = tid; k < N; k += NT) W[fpad(k)] = Wg[k];
+  // thread 0 takes the next task index while the current task runs, and publishes a
+  // finished row task at the top of the next iteration (after the barrier that follows
+  // the task's last store)
+  int nq = 0, pub = -1;
+  if (tid == 0) s_task[0] = atomicAdd(next, 1);
+  __syncthreads();
+  for (int it = 0;; ++it) {
+    const int q = s_task[it & 1];
+    if (tid == 0) {
+      if (pub >= 0) {
+        __threadfence();
+        atomicAdd(done + pub, 1);
+        pub = -1;
+      }
+      if (q < total) nq = atomicAdd(next, 1);
+    }
+    if (q >= total) break;
+    int band;
+    bool col;
+    const int img = decode(q, NB, L, batch, &band, &col);
+    float2* ob = out + (size_t)img * N * N;
+    if (!col) {
+      // ---- row task: group g = tid / T takes row g of the band
+      const int g = tid / T, t = tid % T;
+      float2 v[R];
+      const float2* src = in + (size_t)img * N * N + (size_t)(band * kBand + g) * N + t;
+#pragma unroll
+      for (int n2 = 0; n2 < R; ++n2) v[n2] = __ldcs(src + T * n2);
+      float2* sc = S + g * RS;
+      dft_small<R, INV>(v);
+#pragma unroll
+      for (int k2 = 1; k2 < R; ++k2) v[k2] = cmul(v[k2], twn<INV>(W, t * k2));   // t k2 < N
+      // Y[n1 = t][k2] to slot k2 T + (n1 ^ (k2 mod T))
+#pragma unroll
+      for (int k2 = 0; k2 < R; ++k2) sc[k2 * T + (t ^ (k2 % T))] = v[k2];
+      __syncwarp();
+      float2* dst = ob + (size_t)(band * kBand + g) * N;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int k2 = t + T * j;
+        float2 u[T];
+#pragma unroll
+        for (int n1 = 0; n1 < T; ++n1) u[n1] = sc[k2 * T + (n1 ^ t)];
+        dft_small<T, INV>(u);
+#pragma unroll
+        for (int k1 = 0; k1 < T; ++k1) __stcg(dst + k2 + R * k1, u[k1]);   // X[k2 + R k1]
+      }
+      if (tid == 0) pub = img;
+    } else {
+      // ---- column task: lane c = column band * 32 + c, warp t = four-step index
+      if (tid == 0) {
+        const long long t0 = clock64();
+        while (ld_acquire(done + img) < NB) {
+          if (clock64() - t0 > 2000000000LL) {
+            atomicOr(err, 1);
+            break;
+          }
+        }
+      }
+      __syncthreads();
+      const int c = tid & 31, t = tid >> 5;
+      float2* cb = ob + band * kBand + c;
+      float2 v[R];
+#pragma unroll
+      for (int n2 = 0; n2 < R; ++n2) v[n2] = __ldcg(cb + (size_t)(t + T * n2) * N);
+      dft_small<R, INV>(v);
+#pragma unroll
+      for (int k2 = 1; k2 < R; ++k2) v[k2] = cmul(v[k2], twn<INV>(W, t * k2));
+#pragma unroll
+      for (int k2 = 0; k2 < R; ++k2) S[(k2 * T + t) * kBand + c] = v[k2];
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int k2 = t + T * j;
+        float2 u[T];
+#pragma unroll
+        for (int n1 = 0; n1 < T; ++n1) u[n1] = S[(k2 * T + n1) * kBand + c];
+        dft_small<T, INV>(u);
+#pragma unroll
+        for (int k1 = 0; k1 < T; ++k1) __stcs(cb + (size_t)(k2 + R * k1) * N, cscale(u[k1], scale));
+      }
+    }
+    if (tid == 0) s_task[(it + 1) & 1] = nq;
+    __syncthreads();   // the task's stores are issued; S and s_task[it & 1] are free
+  }
+}
+
+template <int N>
+constexpr int smem_bytes() {
+  return (int)sizeof(float2) * (kBand * row_stride<N>() + N + (N - 1) / 16);   // S and fsz(N)
+}
+
+// Stream-ordered memory for the task counters of a call, from a pool of this library that
+// keeps its memory between calls (the device's default pool returns it at every
+// synchronisation, and mapping it again costs more than a small transform). One pool per
+// device, created on first use.
+cudaMemPool_t ctrl_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = ~0ull;
+    if (cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+      cudaMemPoolDestroy(p);
+      return nullptr;
+    }
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
+template <int N, bool INV>
+int launch_t(const float2* in, float2* out, int batch, const float2* W, int* err, cudaStream_t st) {
+  constexpr int NB = N / kBand;
+  constexpr int smem = smem_bytes<N>();
+  static int grid = 0;
+  if (grid == 0) {
+    if (cudaFuncSetAttribute(fft2d_square_kernel<N, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess)
+      return TTS_ECUDA;
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fft2d_square_kernel<N, INV>, Shape<N>::NT, smem) !=
+            cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1)
+      return TTS_ECUDA;
+    grid = per_sm * sms;
+  }
+  const int tasks = 2 * NB * batch;
+  const int g = std::min(grid, tasks);
+  // lag between an image's row and column tasks: about 1.5 times the tasks in flight
+  const int L = std::max(1, (3 * g) / (4 * NB) + 1);
+  int* ctrl = nullptr;
+  const size_t cb = sizeof(int) * (1 + (size_t)batch);
+  cudaMemPool_t pool = ctrl_pool();
+  if (!pool || cudaMallocFromPoolAsync((void**)&ctrl, cb, pool, st) != cudaSuccess) return TTS_ECUDA;
+  if (cudaMemsetAsync(ctrl, 0, cb, st) != cudaSuccess) return TTS_ECUDA;
+  fft2d_square_kernel<N, INV><<<g, Shape<N>::NT, smem, st>>>(in, out, batch, L, W, 1.0f / (float)N, ctrl, err);
+  const cudaError_t e = cudaGetLastError();
+  if (cudaFreeAsync(ctrl, st) != cudaSuccess || e != cudaSuccess) return TTS_ECUDA;
+  return TTS_OK;
+}
+
+template <int N>
+int launch_n(const float2* in, float2* out, int batch, int inverse, const float2* W, int* err, cudaStream_t st) {
+  return inverse ? launch_t<N, true>(in, out, batch, W, err, st) : launch_t<N, false>(in, out, batch, W, err, st);
+}
+
+}  // namespace
+
+bool fft2d_square_ok(int Nx, int Ny) { return Nx == Ny && (Nx == 64 || Nx == 128 || Nx == 256); }
+
+int launch_fft2d_square(const float2* in, float2* out, int batch, int N, int inverse, const float2* W, int* err,
+                        cudaStream_t st) {
+  if (batch <= 0) return TTS_OK;
+  switch (N) {
+    case 256: return launch_n<256>(in, out, batch, inverse, W, err, st);
+    case 128: return launch_n<128>(in, out, batch, inverse, W, err, st);
+    case 64: return launch_n<64>(in, out, batch, inverse, W, err, st);
+    default: return TTS_EINVAL;
+  }
+}

@@ -435,10 +435,11 @@ void tts_internal_set_error(const char* msg);   // message returned by tts_last_
 int launch_fft2d(const float2* in, float2* out, int batch, int Nx, int Ny, int inverse, const float2* Wx,
                  const float2* Wy, float2* scratch, cudaStream_t st);
 int launch_ridge(const double2* G, const double2* h, int R, double2* gamma, cudaStream_t st);
-// single-pass cluster form of the batched 2D DFT (tts_fft_cluster.cu), square N in {64, 128, 256}
-bool fft2d_cluster_ok(int Nx, int Ny);
-int launch_fft2d_cluster(const float2* in, float2* out, int batch, int N, int inverse, const float2* W, int* err,
-                         cudaStream_t st);
+// batched 2D DFT for square N in {64, 128, 256} as one persistent launch over row and
+// column band tasks (tts_fft_square.cu)
+bool fft2d_square_ok(int Nx, int Ny);
+int launch_fft2d_square(const float2* in, float2* out, int batch, int N, int inverse, const float2* W, int* err,
+                        cudaStream_t st);
 // 2D DFT as tensor-core matrix products (tts_dft_gemm.cu)
 bool dft_gemm_size_ok(int N);
 // Inverse unitary DFT of the acquired rows (mask lines) of a frame, Yt = y_S conj(F_Ny),

@@ -373,7 +373,7 @@ __global__ void init_kernel(float2* A, int N, int R, unsigned long long seed, ui
 // ------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) fft_rows_kernel(const float2* __restrict__ in, float2* __restrict__ out,
                                                        long nrows, int Ny, int rows_per_cta, int sign,
-                                                       const float2* __restrict__ Wy, float scale) {
+                                                       const float2* __restrict__ Wy, float scale, int vec) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ld = fsz(Ny);   // padded row stride in shared memory
   float2* W = (float2*)smem_raw;
@@ -385,8 +385,9 @@ __global__ void __launch_bounds__(256) fft_rows_kernel(const float2* __restrict_
   const int nr = (int)min((long)rows_per_cta, nrows - r0);
   if (nr <= 0) return;
   const int n2 = nr * Ny;
-  if ((Ny & 1) == 0) {
-    // float4 global loads: two elements of one row (a pair never straddles a pad slot)
+  if (vec) {
+    // float4 global loads (Ny even, in and out 16-byte aligned): two elements of one row
+    // (a pair never straddles a pad slot)
     const float4* src = (const float4*)(in + r0 * Ny);
     for (int e = tid; e < n2 / 2; e += blockDim.x) {
       const float4 v = src[e];
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(256) fft_rows_kernel(const float2* __restrict_
   __syncthreads();
   const FftPlan plan = fft_plan(Ny);
   float2* res = fft_smem(buf, tmp, plan, nr, ld, W, sign, tid, blockDim.x);
-  if ((Ny & 1) == 0) {
+  if (vec) {
     float4* dst = (float4*)(out + r0 * Ny);
     for (int e = tid; e < n2 / 2; e += blockDim.x) {
       const int i0 = 2 * e, r = i0 / Ny, c = i0 - r * Ny;
@@ -567,13 +568,15 @@ int launch_fft2d(const float2* in, float2* out, int batch, int Nx, int Ny, int i
   // column pass reads it back: DRAM then sees about one read of in and one write of out.
   const size_t img = (size_t)Nx * Ny * sizeof(float2);
   const size_t l2_budget = 32u << 20;
+  // 16-byte vector accesses need even rows and 16-byte aligned images
+  const int vec = (Ny % 2 == 0) && ((uintptr_t)in % 16 == 0) && ((uintptr_t)out % 16 == 0);
   const int group = (int)std::max<size_t>(1, std::min<size_t>((size_t)batch, l2_budget / img));
   for (int g0 = 0; g0 < batch; g0 += group) {
     const int gb = std::min(group, batch - g0);
     const long nrows = (long)gb * Nx;
     const long grid_r = (nrows + rows_per_cta - 1) / rows_per_cta;
     fft_rows_kernel<<<(unsigned)grid_r, 256, smem_r, st>>>(in + (size_t)g0 * Nx * Ny, out + (size_t)g0 * Nx * Ny, nrows,
-                                                            Ny, rows_per_cta, sign, Wy, 1.0f / sqrtf((float)Ny));
+                                                            Ny, rows_per_cta, sign, Wy, 1.0f / sqrtf((float)Ny), vec);
     if (cudaGetLastError() != cudaSuccess) return TTS_ECUDA;
     const long grid_c = (long)gb * ((Ny + cols_per_cta - 1) / cols_per_cta);
     fft_cols_kernel<<<(unsigned)grid_c, 256, smem_c, st>>>(out + (size_t)g0 * Nx * Ny, Nx, Ny, cols_per_cta, sign, Wx,

@@ -69,6 +69,11 @@ def test_in_place_and_errors(tts):
     bad = torch.zeros((1, 48, 64), dtype=torch.complex64, device="cuda")
     with pytest.raises(tts.TtsError):
         tts.tts_dft2d_gemm(bad, torch.empty_like(bad), torch.empty_like(bad))   # 48 is not a multiple of 32
+    buf = torch.empty(2 * 64 * 96 + 1, dtype=torch.complex64, device="cuda")
+    off = buf[1:].view(2, 64, 96)                             # 8 bytes past a 16-byte boundary
+    assert off.data_ptr() % 16 == 8
+    with pytest.raises(tts.TtsError):
+        tts.tts_dft2d_gemm(off, torch.empty_like(x), torch.empty_like(x))
 
 
 @pytest.mark.parametrize("row_dft,bound", [(1, 1e-4), (2, None)])
