@@ -2,25 +2,26 @@
 // tasks, with the intermediate image kept in L2, so that HBM sees about one read and one
 // write of every image.
 //
-// The image splits into NB = N / 32 bands of 32 rows and NB bands of 32 columns. A row task
-// (image i, band b) transforms rows [32 b, 32 b + 32) of in[i] and writes them, unscaled, to
-// out[i]; a column task transforms columns [32 b, 32 b + 32) of out[i] in place and scales
-// by 1 / N (the two unitary 1 / sqrt N factors). Tasks are taken in a fixed order from one
-// counter: the row tasks of image i come L images ahead of its column tasks (L about the
-// number of resident CTAs over 2 NB), so a column task almost never waits, and the L images
-// between the two passes (a few MB) stay in L2. A column task waits until the NB row tasks
-// of its image have published (a per-image counter, release / acquire at GPU scope; the
-// wait is bounded). A row task never waits, and every task waits only on tasks taken
-// before it, so the launch cannot deadlock.
+// The image splits into NB = N / BAND bands of BAND rows and NB bands of BAND columns
+// (BAND = 16). A row task (image i, band b) transforms rows
+// [BAND b, BAND (b + 1)) of in[i] and writes them, unscaled, to out[i]; a column task
+// transforms columns [BAND b, BAND (b + 1)) of out[i] in place and scales by 1 / N (the two
+// unitary 1 / sqrt N factors). Tasks are taken in a fixed order from one counter: the row
+// tasks of image i come L images ahead of its column tasks (L about 1.5 times the CTAs
+// over 2 NB), so a column task almost never waits, and the L images between the two passes
+// (a few MB) stay in L2. A column task waits until the NB row tasks of its image have
+// published (a per-image counter, release / acquire at GPU scope; the wait is bounded). A
+// row task never waits, and every task waits only on tasks taken before it, so the launch
+// cannot deadlock. Small CTAs (BAND x T threads, at most 35 KB of shared memory, four or
+// eight per SM) let the other CTAs of an SM run through one CTA's barrier and memory waits.
 //
 // Both task kinds run the four-step FFT N = T x R per line: a length-R DFT in registers over
 // the elements t + T n2, twiddles w_N^(t k2), a transpose through shared memory, length-T
 // DFTs.
 //   rows:    T threads per row (a half-warp or a quarter-warp), loads and stores of T
-//            consecutive values; the transpose through the row's own 2N-byte region;
-//   columns: lane = column of the band, warp = the four-step index t; every load and store
-//            of a warp moves 32 consecutive values (256 bytes) of one row, the transpose
-//            through the band's N x 32 buffer.
+//            consecutive values; the transpose through the row's own region;
+//   columns: thread (t, c) for column c of the band, every load and store of BAND
+//            consecutive values of one row, the transpose through the band's N x BAND buffer.
 // Global loads bypass L1 (the data of a column task was written by other SMs).
 #include <algorithm>
 #include <cstdint>
@@ -30,22 +31,21 @@
 
 namespace {
 
-constexpr int kBand = 32;      // rows or columns per task
-
-// T x R = N; NT threads, one line of the band each (32 T = NT); MINB CTAs per SM
+// T x R = N; BAND rows (row task) or columns (column task) per task; NT threads, one line
+// of the band each (BAND T = NT); MINB CTAs per SM
 template <int N>
 struct Shape;
 template <>
 struct Shape<256> {
-  static constexpr int T = 16, R = 16, NT = 512, MINB = 2;
+  static constexpr int T = 16, R = 16, BAND = 16, NT = 256, MINB = 4;
 };
 template <>
 struct Shape<128> {
-  static constexpr int T = 8, R = 16, NT = 256, MINB = 4;
+  static constexpr int T = 8, R = 16, BAND = 16, NT = 128, MINB = 8;
 };
 template <>
 struct Shape<64> {
-  static constexpr int T = 8, R = 8, NT = 256, MINB = 4;
+  static constexpr int T = 8, R = 8, BAND = 16, NT = 128, MINB = 8;
 };
 
 // w_16^k = exp(-2 pi i k / 16) for the k the small DFTs use (conjugated for the inverse)
@@ -156,12 +156,13 @@ template <int N, bool INV>
 __global__ void __launch_bounds__(Shape<N>::NT, Shape<N>::MINB)
     fft2d_square_kernel(const float2* in, float2* out, int batch, int L, const float2* __restrict__ Wg, float scale,
                         int* ctrl, int* err) {
-  constexpr int T = Shape<N>::T, R = Shape<N>::R, NT = Shape<N>::NT, J = R / T, NB = N / kBand;
-  static_assert(kBand * T == NT, "one line of the band per thread");
+  constexpr int T = Shape<N>::T, R = Shape<N>::R, BAND = Shape<N>::BAND, NT = Shape<N>::NT;
+  constexpr int J = R / T, NB = N / BAND;
+  static_assert(BAND * T == NT, "one line of the band per thread");
   constexpr int RS = row_stride<N>();       // row regions of a row task in S
   extern __shared__ __align__(16) unsigned char smem[];
-  float2* S = (float2*)smem;                // transposes: kBand x RS (rows), N x kBand (columns)
-  float2* W = S + kBand * RS;               // fsz(N), padded
+  float2* S = (float2*)smem;                // transposes: BAND x RS (rows), N x BAND (columns)
+  float2* W = S + BAND * RS;                // fsz(N), padded
   __shared__ int s_task[2];
   int* next = ctrl;                         // task counter
   int* done = ctrl + 1;                     // row tasks published, per image
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(Shape<N>::NT, Shape<N>::MINB)
       // ---- row task: group g = tid / T takes row g of the band
       const int g = tid / T, t = tid % T;
       float2 v[R];
-      const float2* src = in + (size_t)img * N * N + (size_t)(band * kBand + g) * N + t;
+      const float2* src = in + (size_t)img * N * N + (size_t)(band * BAND + g) * N + t;
 #pragma unroll
       for (int n2 = 0; n2 < R; ++n2) v[n2] = __ldcs(src + T * n2);
       float2* sc = S + g * RS;
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(Shape<N>::NT, Shape<N>::MINB)
 #pragma unroll
       for (int k2 = 0; k2 < R; ++k2) sc[k2 * T + (t ^ (k2 % T))] = v[k2];
       __syncwarp();
-      float2* dst = ob + (size_t)(band * kBand + g) * N;
+      float2* dst = ob + (size_t)(band * BAND + g) * N;
 #pragma unroll
       for (int j = 0; j < J; ++j) {
         const int k2 = t + T * j;
@@ -217,7 +218,8 @@ __global__ void __launch_bounds__(Shape<N>::NT, Shape<N>::MINB)
       }
       if (tid == 0) pub = img;
     } else {
-      // ---- column task: lane c = column band * 32 + c, warp t = four-step index
+      // ---- column task: c = tid mod BAND is column band * BAND + c, t = tid / BAND the
+      // four-step index (a warp holds 32 / BAND values of t)
       if (tid == 0) {
         const long long t0 = clock64();
         while (ld_acquire(done + img) < NB) {
@@ -228,8 +230,8 @@ __global__ void __launch_bounds__(Shape<N>::NT, Shape<N>::MINB)
         }
       }
       __syncthreads();
-      const int c = tid & 31, t = tid >> 5;
-      float2* cb = ob + band * kBand + c;
+      const int c = tid % BAND, t = tid / BAND;
+      float2* cb = ob + band * BAND + c;
       float2 v[R];
 #pragma unroll
       for (int n2 = 0; n2 < R; ++n2) v[n2] = __ldcg(cb + (size_t)(t + T * n2) * N);
@@ -237,14 +239,14 @@ __global__ void __launch_bounds__(Shape<N>::NT, Shape<N>::MINB)
 #pragma unroll
       for (int k2 = 1; k2 < R; ++k2) v[k2] = cmul(v[k2], twn<INV>(W, t * k2));
 #pragma unroll
-      for (int k2 = 0; k2 < R; ++k2) S[(k2 * T + t) * kBand + c] = v[k2];
+      for (int k2 = 0; k2 < R; ++k2) S[(k2 * T + t) * BAND + c] = v[k2];
       __syncthreads();
 #pragma unroll
       for (int j = 0; j < J; ++j) {
         const int k2 = t + T * j;
         float2 u[T];
 #pragma unroll
-        for (int n1 = 0; n1 < T; ++n1) u[n1] = S[(k2 * T + n1) * kBand + c];
+        for (int n1 = 0; n1 < T; ++n1) u[n1] = S[(k2 * T + n1) * BAND + c];
         dft_small<T, INV>(u);
 #pragma unroll
         for (int k1 = 0; k1 < T; ++k1) __stcs(cb + (size_t)(k2 + R * k1) * N, cscale(u[k1], scale));
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(Shape<N>::NT, Shape<N>::MINB)
 
 template <int N>
 constexpr int smem_bytes() {
-  return (int)sizeof(float2) * (kBand * row_stride<N>() + N + (N - 1) / 16);   // S and fsz(N)
+  return (int)sizeof(float2) * (Shape<N>::BAND * row_stride<N>() + N + (N - 1) / 16);   // S and fsz(N)
 }
 
 // Stream-ordered memory for the task counters of a call, from a pool of this library that
@@ -289,7 +291,7 @@ cudaMemPool_t ctrl_pool() {
 
 template <int N, bool INV>
 int launch_t(const float2* in, float2* out, int batch, const float2* W, int* err, cudaStream_t st) {
-  constexpr int NB = N / kBand;
+  constexpr int NB = N / Shape<N>::BAND;
   constexpr int smem = smem_bytes<N>();
   static int grid = 0;
   if (grid == 0) {
