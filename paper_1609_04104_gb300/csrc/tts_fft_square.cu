@@ -119,6 +119,9 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ void red_release_add(int* p, int v) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 // Task q of the fixed order: row tasks of images [0, L) first, then per image i >= L the
 // column tasks of image i - L followed by the row tasks of image i, then the column tasks
@@ -179,8 +182,7 @@ __global__ void __launch_bounds__(Shape<N>::NT, Shape<N>::MINB)
     const int q = s_task[it & 1];
     if (tid == 0) {
       if (pub >= 0) {
-        __threadfence();
-        atomicAdd(done + pub, 1);
+        red_release_add(done + pub, 1);   // cumulative over the CTA's stores (the barrier before)
         pub = -1;
       }
       if (q < total) nq = atomicAdd(next, 1);
