@@ -27,91 +27,54 @@
 #include <cstdint>
 #include <mutex>
 
+#include "tts_fft_small.cuh"
 #include "tts_internal.cuh"
 
 namespace {
 
-// T x R = N; BAND rows (row task) or columns (column task) per task; NT threads, one line
-// of the band each (BAND T = NT); MINB CTAs per SM
+// T x R = N (T a power of two, threads per line in a row task; R the register length); BAND
+// rows (row task) or columns (column task) per task; NT = BAND T threads, one line of the
+// band each; MINB CTAs per SM (registers: 64 for R <= 16, more for the longer R)
 template <int N>
 struct Shape;
 template <>
-struct Shape<256> {
-  static constexpr int T = 16, R = 16, BAND = 16, NT = 256, MINB = 4;
+struct Shape<64> {
+  static constexpr int T = 8, R = 8, BAND = 16, NT = 128, MINB = 8;
+};
+template <>
+struct Shape<96> {
+  static constexpr int T = 8, R = 12, BAND = 16, NT = 128, MINB = 6;
 };
 template <>
 struct Shape<128> {
   static constexpr int T = 8, R = 16, BAND = 16, NT = 128, MINB = 8;
 };
 template <>
-struct Shape<64> {
-  static constexpr int T = 8, R = 8, BAND = 16, NT = 128, MINB = 8;
+struct Shape<160> {
+  static constexpr int T = 16, R = 10, BAND = 16, NT = 256, MINB = 4;
+};
+template <>
+struct Shape<192> {
+  static constexpr int T = 16, R = 12, BAND = 16, NT = 256, MINB = 3;
+};
+template <>
+struct Shape<256> {
+  static constexpr int T = 16, R = 16, BAND = 16, NT = 256, MINB = 4;
+};
+template <>
+struct Shape<320> {
+  static constexpr int T = 16, R = 20, BAND = 16, NT = 256, MINB = 2;
+};
+template <>
+struct Shape<384> {
+  static constexpr int T = 16, R = 24, BAND = 16, NT = 256, MINB = 2;
 };
 
-// w_16^k = exp(-2 pi i k / 16) for the k the small DFTs use (conjugated for the inverse)
-constexpr float kC1 = 0.92387953251128675613f;   // cos(pi / 8)
-constexpr float kS1 = 0.38268343236508977173f;   // sin(pi / 8)
-constexpr float kH = 0.70710678118654752440f;    // cos(pi / 4)
-
-template <bool INV>
-__device__ __forceinline__ float2 w16(int k) {
-  float2 w;
-  switch (k & 15) {
-    case 1: w = make_float2(kC1, -kS1); break;
-    case 2: w = make_float2(kH, -kH); break;
-    case 3: w = make_float2(kS1, -kC1); break;
-    case 4: w = make_float2(0.f, -1.f); break;
-    case 6: w = make_float2(-kH, -kH); break;
-    default: w = make_float2(-kC1, kS1); break;   // k = 9
-  }
-  return INV ? make_float2(w.x, -w.y) : w;
-}
-
-// 16-point DFT in registers: n = 4 n1 + n2, k = k1 + 4 k2, inner twiddles w_16^(n2 k1)
-template <bool INV>
-__device__ __forceinline__ void dft16c(float2* v) {
-  constexpr int sg = INV ? 1 : -1;
-  float2 t[16];
-#pragma unroll
-  for (int n2 = 0; n2 < 4; ++n2) {
-    float2 r0, r1, r2, r3;
-    bfly4(v[n2], v[4 + n2], v[8 + n2], v[12 + n2], sg, r0, r1, r2, r3);
-    t[n2 * 4 + 0] = r0;
-    t[n2 * 4 + 1] = n2 == 0 ? r1 : cmul(r1, w16<INV>(n2));
-    t[n2 * 4 + 2] = n2 == 0 ? r2 : cmul(r2, w16<INV>(2 * n2));
-    t[n2 * 4 + 3] = n2 == 0 ? r3 : cmul(r3, w16<INV>(3 * n2));
-  }
-#pragma unroll
-  for (int k1 = 0; k1 < 4; ++k1)
-    bfly4(t[k1], t[4 + k1], t[8 + k1], t[12 + k1], sg, v[k1], v[k1 + 4], v[k1 + 8], v[k1 + 12]);
-}
-
-// 8-point DFT in registers: n = 4 n1 + n2 (n1 < 2), k = k1 + 2 k2, inner twiddles w_8^(n2)
-template <bool INV>
-__device__ __forceinline__ void dft8c(float2* v) {
-  constexpr int sg = INV ? 1 : -1;
-  float2 t0[4], t1[4];
-#pragma unroll
-  for (int n2 = 0; n2 < 4; ++n2) {
-    t0[n2] = cadd(v[n2], v[4 + n2]);
-    const float2 d = csub(v[n2], v[4 + n2]);
-    t1[n2] = n2 == 0 ? d : cmul(d, w16<INV>(2 * n2));
-  }
-  bfly4(t0[0], t0[1], t0[2], t0[3], sg, v[0], v[2], v[4], v[6]);
-  bfly4(t1[0], t1[1], t1[2], t1[3], sg, v[1], v[3], v[5], v[7]);
-}
+using fftsmall::twn;
 
 template <int L, bool INV>
-__device__ __forceinline__ void dft_small(float2* v) {
-  if constexpr (L == 16) dft16c<INV>(v);
-  else dft8c<INV>(v);
-}
-
-// w_N^idx from the padded table of exp(-2 pi i k / N)
-template <bool INV>
-__device__ __forceinline__ float2 twn(const float2* W, int idx) {
-  const float2 w = W[fpad(idx)];
-  return INV ? make_float2(w.x, -w.y) : w;
+__device__ __forceinline__ void dft_small(float2* v, const float2* W, int N) {
+  fftsmall::Dft<L, INV>::run(v, W, N);
 }
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
@@ -160,7 +123,7 @@ __global__ void __launch_bounds__(Shape<N>::NT, Shape<N>::MINB)
     fft2d_square_kernel(const float2* in, float2* out, int batch, int L, const float2* __restrict__ Wg, float scale,
                         int* ctrl, int* err) {
   constexpr int T = Shape<N>::T, R = Shape<N>::R, BAND = Shape<N>::BAND, NT = Shape<N>::NT;
-  constexpr int J = R / T, NB = N / BAND;
+  constexpr int J = (R + T - 1) / T, NB = N / BAND;   // second-stage lines per thread
   static_assert(BAND * T == NT, "one line of the band per thread");
   constexpr int RS = row_stride<N>();       // row regions of a row task in S
   extern __shared__ __align__(16) unsigned char smem[];
@@ -200,7 +163,7 @@ __global__ void __launch_bounds__(Shape<N>::NT, Shape<N>::MINB)
 #pragma unroll
       for (int n2 = 0; n2 < R; ++n2) v[n2] = __ldcs(src + T * n2);
       float2* sc = S + g * RS;
-      dft_small<R, INV>(v);
+      dft_small<R, INV>(v, W, N);
 #pragma unroll
       for (int k2 = 1; k2 < R; ++k2) v[k2] = cmul(v[k2], twn<INV>(W, t * k2));   // t k2 < N
       // Y[n1 = t][k2] to slot k2 T + (n1 ^ (k2 mod T))
@@ -211,12 +174,14 @@ __global__ void __launch_bounds__(Shape<N>::NT, Shape<N>::MINB)
 #pragma unroll
       for (int j = 0; j < J; ++j) {
         const int k2 = t + T * j;
-        float2 u[T];
+        if (J * T == R || k2 < R) {
+          float2 u[T];
 #pragma unroll
-        for (int n1 = 0; n1 < T; ++n1) u[n1] = sc[k2 * T + (n1 ^ t)];
-        dft_small<T, INV>(u);
+          for (int n1 = 0; n1 < T; ++n1) u[n1] = sc[k2 * T + (n1 ^ (k2 % T))];
+          dft_small<T, INV>(u, W, N);
 #pragma unroll
-        for (int k1 = 0; k1 < T; ++k1) __stcg(dst + k2 + R * k1, u[k1]);   // X[k2 + R k1]
+          for (int k1 = 0; k1 < T; ++k1) __stcg(dst + k2 + R * k1, u[k1]);   // X[k2 + R k1]
+        }
       }
       if (tid == 0) pub = img;
     } else {
@@ -237,7 +202,7 @@ __global__ void __launch_bounds__(Shape<N>::NT, Shape<N>::MINB)
       float2 v[R];
 #pragma unroll
       for (int n2 = 0; n2 < R; ++n2) v[n2] = __ldcg(cb + (size_t)(t + T * n2) * N);
-      dft_small<R, INV>(v);
+      dft_small<R, INV>(v, W, N);
 #pragma unroll
       for (int k2 = 1; k2 < R; ++k2) v[k2] = cmul(v[k2], twn<INV>(W, t * k2));
 #pragma unroll
@@ -246,12 +211,14 @@ __global__ void __launch_bounds__(Shape<N>::NT, Shape<N>::MINB)
 #pragma unroll
       for (int j = 0; j < J; ++j) {
         const int k2 = t + T * j;
-        float2 u[T];
+        if (J * T == R || k2 < R) {
+          float2 u[T];
 #pragma unroll
-        for (int n1 = 0; n1 < T; ++n1) u[n1] = S[(k2 * T + n1) * BAND + c];
-        dft_small<T, INV>(u);
+          for (int n1 = 0; n1 < T; ++n1) u[n1] = S[(k2 * T + n1) * BAND + c];
+          dft_small<T, INV>(u, W, N);
 #pragma unroll
-        for (int k1 = 0; k1 < T; ++k1) __stcs(cb + (size_t)(k2 + R * k1) * N, cscale(u[k1], scale));
+          for (int k1 = 0; k1 < T; ++k1) __stcs(cb + (size_t)(k2 + R * k1) * N, cscale(u[k1], scale));
+        }
       }
     }
     if (tid == 0) s_task[(it + 1) & 1] = nq;
@@ -330,15 +297,26 @@ int launch_n(const float2* in, float2* out, int batch, int inverse, const float2
 
 }  // namespace
 
-bool fft2d_square_ok(int Nx, int Ny) { return Nx == Ny && (Nx == 64 || Nx == 128 || Nx == 256); }
+bool fft2d_square_ok(int Nx, int Ny) {
+  if (Nx != Ny) return false;
+  switch (Nx) {
+    case 64: case 96: case 128: case 160: case 192: case 256: case 320: case 384: return true;
+    default: return false;
+  }
+}
 
 int launch_fft2d_square(const float2* in, float2* out, int batch, int N, int inverse, const float2* W, int* err,
                         cudaStream_t st) {
   if (batch <= 0) return TTS_OK;
   switch (N) {
-    case 256: return launch_n<256>(in, out, batch, inverse, W, err, st);
-    case 128: return launch_n<128>(in, out, batch, inverse, W, err, st);
     case 64: return launch_n<64>(in, out, batch, inverse, W, err, st);
+    case 96: return launch_n<96>(in, out, batch, inverse, W, err, st);
+    case 128: return launch_n<128>(in, out, batch, inverse, W, err, st);
+    case 160: return launch_n<160>(in, out, batch, inverse, W, err, st);
+    case 192: return launch_n<192>(in, out, batch, inverse, W, err, st);
+    case 256: return launch_n<256>(in, out, batch, inverse, W, err, st);
+    case 320: return launch_n<320>(in, out, batch, inverse, W, err, st);
+    case 384: return launch_n<384>(in, out, batch, inverse, W, err, st);
     default: return TTS_EINVAL;
   }
 }

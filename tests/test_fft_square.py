@@ -1,4 +1,4 @@
-"""The square form of the batched 2D DFT (tts_fft2d for square 64, 128, 256: one persistent
+"""The square form of the batched 2D DFT (tts_fft2d for square 64 ... 384: one persistent
 launch over row-band and column-band tasks, the column tasks of an image waiting on its
 row tasks): against the FP64 oracle's DFT, with batches smaller and much larger than the
 tasks in flight (every ordering case of the task list), both directions, in place, and an
@@ -28,13 +28,18 @@ def check(tts, N, batch, inverse, inplace, seed):
         assert np.linalg.norm(got[b] - ref) / np.linalg.norm(ref) <= 1e-5, (N, batch, b)
 
 
-@pytest.mark.parametrize("N", [64, 128, 256])
+SIZES = [64, 96, 128, 160, 192, 256, 320, 384]   # line lengths T x R with R in 8, 10, 12, 16, 20, 24
+
+
+@pytest.mark.parametrize("N", SIZES)
 @pytest.mark.parametrize("batch", [3, 300])
 def test_square_fft_forward(tts, N, batch):
+    if N >= 320 and batch > 100:
+        batch = 100
     check(tts, N, batch, False, False, N + batch)
 
 
-@pytest.mark.parametrize("N", [64, 256])
+@pytest.mark.parametrize("N", SIZES)
 def test_square_fft_inverse_in_place(tts, N):
     check(tts, N, 77, True, True, 5 * N)
 
@@ -52,7 +57,7 @@ def test_square_fft_round_trip(tts):
     assert np.linalg.norm(z.cpu().numpy() - X) / np.linalg.norm(X) <= 1e-6
 
 
-@pytest.mark.parametrize("N,batch", [(64, 1), (128, 300), (256, 200)])
+@pytest.mark.parametrize("N,batch", [(64, 1), (128, 300), (192, 150), (256, 200), (384, 60)])
 def test_square_fft_every_image(tts, N, batch):
     """Every image of a batch with many more tasks than CTAs (row and column tasks of
     different images interleaved, the intermediate images in flight in L2)."""
