@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtts.so")
 SOURCES = ["tts_api.cu", "tts_frame.cu", "tts_kernels.cu", "tts_noalloc.cu", "tts_engine.cu", "tts_dft_gemm.cu",
-           "tts_fft_square.cu", "tts_multicoil.cu"]
+           "tts_fft_square.cu", "tts_fft_lines.cu",
+           "tts_multicoil.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

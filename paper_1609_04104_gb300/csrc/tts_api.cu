@@ -663,6 +663,8 @@ int tts_fft2d(const tts_c64* in, tts_c64* out, int batch, int Nx, int Ny, int in
     int* st = device_status(&rc);
     if (!st) return fail(rc, "device status word%s");
     rc = launch_fft2d_square((const float2*)in, (float2*)out, batch, Nx, inverse, wx, st, (cudaStream_t)cuda_stream);
+  } else if (fft2d_lines_ok(Nx, Ny)) {
+    rc = launch_fft2d_lines((const float2*)in, (float2*)out, batch, Nx, Ny, inverse, wx, wy, (cudaStream_t)cuda_stream);
   } else {
     rc = launch_fft2d((const float2*)in, (float2*)out, batch, Nx, Ny, inverse, wx, wy, nullptr,
                       (cudaStream_t)cuda_stream);

@@ -1,81 +1,32 @@
-// Batched unitary 2D DFT for square N in {64, 128, 256} as one persistent launch over band
-// tasks, with the intermediate image kept in L2, so that HBM sees about one read and one
-// write of every image.
+// Batched unitary 2D DFT for square N (64, 96, 128, 160, 192, 256, 320, 384) as one
+// persistent launch over band tasks, with the intermediate image kept in L2, so that HBM
+// sees about one read and one write of every image.
 //
 // The image splits into NB = N / BAND bands of BAND rows and NB bands of BAND columns
-// (BAND = 16). A row task (image i, band b) transforms rows
-// [BAND b, BAND (b + 1)) of in[i] and writes them, unscaled, to out[i]; a column task
-// transforms columns [BAND b, BAND (b + 1)) of out[i] in place and scales by 1 / N (the two
-// unitary 1 / sqrt N factors). Tasks are taken in a fixed order from one counter: the row
-// tasks of image i come L images ahead of its column tasks (L about 1.5 times the CTAs
-// over 2 NB), so a column task almost never waits, and the L images between the two passes
-// (a few MB) stay in L2. A column task waits until the NB row tasks of its image have
-// published (a per-image counter, release / acquire at GPU scope; the wait is bounded). A
-// row task never waits, and every task waits only on tasks taken before it, so the launch
-// cannot deadlock. Small CTAs (BAND x T threads, at most 35 KB of shared memory, four or
-// eight per SM) let the other CTAs of an SM run through one CTA's barrier and memory waits.
-//
-// Both task kinds run the four-step FFT N = T x R per line: a length-R DFT in registers over
-// the elements t + T n2, twiddles w_N^(t k2), a transpose through shared memory, length-T
-// DFTs.
-//   rows:    T threads per row (a half-warp or a quarter-warp), loads and stores of T
-//            consecutive values; the transpose through the row's own region;
-//   columns: thread (t, c) for column c of the band, every load and store of BAND
-//            consecutive values of one row, the transpose through the band's N x BAND buffer.
-// Global loads bypass L1 (the data of a column task was written by other SMs).
+// (BAND = 16). A row task (image i, band b) transforms rows [BAND b, BAND (b + 1)) of in[i]
+// and writes them, unscaled, to out[i]; a column task transforms columns
+// [BAND b, BAND (b + 1)) of out[i] in place and scales by 1 / N (the two unitary 1 / sqrt N
+// factors); both are the band transforms of tts_fft_band.cuh. Tasks are taken in a fixed
+// order from one counter: the row tasks of image i come L images ahead of its column tasks
+// (L about 1.5 times the CTAs over 2 NB), so a column task almost never waits, and the L
+// images between the two passes (a few MB) stay in L2. A column task waits until the NB row
+// tasks of its image have published (a per-image counter: thread 0 of a row task's CTA
+// raises it with a release reduction after the barrier that follows the task's stores,
+// thread 0 of a column task's CTA reads it with acquire loads; GPU scope; the wait is
+// bounded). A row task never waits, and every task waits only on tasks taken before it, so
+// the launch cannot deadlock. Small CTAs (BAND x T threads, at most 52 KB of shared memory,
+// two to eight per SM) let the other CTAs of an SM run through one CTA's barrier and memory
+// waits.
 #include <algorithm>
 #include <cstdint>
 #include <mutex>
 
-#include "tts_fft_small.cuh"
+#include "tts_fft_band.cuh"
 #include "tts_internal.cuh"
 
 namespace {
 
-// T x R = N (T a power of two, threads per line in a row task; R the register length); BAND
-// rows (row task) or columns (column task) per task; NT = BAND T threads, one line of the
-// band each; MINB CTAs per SM (registers: 64 for R <= 16, more for the longer R)
-template <int N>
-struct Shape;
-template <>
-struct Shape<64> {
-  static constexpr int T = 8, R = 8, BAND = 16, NT = 128, MINB = 8;
-};
-template <>
-struct Shape<96> {
-  static constexpr int T = 8, R = 12, BAND = 16, NT = 128, MINB = 6;
-};
-template <>
-struct Shape<128> {
-  static constexpr int T = 8, R = 16, BAND = 16, NT = 128, MINB = 8;
-};
-template <>
-struct Shape<160> {
-  static constexpr int T = 16, R = 10, BAND = 16, NT = 256, MINB = 4;
-};
-template <>
-struct Shape<192> {
-  static constexpr int T = 16, R = 12, BAND = 16, NT = 256, MINB = 3;
-};
-template <>
-struct Shape<256> {
-  static constexpr int T = 16, R = 16, BAND = 16, NT = 256, MINB = 4;
-};
-template <>
-struct Shape<320> {
-  static constexpr int T = 16, R = 20, BAND = 16, NT = 256, MINB = 2;
-};
-template <>
-struct Shape<384> {
-  static constexpr int T = 16, R = 24, BAND = 16, NT = 256, MINB = 2;
-};
-
-using fftsmall::twn;
-
-template <int L, bool INV>
-__device__ __forceinline__ void dft_small(float2* v, const float2* W, int N) {
-  fftsmall::Dft<L, INV>::run(v, W, N);
-}
+using fftband::Shape;
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
@@ -111,24 +62,15 @@ __device__ __forceinline__ int decode(int q, int NB, int L, int batch, int* band
   return mid_imgs + qq / NB;
 }
 
-// Row regions of a row task: with quarter-warp rows (T = 8) a pad of 64 bytes puts the two
-// rows of a half-warp on different banks.
-template <int N>
-__host__ __device__ constexpr int row_stride() {
-  return N + (Shape<N>::T == 8 ? 8 : 0);
-}
-
 template <int N, bool INV>
 __global__ void __launch_bounds__(Shape<N>::NT, Shape<N>::MINB)
     fft2d_square_kernel(const float2* in, float2* out, int batch, int L, const float2* __restrict__ Wg, float scale,
                         int* ctrl, int* err) {
-  constexpr int T = Shape<N>::T, R = Shape<N>::R, BAND = Shape<N>::BAND, NT = Shape<N>::NT;
-  constexpr int J = (R + T - 1) / T, NB = N / BAND;   // second-stage lines per thread
-  static_assert(BAND * T == NT, "one line of the band per thread");
-  constexpr int RS = row_stride<N>();       // row regions of a row task in S
+  constexpr int BAND = Shape<N>::BAND, NT = Shape<N>::NT, NB = N / BAND;
+  static_assert(BAND * Shape<N>::T == NT && N % BAND == 0, "one line of the band per thread");
   extern __shared__ __align__(16) unsigned char smem[];
-  float2* S = (float2*)smem;                // transposes: BAND x RS (rows), N x BAND (columns)
-  float2* W = S + BAND * RS;                // fsz(N), padded
+  float2* S = (float2*)smem;                                 // band transposes
+  float2* W = S + BAND * fftband::row_stride<N>();           // fsz(N), padded
   __shared__ int s_task[2];
   int* next = ctrl;                         // task counter
   int* done = ctrl + 1;                     // row tasks published, per image
@@ -156,38 +98,10 @@ __global__ void __launch_bounds__(Shape<N>::NT, Shape<N>::MINB)
     const int img = decode(q, NB, L, batch, &band, &col);
     float2* ob = out + (size_t)img * N * N;
     if (!col) {
-      // ---- row task: group g = tid / T takes row g of the band
-      const int g = tid / T, t = tid % T;
-      float2 v[R];
-      const float2* src = in + (size_t)img * N * N + (size_t)(band * BAND + g) * N + t;
-#pragma unroll
-      for (int n2 = 0; n2 < R; ++n2) v[n2] = __ldcs(src + T * n2);
-      float2* sc = S + g * RS;
-      dft_small<R, INV>(v, W, N);
-#pragma unroll
-      for (int k2 = 1; k2 < R; ++k2) v[k2] = cmul(v[k2], twn<INV>(W, t * k2));   // t k2 < N
-      // Y[n1 = t][k2] to slot k2 T + (n1 ^ (k2 mod T))
-#pragma unroll
-      for (int k2 = 0; k2 < R; ++k2) sc[k2 * T + (t ^ (k2 % T))] = v[k2];
-      __syncwarp();
-      float2* dst = ob + (size_t)(band * BAND + g) * N;
-#pragma unroll
-      for (int j = 0; j < J; ++j) {
-        const int k2 = t + T * j;
-        if (J * T == R || k2 < R) {
-          float2 u[T];
-#pragma unroll
-          for (int n1 = 0; n1 < T; ++n1) u[n1] = sc[k2 * T + (n1 ^ (k2 % T))];
-          dft_small<T, INV>(u, W, N);
-#pragma unroll
-          for (int k1 = 0; k1 < T; ++k1) __stcg(dst + k2 + R * k1, u[k1]);   // X[k2 + R k1]
-        }
-      }
+      fftband::row_band<N, INV, false>(in + (size_t)img * N * N, ob, N, band * BAND, W, S);
       if (tid == 0) pub = img;
     } else {
-      // ---- column task: c = tid mod BAND is column band * BAND + c, t = tid / BAND the
-      // four-step index (a warp holds 32 / BAND values of t)
-      if (tid == 0) {
+      if (tid == 0) {   // acquire the NB row tasks of the image
         const long long t0 = clock64();
         while (ld_acquire(done + img) < NB) {
           if (clock64() - t0 > 2000000000LL) {
@@ -197,38 +111,11 @@ __global__ void __launch_bounds__(Shape<N>::NT, Shape<N>::MINB)
         }
       }
       __syncthreads();
-      const int c = tid % BAND, t = tid / BAND;
-      float2* cb = ob + band * BAND + c;
-      float2 v[R];
-#pragma unroll
-      for (int n2 = 0; n2 < R; ++n2) v[n2] = __ldcg(cb + (size_t)(t + T * n2) * N);
-      dft_small<R, INV>(v, W, N);
-#pragma unroll
-      for (int k2 = 1; k2 < R; ++k2) v[k2] = cmul(v[k2], twn<INV>(W, t * k2));
-#pragma unroll
-      for (int k2 = 0; k2 < R; ++k2) S[(k2 * T + t) * BAND + c] = v[k2];
-      __syncthreads();
-#pragma unroll
-      for (int j = 0; j < J; ++j) {
-        const int k2 = t + T * j;
-        if (J * T == R || k2 < R) {
-          float2 u[T];
-#pragma unroll
-          for (int n1 = 0; n1 < T; ++n1) u[n1] = S[(k2 * T + n1) * BAND + c];
-          dft_small<T, INV>(u, W, N);
-#pragma unroll
-          for (int k1 = 0; k1 < T; ++k1) __stcs(cb + (size_t)(k2 + R * k1) * N, cscale(u[k1], scale));
-        }
-      }
+      fftband::col_band<N, INV, false>(ob, N, band * BAND, W, S, scale);
     }
     if (tid == 0) s_task[(it + 1) & 1] = nq;
     __syncthreads();   // the task's stores are issued; S and s_task[it & 1] are free
   }
-}
-
-template <int N>
-constexpr int smem_bytes() {
-  return (int)sizeof(float2) * (Shape<N>::BAND * row_stride<N>() + N + (N - 1) / 16);   // S and fsz(N)
 }
 
 // Stream-ordered memory for the task counters of a call, from a pool of this library that
@@ -261,7 +148,7 @@ cudaMemPool_t ctrl_pool() {
 template <int N, bool INV>
 int launch_t(const float2* in, float2* out, int batch, const float2* W, int* err, cudaStream_t st) {
   constexpr int NB = N / Shape<N>::BAND;
-  constexpr int smem = smem_bytes<N>();
+  constexpr int smem = fftband::smem_bytes<N>();
   static int grid = 0;
   if (grid == 0) {
     if (cudaFuncSetAttribute(fft2d_square_kernel<N, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=

@@ -440,6 +440,11 @@ int launch_ridge(const double2* G, const double2* h, int R, double2* gamma, cuda
 bool fft2d_square_ok(int Nx, int Ny);
 int launch_fft2d_square(const float2* in, float2* out, int batch, int N, int inverse, const float2* W, int* err,
                         cudaStream_t st);
+// batched 2D DFT for other Nx x Ny whose line lengths both have a band shape: a row-band and a
+// column-band launch per group of images that fits L2 (tts_fft_lines.cu)
+bool fft2d_lines_ok(int Nx, int Ny);
+int launch_fft2d_lines(const float2* in, float2* out, int batch, int Nx, int Ny, int inverse, const float2* Wx,
+                       const float2* Wy, cudaStream_t st);
 // 2D DFT as tensor-core matrix products (tts_dft_gemm.cu)
 bool dft_gemm_size_ok(int N);
 // Inverse unitary DFT of the acquired rows (mask lines) of a frame, Yt = y_S conj(F_Ny),
