@@ -2,6 +2,7 @@
 // batched unitary 2D DFT.
 #include <algorithm>
 
+#include "tts_fft_band.cuh"
 #include "tts_internal.cuh"
 
 namespace {
@@ -114,6 +115,103 @@ __device__ __forceinline__ int upper_bound_u64(const unsigned long long* Q, int 
   return lo;
 }
 
+// Row scores of the informative sampler for a line length with a band shape: per pass, one
+// group of T threads per column r of A (up to `cols` columns at once): the column's length-N
+// DFT Ahat[:, r] = F_N a_r by the four-step FFT of tts_fft_band.cuh (or the column itself
+// with no_fft), its squared norm by a reduction over the group, and the weights
+// |Ahat_kr|^2 / ||ahat_r||^2 (1 / N for a zero column) into a cols x N table; then every row
+// k adds its weights in column order to rowacc[k]. buf holds the transposes and the table
+// (cols (row_stride + (N + 16) / 2) float2, within the sampler's FFT buffer).
+template <int N>
+__device__ __forceinline__ void sampler_scores_band(const float2* __restrict__ A, int R, int no_fft, const float2* W,
+                                                    float2* buf, float* rowacc, int cols) {
+  using fftband::Shape;
+  constexpr int T = Shape<N>::T, RL = Shape<N>::R, J = (RL + T - 1) / T, RS = fftband::row_stride<N>();
+  constexpr int WS = N + 16;   // weight-table row stride (floats): neighbouring groups on other banks
+  float* Wt = (float*)(buf + cols * RS);
+  const int tid = threadIdx.x, g = tid / T, t = tid % T;
+  const unsigned gmask = T == 32 ? 0xffffffffu : (((1u << T) - 1u) << ((tid & 31) & ~(T - 1)));
+  for (int r0 = 0; r0 < R; r0 += cols) {
+    const int nc = min(cols, R - r0);
+    if (g < nc) {   // uniform over the group
+      const float2* a = A + r0 + g;
+      float2 v[RL];
+#pragma unroll
+      for (int n2 = 0; n2 < RL; ++n2) v[n2] = a[(size_t)(t + T * n2) * R];
+      float* wrow = Wt + g * WS;
+      if (no_fft) {
+        float s = 0.f;
+#pragma unroll
+        for (int n2 = 0; n2 < RL; ++n2) s += cabs2(v[n2]);
+#pragma unroll
+        for (int o = T / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
+        const float inv = s > 0.f ? 1.f / s : 0.f;
+#pragma unroll
+        for (int n2 = 0; n2 < RL; ++n2) wrow[t + T * n2] = inv > 0.f ? cabs2(v[n2]) * inv : 1.f / (float)N;
+      } else {
+        float2* sc = buf + g * RS;
+        fftband::dft_small<RL, false>(v, W, N);
+#pragma unroll
+        for (int k2 = 1; k2 < RL; ++k2) v[k2] = cmul(v[k2], fftsmall::twn<false>(W, t * k2));
+#pragma unroll
+        for (int k2 = 0; k2 < RL; ++k2) sc[k2 * T + (t ^ (k2 % T))] = v[k2];
+        __syncwarp(gmask);
+        float2 u[J][T];
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const int k2 = t + T * j;
+          if (J * T == RL || k2 < RL) {
+#pragma unroll
+            for (int n1 = 0; n1 < T; ++n1) u[j][n1] = sc[k2 * T + (n1 ^ (k2 % T))];
+            fftband::dft_small<T, false>(u[j], W, N);
+#pragma unroll
+            for (int k1 = 0; k1 < T; ++k1) s += cabs2(u[j][k1]);
+          }
+        }
+#pragma unroll
+        for (int o = T / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
+        const float inv = s > 0.f ? 1.f / s : 0.f;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const int k2 = t + T * j;
+          if (J * T == RL || k2 < RL) {
+#pragma unroll
+            for (int k1 = 0; k1 < T; ++k1)
+              wrow[k2 + RL * k1] = inv > 0.f ? cabs2(u[j][k1]) * inv : 1.f / (float)N;   // row k2 + RL k1
+          }
+        }
+      }
+    }
+    __syncthreads();
+    for (int k = tid; k < N; k += blockDim.x) {
+      float acc = rowacc[k];
+      for (int c = 0; c < nc; ++c) acc += Wt[c * WS + k];
+      rowacc[k] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// the band-shape lengths: scores through sampler_scores_band; false for any other Nx
+__device__ __forceinline__ bool sampler_scores_fast(int Nx, const float2* A, int R, int no_fft, const float2* W,
+                                                    float2* buf, float* rowacc, int fft_cols) {
+  auto cols_for = [&](int T) { return min(min((int)blockDim.x / T, R), fft_cols); };
+  switch (Nx) {
+    case 64: sampler_scores_band<64>(A, R, no_fft, W, buf, rowacc, cols_for(8)); return true;
+    case 96: sampler_scores_band<96>(A, R, no_fft, W, buf, rowacc, cols_for(8)); return true;
+    case 120: sampler_scores_band<120>(A, R, no_fft, W, buf, rowacc, cols_for(8)); return true;
+    case 128: sampler_scores_band<128>(A, R, no_fft, W, buf, rowacc, cols_for(8)); return true;
+    case 160: sampler_scores_band<160>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
+    case 192: sampler_scores_band<192>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
+    case 240: sampler_scores_band<240>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
+    case 256: sampler_scores_band<256>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
+    case 320: sampler_scores_band<320>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
+    case 384: sampler_scores_band<384>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
+    default: return false;
+  }
+}
+
 __device__ __forceinline__ void sampler_run(const SamplerJob& job, unsigned char* smem_raw) {
   const float2* __restrict__ A = job.A;
   const int Nx = job.Nx, Ny = job.Ny, R = job.R;
@@ -150,7 +248,8 @@ __device__ __forceinline__ void sampler_run(const SamplerJob& job, unsigned char
     __syncthreads();
     const FftPlan plan = fft_plan(Nx);
     const int ld = fsz(Nx) | 1;   // padded column stride (odd) in shared memory
-    for (int r0 = 0; r0 < R; r0 += fft_cols) {
+    const bool fast = sampler_scores_fast(Nx, A, R, job.no_fft, W, buf, rowacc, fft_cols);
+    for (int r0 = 0; r0 < (fast ? 0 : R); r0 += fft_cols) {
       const int nc = min(fft_cols, R - r0);
       // coalesced along the rows of A, transposed into columns
       for (int base = tid; base < nc * Nx; base += 8 * blockDim.x) {
