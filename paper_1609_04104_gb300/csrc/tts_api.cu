@@ -204,7 +204,40 @@ int handle_create(const tts_config* cfg, void* mem, tts_handle** out) {
   return TTS_OK;
 }
 
-int handle_stage_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line_mask, int flags, FrameParams* pout) {
+// Gathers the acquired rows of a host frame (compact |S| x Ny, or a full Nx x Ny frame) into
+// the next pinned staging buffer, checking every value for NaN/Inf on the way; *out is the
+// buffer. The buffer's previous copy has completed before it is overwritten.
+static int gather_host_rows(tts_handle* h, const float* y, const uint8_t* m, bool full, float2** out) {
+  const int Nx = h->cfg.Nx, Ny = h->cfg.Ny;
+  const int b = h->hstage_next;
+  if (!h->hstage[b]) {
+    CK(cudaMallocHost((void**)&h->hstage[b], sizeof(float2) * (size_t)Nx * Ny));
+    CK(cudaEventCreateWithFlags(&h->hstage_done[b], cudaEventDisableTiming));
+  } else {
+    CK(cudaEventSynchronize(h->hstage_done[b]));
+  }
+  float* dst = (float*)h->hstage[b];
+  const size_t row = 2 * (size_t)Ny;   // floats per row
+  uint32_t bad = 0;
+  for (int i = 0, m_ = 0; i < Nx; ++i) {
+    if (!m[i]) continue;
+    const float* src = y + row * (full ? (size_t)i : (size_t)m_);
+    float* d = dst + row * (size_t)m_;
+    memcpy(d, src, sizeof(float) * row);
+    for (size_t e = 0; e < row; ++e) {   // exponent all ones: Inf or NaN
+      uint32_t u;
+      memcpy(&u, d + e, sizeof(u));
+      bad |= (uint32_t)((u & 0x7f800000u) == 0x7f800000u);
+    }
+    ++m_;
+  }
+  if (bad) return fail(TTS_ENONFINITE, "frame holds NaN or Inf; not applied%s");
+  *out = h->hstage[b];
+  return TTS_OK;
+}
+
+int handle_stage_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line_mask, int flags, FrameParams* pout,
+                       bool pinned_gather) {
   const int Nx = h->cfg.Nx, Ny = h->cfg.Ny;
   FrameParams p = h->fp;
   p.full_frame = (flags & TTS_FULL_FRAME) ? 1 : 0;
@@ -226,6 +259,20 @@ int handle_stage_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line
     int s = 0;
     for (int i = 0; i < Nx; ++i) s += m[i] != 0;
     if (s == 0) return fail(TTS_EINVAL, "the line mask selects no line%s");
+    if (pinned_gather) {
+      float2* staged = nullptr;
+      const int rg = gather_host_rows(h, (const float*)y_rows, m, (flags & TTS_FULL_FRAME) != 0, &staged);
+      if (rg != TTS_OK) return rg;
+      if (line_mask) CK(cudaMemcpyAsync(h->dmask_push, m, Nx, cudaMemcpyHostToDevice, h->stream));
+      CK(cudaMemcpyAsync(h->ystage, staged, sizeof(float2) * (size_t)s * Ny, cudaMemcpyHostToDevice, h->stream));
+      CK(cudaEventRecord(h->hstage_done[h->hstage_next], h->stream));
+      h->hstage_next ^= 1;
+      p.mask = line_mask ? h->dmask_push : h->dmask_next;
+      p.yrows = h->ystage;
+      p.full_frame = 0;   // compact rows on the device
+      *pout = p;
+      return TTS_OK;
+    }
     const size_t nrows_in = (flags & TTS_FULL_FRAME) ? (size_t)Nx : (size_t)s;
     const float* f = (const float*)y_rows;
     for (int i = 0, m_ = 0; i < Nx; ++i) {
@@ -290,6 +337,10 @@ void tts_destroy(tts_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   mc_detach(h);
+  for (int b = 0; b < 2; ++b) {
+    if (h->hstage[b]) cudaFreeHost(h->hstage[b]);
+    if (h->hstage_done[b]) cudaEventDestroy(h->hstage_done[b]);
+  }
   if (h->own_mem) cudaFree(h->dmem);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -379,7 +430,7 @@ int tts_push_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line_mas
   if (h->cfg.row_dft != TTS_ROWDFT_FFT && (flags & TTS_DEVICE_PTRS) && (uintptr_t)y_rows % 16 != 0)
     return fail(TTS_EINVAL, "the tensor-core row transform reads 16-byte aligned device rows%s");
   FrameParams p;
-  const int rs = handle_stage_frame(h, y_rows, line_mask, flags, &p);
+  const int rs = handle_stage_frame(h, y_rows, line_mask, flags, &p, true);
   if (rs != TTS_OK) return rs;
   if (h->cfg.row_dft != TTS_ROWDFT_FFT) {
     // the acquired rows' transform on the tensor cores, straight into Yt
@@ -551,6 +602,8 @@ int tts_load(tts_handle* h, const void* buf, size_t len) {
   CK(cudaMemcpyAsync(h->fp.B, i, sizeof(float2) * Ny * R, cudaMemcpyHostToDevice, h->stream));
   i += sizeof(float2) * Ny * R;
   CK(cudaMemcpyAsync(h->fp.gamma, i, sizeof(float2) * R, cudaMemcpyHostToDevice, h->stream));
+  // the drawn mask on the device too (a push with no mask reads the device copy)
+  CK(cudaMemcpyAsync(h->dmask_next, h->next_host.data(), Nx, cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   h->t = hd.t;
   h->have_next = hd.have_next != 0;

@@ -30,6 +30,11 @@ struct tts_handle {
   bool in_engine = false;       // a slot of an engine (no coil maps)
   std::vector<uint8_t> next_host;
   MultiCoil* mc = nullptr;      // set by tts_set_coil_maps
+  // pinned host staging of the acquired rows of host pushes (tts_push_frame): two buffers
+  // of Nx x Ny, each reused once the copy recorded by its event has completed
+  float2* hstage[2] = {nullptr, nullptr};
+  cudaEvent_t hstage_done[2] = {nullptr, nullptr};
+  int hstage_next = 0;
 };
 
 // Validates a configuration (message through tts_last_error on failure).
@@ -42,8 +47,13 @@ size_t handle_footprint(const tts_config& cfg);
 // cfg->cuda_stream (or a stream of its own) and is complete on return.
 int handle_create(const tts_config* cfg, void* mem, tts_handle** out);
 // Fills p (a copy of h->fp) with the frame's mask and rows, staging host inputs into the
-// handle's device buffers on h->stream, with the checks of tts_push_frame.
-int handle_stage_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line_mask, int flags, FrameParams* p);
+// handle's device buffers on h->stream, with the checks of tts_push_frame. With
+// pinned_gather, host rows go through the handle's pinned staging (only the acquired rows,
+// also of a full frame, checked for NaN/Inf while they are gathered) and a line mask of
+// NULL is read from the device copy of the last draw; otherwise the rows are copied from
+// y_rows as they are.
+int handle_stage_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line_mask, int flags, FrameParams* p,
+                       bool pinned_gather = false);
 // Philox counter of the next draw: stream_id in the high bits, frames processed below.
 uint64_t handle_draw_counter(const tts_handle* h);
 // Lines a draw at this rate keeps: max(central, round(rate Nx)).

@@ -543,12 +543,12 @@ class Tracker:
     def set_coil_maps(self, maps):
         tts_set_coil_maps(self.h, np.ascontiguousarray(maps, np.complex64) if isinstance(maps, np.ndarray) else maps)
 
-    def push_frame(self, y_rows, line_mask=None):
+    def push_frame(self, y_rows, line_mask=None, full_frame=False):
         if isinstance(y_rows, np.ndarray):
             y_rows = np.ascontiguousarray(y_rows, np.complex64)
         if isinstance(line_mask, np.ndarray):
             line_mask = np.ascontiguousarray(line_mask, np.uint8)
-        tts_push_frame(self.h, y_rows, line_mask)
+        tts_push_frame(self.h, y_rows, line_mask, full_frame)
 
     def image(self, t=None, out=None):
         if t is None:
