@@ -89,19 +89,18 @@ __device__ __forceinline__ void dft_small(float2* v, const float2* W, int N) {
   fftsmall::Dft<L, INV>::run(v, W, N);
 }
 
-// Rows [r0, r0 + BAND) (with RAGGED, those below nrows) of length N: src rows to dst rows
-// (row stride N), unscaled, stored with L2 caching (they are read back soon). W: the padded
-// length-N table.
-template <int N, bool INV, bool RAGGED>
-__device__ __forceinline__ void row_band(const float2* src, float2* dst, int nrows, int r0, const float2* W, float2* S) {
+// Rows [r0, r0 + BAND) (with RAGGED, those below nrows) of length N, element j of row i
+// given by load(i, j), to dst rows (row stride N), unscaled, stored with L2 caching (they are
+// read back soon). W: the padded length-N table.
+template <int N, bool INV, bool RAGGED, typename Load>
+__device__ __forceinline__ void row_band_f(Load load, float2* dst, int nrows, int r0, const float2* W, float2* S) {
   constexpr int T = Shape<N>::T, R = Shape<N>::R, J = (R + T - 1) / T;
   const int g = threadIdx.x / T, t = threadIdx.x % T;
   const int row = r0 + g;
   if (RAGGED && row >= nrows) return;   // uniform over the row's T threads
   float2 v[R];
-  const float2* s = src + (size_t)row * N + t;
 #pragma unroll
-  for (int n2 = 0; n2 < R; ++n2) v[n2] = __ldcs(s + T * n2);
+  for (int n2 = 0; n2 < R; ++n2) v[n2] = load(row, t + T * n2);
   float2* sc = S + g * row_stride<N>();
   dft_small<R, INV>(v, W, N);
 #pragma unroll
@@ -126,9 +125,57 @@ __device__ __forceinline__ void row_band(const float2* src, float2* dst, int nro
   }
 }
 
+// row_band_f over the rows of src (row stride N), read streaming
+template <int N, bool INV, bool RAGGED>
+__device__ __forceinline__ void row_band(const float2* src, float2* dst, int nrows, int r0, const float2* W, float2* S) {
+  row_band_f<N, INV, RAGGED>([src](int i, int j) { return __ldcs(src + (size_t)i * N + j); }, dst, nrows, r0, W, S);
+}
+
 // Columns [c0, c0 + BAND) (with RAGGED, those below ncols) of length N of an image with row
-// stride ncols, in place, scaled by `scale`, stored streaming. Every thread of the CTA must
-// call it (it synchronises the CTA once, after its shared-memory stores).
+// stride ncols; output k of column c goes to store(k, c, value) unscaled. Every thread of the
+// CTA must call it (it synchronises the CTA once, after its shared-memory stores).
+template <int N, bool INV, bool RAGGED, typename Store>
+__device__ __forceinline__ void col_band_f(const float2* img, int ncols, int c0, const float2* W, float2* S,
+                                           Store store) {
+  constexpr int T = Shape<N>::T, R = Shape<N>::R, BAND = Shape<N>::BAND, J = (R + T - 1) / T;
+  const int c = threadIdx.x % BAND, t = threadIdx.x / BAND;
+  const bool live = !RAGGED || c0 + c < ncols;
+  const float2* cb = img + c0 + c;
+  const float2* p = cb + (size_t)t * ncols;   // rows t + T n2 of the column
+  const size_t step = (size_t)T * ncols;
+  float2 v[R];
+  if (live) {
+#pragma unroll
+    for (int n2 = 0; n2 < R; ++n2) v[n2] = __ldcg(p + n2 * step);
+  } else {
+#pragma unroll
+    for (int n2 = 0; n2 < R; ++n2) v[n2] = make_float2(0.f, 0.f);
+  }
+  dft_small<R, INV>(v, W, N);
+#pragma unroll
+  for (int k2 = 1; k2 < R; ++k2) v[k2] = cmul(v[k2], twn<INV>(W, t * k2));
+#pragma unroll
+  for (int k2 = 0; k2 < R; ++k2) S[(k2 * T + t) * BAND + c] = v[k2];
+  __syncthreads();
+  if (!live) return;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int k2 = t + T * j;
+    if (J * T == R || k2 < R) {
+      float2 u[T];
+#pragma unroll
+      for (int n1 = 0; n1 < T; ++n1) u[n1] = S[(k2 * T + n1) * BAND + c];
+      dft_small<T, INV>(u, W, N);
+#pragma unroll
+      for (int k1 = 0; k1 < T; ++k1) store(k2 + R * k1, c0 + c, u[k1]);   // X[k2 + R k1]
+    }
+  }
+}
+
+// Columns [c0, c0 + BAND) (with RAGGED, those below ncols) of length N of an image with row
+// stride ncols, in place, scaled by `scale`, stored streaming: the same transform as
+// col_band_f with the output addressed by pointer steps (fewer live registers). Every thread
+// of the CTA must call it.
 template <int N, bool INV, bool RAGGED>
 __device__ __forceinline__ void col_band(float2* img, int ncols, int c0, const float2* W, float2* S, float scale) {
   constexpr int T = Shape<N>::T, R = Shape<N>::R, BAND = Shape<N>::BAND, J = (R + T - 1) / T;

@@ -7,7 +7,10 @@
 // Per frame (all on the handle's stream, FP32 data, FP64 scalars and ridge system):
 //   begin:   w <- lf w + 1, rho = mu / w; anchors A0 = A, B0 = B
 //   per MM iteration (Gauss-Seidel gamma -> A -> B):
-//     (S1)  Z[c][r] = H_c .* a_r b_r^T; batched 2D DFT; Phi rows = Z[c][r][S, :]
+//     (S1)  Z[c][r] = H_c .* a_r b_r^T; batched 2D DFT; Phi rows = Z[c][r][S, :] kept
+//           compact (Zs, |S| rows per image): for band-shape Nx, Ny the rows of the
+//           rank-one images are generated inside the row transform and the column
+//           transform stores only the rows of S
 //           G = Phi^H Phi + mu I (FP32 per acquired row, FP64 across rows), h = Phi^H y;
 //           gamma = G^{-1} h (FP32 Gauss-Jordan + float-float refinement, FP64 grade)
 //     (S2)  E_c = P_Omega(y_c - sum_r gamma_r Z[c][r]) (zero-filled), batched inverse DFT,
@@ -23,6 +26,7 @@
 
 #include <algorithm>
 
+#include "tts_fft_band.cuh"
 #include "tts_handle.cuh"
 
 namespace {
@@ -43,38 +47,76 @@ __global__ void mc_rank1_kernel(const float2* __restrict__ H, const float2* __re
 }
 
 // Partial Gram and right-hand side of one acquired row (c, m): over j < Ny,
-// G[q][r] += conj(Phi_q) Phi_r, h[q] += conj(Phi_q) y with Phi_r = Z[c][r][S_m][j].
-// One CTA per (c, m); the R x Ny block of Phi staged in shared memory.
-__global__ void __launch_bounds__(kT) mc_gram_kernel(const float2* __restrict__ Z, const float2* __restrict__ y,
-                                                     const int* __restrict__ rows, int C, int R, int Nx, int Ny,
-                                                     int s, double2* __restrict__ part) {
+// G[q][r] += conj(Phi_q) Phi_r, h[q] += conj(Phi_q) y with Phi_r = Zs[c R + r][m][j] (the
+// transformed rank-one images on the rows of S, compact). One CTA per (c, m); the R x Ny
+// block of Phi staged in shared memory.
+__global__ void __launch_bounds__(kT) mc_gram_kernel(const float2* __restrict__ Zs, const float2* __restrict__ y,
+                                                     int C, int R, int Ny, int s, double2* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int LD = Ny + 1;            // odd row stride: consecutive r hit distinct banks
   float2* ph = (float2*)smem_raw;   // R x LD
   float2* yr = ph + R * LD;         // Ny
   const int cm = blockIdx.x, c = cm / s, m = cm - c * s;
-  const size_t NN = (size_t)Nx * Ny;
-  const int row = rows[m];
   for (int e = threadIdx.x; e < R * Ny; e += blockDim.x) {
     const int r = e / Ny, j = e - r * Ny;
-    ph[r * LD + j] = Z[((size_t)c * R + r) * NN + (size_t)row * Ny + j];
+    ph[r * LD + j] = Zs[(((size_t)c * R + r) * s + m) * Ny + j];
   }
   for (int j = threadIdx.x; j < Ny; j += blockDim.x) yr[j] = y[((size_t)c * s + m) * Ny + j];
   __syncthreads();
   const int E = R * R + R;
   double2* out = part + (size_t)cm * E;
-  for (int e = threadIdx.x; e < E; e += blockDim.x) {
-    const int q = e < R * R ? e / R : e - R * R;
-    const float2* b = e < R * R ? ph + (e - q * R) * LD : yr;
-    const float2* a = ph + q * LD;
+  // G in 2 x 2 register tiles: tile (qt, rt) holds q in {qt, qt + hR}, r in {rt, rt + hR}
+  // (rows hR apart: the LD-strided loads of a warp land on distinct banks). Every output
+  // sums even j and odd j in its own accumulators, in increasing j.
+  const int hR = (R + 1) / 2;
+  for (int tile = threadIdx.x; tile < hR * hR; tile += blockDim.x) {
+    const int qt = tile / hR, rt = tile - qt * hR;
+    const int q[2] = {qt, qt + hR}, r[2] = {rt, rt + hR};
+    const bool qv1 = q[1] < R, rv1 = r[1] < R;
+    const float2* a0 = ph + q[0] * LD;
+    const float2* a1 = ph + (qv1 ? q[1] : q[0]) * LD;
+    const float2* b0 = ph + r[0] * LD;
+    const float2* b1 = ph + (rv1 ? r[1] : r[0]) * LD;
+    float2 e0[4], e1[4];   // outputs (q0 r0, q0 r1, q1 r0, q1 r1), even / odd j
+#pragma unroll
+    for (int o = 0; o < 4; ++o) e0[o] = e1[o] = make_float2(0.f, 0.f);
+    int j = 0;
+    for (; j + 1 < Ny; j += 2) {
+      const float2 x0 = a0[j], x1 = a1[j], y0 = b0[j], y1 = b1[j];
+      const float2 u0 = a0[j + 1], u1 = a1[j + 1], w0 = b0[j + 1], w1 = b1[j + 1];
+      cfmac(e0[0], x0, y0);
+      cfmac(e1[0], u0, w0);
+      cfmac(e0[1], x0, y1);
+      cfmac(e1[1], u0, w1);
+      cfmac(e0[2], x1, y0);
+      cfmac(e1[2], u1, w0);
+      cfmac(e0[3], x1, y1);
+      cfmac(e1[3], u1, w1);
+    }
+    if (j < Ny) {
+      cfmac(e0[0], a0[j], b0[j]);
+      cfmac(e0[1], a0[j], b1[j]);
+      cfmac(e0[2], a1[j], b0[j]);
+      cfmac(e0[3], a1[j], b1[j]);
+    }
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      const int qq = q[o >> 1], rr = r[o & 1];
+      if (qq < R && rr < R)
+        out[qq * R + rr] = make_double2((double)e0[o].x + (double)e1[o].x, (double)e0[o].y + (double)e1[o].y);
+    }
+  }
+  // h: conj(Phi_q) y
+  for (int qq = threadIdx.x; qq < R; qq += blockDim.x) {
+    const float2* a = ph + qq * LD;
     float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
     int j = 0;
     for (; j + 1 < Ny; j += 2) {
-      cfmac(acc0, a[j], b[j]);
-      cfmac(acc1, a[j + 1], b[j + 1]);
+      cfmac(acc0, a[j], yr[j]);
+      cfmac(acc1, a[j + 1], yr[j + 1]);
     }
-    if (j < Ny) cfmac(acc0, a[j], b[j]);
-    out[e] = make_double2((double)acc0.x + (double)acc1.x, (double)acc0.y + (double)acc1.y);
+    if (j < Ny) cfmac(acc0, a[j], yr[j]);
+    out[R * R + qq] = make_double2((double)acc0.x + (double)acc1.x, (double)acc0.y + (double)acc1.y);
   }
 }
 
@@ -106,9 +148,10 @@ __global__ void mc_gram_reduce_kernel(const double2* __restrict__ part, int npar
   }
 }
 
-// Zero-filled coil residuals: E_c[S_m][j] = y_c[m][j] - sum_r gamma_r Zf[c][r][S_m][j] where
-// Zf holds the transformed rank-one images (gamma from FP64), other rows 0. With Zx set
-// (the refresh), the model value is Zx[c][S_m][j] instead of the gamma-weighted sum.
+// Zero-filled coil residuals: E_c[S_m][j] = y_c[m][j] - sum_r gamma_r Zs[c][r][m][j] where
+// Zs holds the transformed rank-one images on the rows of S, compact (gamma from FP64),
+// other rows 0. With Zx set (the refresh), the model value is Zx[c][S_m][j] instead of the
+// gamma-weighted sum.
 __global__ void mc_residual_kernel(const float2* __restrict__ Zf, const float2* __restrict__ Zx,
                                    const double2* __restrict__ gamma_d, const float2* __restrict__ y,
                                    const int* __restrict__ rows, const int* __restrict__ rowpos, int C, int R, int Nx,
@@ -133,7 +176,7 @@ __global__ void mc_residual_kernel(const float2* __restrict__ Zf, const float2* 
       if (Zx) {
         model = Zx[e];
       } else {
-        for (int r = 0; r < R; ++r) cfma(model, g[r], Zf[((size_t)c * R + r) * NN + pix]);
+        for (int r = 0; r < R; ++r) cfma(model, g[r], Zf[(((size_t)c * R + r) * s + m) * Ny + j]);
       }
       v = csub(y[((size_t)c * s + m) * Ny + j], model);
     }
@@ -183,11 +226,21 @@ __global__ void mc_coeff_kernel(const float2* __restrict__ F, int n, int R, cons
                                 double hmax, double lf, double* sf, int abar_slot, int alpha_slot,
                                 float* __restrict__ coef) {
   __shared__ double red[kT];
-  float acc = 0.f;   // per-thread sums in FP32 (as the single-coil frame kernel), the tree in FP64
-  for (int e = threadIdx.x; e < n * R; e += blockDim.x) {
-    const int r = e % R;
+  __shared__ float g2[TTS_MAX_R];   // |gamma_r|^2 from FP64, once per r (FP64 is slow on this part)
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
     const double2 g = gamma_d[r];
-    acc = fmaf(cabs2(F[e]), (float)(g.x * g.x + g.y * g.y), acc);
+    g2[r] = (float)(g.x * g.x + g.y * g.y);
+  }
+  __syncthreads();
+  float acc = 0.f;   // per-thread sums in FP32 (as the single-coil frame kernel), the tree in FP64
+  const int total = n * R, step = blockDim.x;
+  for (int base = threadIdx.x; base < total; base += 8 * step) {
+    float2 v[8];   // eight loads in flight, then the sums in the same order as one at a time
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = base + u * step < total ? F[base + u * step] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (base + u * step < total) acc = fmaf(cabs2(v[u]), g2[(base + u * step) % R], acc);
   }
   red[threadIdx.x] = (double)acc;
   __syncthreads();
@@ -282,6 +335,140 @@ __global__ void mc_check_kernel(const float2* __restrict__ y, size_t n, int* bad
   if (b) atomicOr(bad, 1);
 }
 
+// The rows of S of n transformed images (Nx x Ny each) into Zs, compact (|S| rows each).
+__global__ void mc_compact_kernel(const float2* __restrict__ Z, const int* __restrict__ rows, int n, int Nx, int Ny,
+                                  int s, float2* __restrict__ Zs) {
+  const size_t total = (size_t)n * s * Ny;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t im = e / Ny;
+    const int j = (int)(e - im * Ny);
+    const size_t img = im / s;
+    const int m = (int)(im - img * s);
+    Zs[e] = Z[(img * Nx + rows[m]) * Ny + j];
+  }
+}
+
+// (S1) for band-shape Nx and Ny (tts_fft_band.cuh): the transformed weighted rank-one images
+// on the rows of S only. Row pass: image img = c R + r, row i generated as
+// H_c[i][j] (a_r[i] b_r[j]) (the product of mc_rank1_kernel) and transformed into Z[img].
+// Column pass: the columns of Z[img] transformed, the rows of S stored compact into Zs
+// (scaled by 1 / sqrt(Nx Ny)), the others dropped. Both persistent over the bands of a group.
+template <int N>
+constexpr int phi_minb() {
+  return fftband::Shape<N>::R == 16 ? (3 * fftband::Shape<N>::MINB) / 4 : fftband::Shape<N>::MINB;
+}
+
+template <int NY>
+__global__ void __launch_bounds__(fftband::Shape<NY>::NT, phi_minb<NY>())
+    mc_phi_rows_kernel(const float2* __restrict__ H, const float2* __restrict__ A, const float2* __restrict__ B, int R,
+                       int Nx, int img0, int nimg, float2* __restrict__ Z, const float2* __restrict__ Wg) {
+  constexpr int BAND = fftband::Shape<NY>::BAND;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* S = (float2*)smem_raw;
+  float2* W = S + BAND * fftband::row_stride<NY>();
+  for (int k = threadIdx.x; k < NY; k += blockDim.x) W[fpad(k)] = Wg[k];
+  const int nb = (Nx + BAND - 1) / BAND;
+  const size_t NN = (size_t)Nx * NY;
+  for (int task = blockIdx.x; task < nimg * nb; task += gridDim.x) {
+    __syncthreads();   // the table; the previous band's last use of S
+    const int il = task / nb, band = task - il * nb;
+    const int img = img0 + il, c = img / R, r = img - c * R;
+    const float2* Hc = H + (size_t)c * NN;
+    fftband::row_band_f<NY, false, true>(
+        [=](int i, int j) { return cmul(Hc[(size_t)i * NY + j], cmul(A[i * R + r], B[j * R + r])); },
+        Z + (size_t)img * NN, Nx, band * BAND, W, S);
+  }
+}
+
+template <int NX>
+__global__ void __launch_bounds__(fftband::Shape<NX>::NT, phi_minb<NX>())
+    mc_phi_cols_kernel(const float2* __restrict__ Z, float2* __restrict__ Zs, const int* __restrict__ rowpos, int s,
+                       int Ny, int img0, int nimg, const float2* __restrict__ Wg, float scale) {
+  constexpr int BAND = fftband::Shape<NX>::BAND;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* S = (float2*)smem_raw;
+  float2* W = S + BAND * fftband::row_stride<NX>();
+  for (int k = threadIdx.x; k < NX; k += blockDim.x) W[fpad(k)] = Wg[k];
+  const int nb = (Ny + BAND - 1) / BAND;
+  const size_t NN = (size_t)NX * Ny;
+  for (int task = blockIdx.x; task < nimg * nb; task += gridDim.x) {
+    __syncthreads();   // the table; the previous band's last use of S
+    const int il = task / nb, band = task - il * nb;
+    const int img = img0 + il;
+    float2* zs = Zs + (size_t)img * s * Ny;
+    fftband::col_band_f<NX, false, true>(Z + (size_t)img * NN, Ny, band * BAND, W, S,
+                                         [=](int k, int col, float2 v) {
+                                           const int m = rowpos[k];
+                                           if (m >= 0) zs[(size_t)m * Ny + col] = cscale(v, scale);
+                                         });
+  }
+}
+
+template <typename K>
+int phi_grid(K kernel, int threads, int smem, int tasks) {
+  int per_sm = 0, dev = 0, sms = 0;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+      cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1)
+    return 0;
+  return std::min(per_sm * sms, tasks);
+}
+
+template <int NY>
+int phi_rows_t(const float2* H, const float2* A, const float2* B, int R, int Nx, int img0, int nimg, float2* Z,
+               const float2* Wy, cudaStream_t st) {
+  constexpr int smem = fftband::smem_bytes<NY>();
+  const int tasks = nimg * ((Nx + fftband::Shape<NY>::BAND - 1) / fftband::Shape<NY>::BAND);
+  const int g = phi_grid(mc_phi_rows_kernel<NY>, fftband::Shape<NY>::NT, smem, tasks);
+  if (g < 1) return TTS_ECUDA;
+  mc_phi_rows_kernel<NY><<<g, fftband::Shape<NY>::NT, smem, st>>>(H, A, B, R, Nx, img0, nimg, Z, Wy);
+  return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
+}
+
+template <int NX>
+int phi_cols_t(const float2* Z, float2* Zs, const int* rowpos, int s, int Ny, int img0, int nimg, const float2* Wx,
+               float scale, cudaStream_t st) {
+  constexpr int smem = fftband::smem_bytes<NX>();
+  const int tasks = nimg * ((Ny + fftband::Shape<NX>::BAND - 1) / fftband::Shape<NX>::BAND);
+  const int g = phi_grid(mc_phi_cols_kernel<NX>, fftband::Shape<NX>::NT, smem, tasks);
+  if (g < 1) return TTS_ECUDA;
+  mc_phi_cols_kernel<NX><<<g, fftband::Shape<NX>::NT, smem, st>>>(Z, Zs, rowpos, s, Ny, img0, nimg, Wx, scale);
+  return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
+}
+
+#define TTS_BAND_CASES(X) X(64) X(96) X(120) X(128) X(160) X(192) X(240) X(256) X(320) X(384)
+
+// the transformed rank-one images on the rows of S into Zs; TTS_EINVAL for other sizes
+int launch_phi(const float2* H, const float2* A, const float2* B, int C, int R, int Nx, int Ny, int s,
+               const int* rowpos, const float2* Wx, const float2* Wy, float2* Z, float2* Zs, cudaStream_t st) {
+  if (!fftband::supported(Nx) || !fftband::supported(Ny)) return TTS_EINVAL;
+  const size_t NN = (size_t)Nx * Ny;
+  const int n = C * R;
+  const int group = (int)std::max<size_t>(1, std::min<size_t>((size_t)n, (40u << 20) / (NN * sizeof(float2))));
+  const float scale = 1.0f / sqrtf((float)Nx * (float)Ny);
+  for (int g0 = 0; g0 < n; g0 += group) {
+    const int k = std::min(group, n - g0);
+    int rc = TTS_EINVAL;
+    switch (Ny) {
+#define ROWS(N) \
+  case N: rc = phi_rows_t<N>(H, A, B, R, Nx, g0, k, Z, Wy, st); break;
+      TTS_BAND_CASES(ROWS)
+#undef ROWS
+    }
+    if (rc != TTS_OK) return rc;
+    rc = TTS_EINVAL;
+    switch (Nx) {
+#define COLS(N) \
+  case N: rc = phi_cols_t<N>(Z, Zs, rowpos, s, Ny, g0, k, Wx, scale, st); break;
+      TTS_BAND_CASES(COLS)
+#undef COLS
+    }
+    if (rc != TTS_OK) return rc;
+  }
+  return TTS_OK;
+}
+
 int grid_for(size_t n) { return (int)std::min<size_t>((n + kT - 1) / kT, 152 * 16); }
 
 }  // namespace
@@ -292,6 +479,7 @@ struct MultiCoil {
   void* mem = nullptr;
   float2* H = nullptr;        // C x Nx x Ny
   float2* Z = nullptr;        // C R x Nx x Ny: weighted rank-one images, transformed in place
+  float2* Zs = nullptr;       // C R x |S| x Ny: their transforms on the rows of S, compact
   float2* E = nullptr;        // C x Nx x Ny: residuals, back-projected in place; the refresh's H_c .* X
   float2* Zx = nullptr;       // C x Nx x Ny: transforms of H_c .* X
   float2* Theta = nullptr;    // Nx x Ny
@@ -340,6 +528,7 @@ int mc_attach(tts_handle* h, const float2* maps, int C, bool device) {
   };
   std::vector<P> ps = {{(void**)&m->H, sizeof(float2) * C * NN},
                        {(void**)&m->Z, sizeof(float2) * (size_t)C * R * NN},
+                       {(void**)&m->Zs, sizeof(float2) * (size_t)C * R * NN},
                        {(void**)&m->E, sizeof(float2) * C * NN},
                        {(void**)&m->Zx, sizeof(float2) * C * NN},
                        {(void**)&m->Theta, sizeof(float2) * NN},
@@ -459,15 +648,20 @@ int mc_push(tts_handle* h, const tts_c64* y_in, const uint8_t* mask_in, int flag
   int rc = TTS_OK;
   for (int k = 0; k < K && rc == TTS_OK; ++k) {
     // (S1)
-    mc_rank1_kernel<<<grid_for((size_t)C * R * NN), kT, 0, st>>>(m->H, p.A, p.B, m->Z, C, R, Nx, Ny);
-    rc = tts_fft2d((const tts_c64*)m->Z, (tts_c64*)m->Z, C * R, Nx, Ny, 0, st);
+    rc = launch_phi(m->H, p.A, p.B, C, R, Nx, Ny, s, m->rowpos, p.Wx, p.Wy, m->Z, m->Zs, st);
+    if (rc == TTS_EINVAL) {   // other sizes: explicit rank-one images, batched DFT, rows of S
+      mc_rank1_kernel<<<grid_for((size_t)C * R * NN), kT, 0, st>>>(m->H, p.A, p.B, m->Z, C, R, Nx, Ny);
+      rc = tts_fft2d((const tts_c64*)m->Z, (tts_c64*)m->Z, C * R, Nx, Ny, 0, st);
+      if (rc != TTS_OK) break;
+      mc_compact_kernel<<<grid_for((size_t)C * R * s * Ny), kT, 0, st>>>(m->Z, p.rows, C * R, Nx, Ny, s, m->Zs);
+    }
     if (rc != TTS_OK) break;
-    mc_gram_kernel<<<C * s, kT, gram_smem, st>>>(m->Z, m->y, p.rows, C, R, Nx, Ny, s, m->part);
+    mc_gram_kernel<<<C * s, kT, gram_smem, st>>>(m->Zs, m->y, C, R, Ny, s, m->part);
     mc_gram_reduce_kernel<<<((R * R + R) * 32 + kT - 1) / kT, kT, 0, st>>>(m->part, C * s, R, p.mu, m->G, m->h);
     rc = launch_ridge(m->G, m->h, R, p.gamma_d, st);
     if (rc != TTS_OK) break;
     // (S2) A block
-    mc_residual_kernel<<<grid_for((size_t)C * NN), kT, 0, st>>>(m->Z, nullptr, p.gamma_d, m->y, p.rows, m->rowpos, C,
+    mc_residual_kernel<<<grid_for((size_t)C * NN), kT, 0, st>>>(m->Zs, nullptr, p.gamma_d, m->y, p.rows, m->rowpos, C,
                                                                 R, Nx, Ny, s, m->E, p.gamma);
     rc = tts_fft2d((const tts_c64*)m->E, (tts_c64*)m->E, C, Nx, Ny, 1, st);
     if (rc != TTS_OK) break;
