@@ -341,6 +341,7 @@ void tts_destroy(tts_handle* h) {
     if (h->hstage[b]) cudaFreeHost(h->hstage[b]);
     if (h->hstage_done[b]) cudaEventDestroy(h->hstage_done[b]);
   }
+  if (h->mask_map) cudaFreeHost(h->mask_map);
   if (h->own_mem) cudaFree(h->dmem);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -470,7 +471,21 @@ int tts_next_mask(tts_handle* h, double rate, uint64_t seed, uint8_t* line_mask_
   if (!(rate > 0.0 && rate <= 1.0)) return fail(TTS_EINVAL, "rate must lie in (0, 1]%s");
   const int Nx = h->cfg.Nx;
   const int k_lines = handle_k_lines(h, rate);
-  uint8_t* out2 = (flags & TTS_DEVICE_PTRS) ? line_mask_out : nullptr;
+  const bool host = !(flags & TTS_DEVICE_PTRS);
+  if (host && !h->mask_map) {
+    uint8_t* m = nullptr;
+    void* d = nullptr;
+    if (cudaHostAlloc((void**)&m, Nx, cudaHostAllocMapped) == cudaSuccess) {
+      if (cudaHostGetDevicePointer(&d, m, 0) == cudaSuccess) {
+        h->mask_map = m;
+        h->mask_map_dev = (uint8_t*)d;
+      } else {
+        cudaFreeHost(m);
+      }
+    }
+    cudaGetLastError();   // without mapped memory the mask is copied back instead
+  }
+  uint8_t* out2 = host ? h->mask_map_dev : line_mask_out;
   int rc = launch_sampler(h->fp.A, Nx, h->cfg.Ny, h->cfg.R, nullptr, h->dp, h->cfg.policy, h->cfg.vd_alpha, k_lines,
                           h->cfg.central_lines, seed, handle_draw_counter(h), h->cfg.with_replacement, h->fp.Wx,
                           h->dmask_next, out2, h->stream, h->cfg.kspace);
@@ -479,8 +494,9 @@ int tts_next_mask(tts_handle* h, double rate, uint64_t seed, uint8_t* line_mask_
   if (flags & TTS_DEVICE_PTRS) {
     h->next_on_host = false;
   } else {
-    CK(cudaMemcpyAsync(h->next_host.data(), h->dmask_next, Nx, cudaMemcpyDeviceToHost, h->stream));
+    if (!h->mask_map) CK(cudaMemcpyAsync(h->next_host.data(), h->dmask_next, Nx, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (h->mask_map) memcpy(h->next_host.data(), h->mask_map, Nx);
     memcpy(line_mask_out, h->next_host.data(), Nx);
     h->next_on_host = true;
   }

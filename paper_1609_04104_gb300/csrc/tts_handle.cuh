@@ -35,6 +35,10 @@ struct tts_handle {
   float2* hstage[2] = {nullptr, nullptr};
   cudaEvent_t hstage_done[2] = {nullptr, nullptr};
   int hstage_next = 0;
+  // the drawn mask for host callers: mapped pinned memory the sampler writes directly
+  // (mask_map on the host, mask_map_dev its device address), so no copy follows the draw
+  uint8_t* mask_map = nullptr;
+  uint8_t* mask_map_dev = nullptr;
 };
 
 // Validates a configuration (message through tts_last_error on failure).
