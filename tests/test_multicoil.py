@@ -1,7 +1,9 @@
 """The multi-coil tracker on the GPU (tts_set_coil_maps: Alg. 3 with C coils, §IV-B)
-against the FP64 multi-coil oracle frame by frame, on square (single-pass cluster DFT) and
-non-square (two-pass DFT) sizes, host rows and full device frames; C = 1 with unit maps
-against the single-coil path; non-finite device frames skipped; argument errors."""
+against the FP64 multi-coil oracle frame by frame: band-shape sizes, square and rectangular
+(the fused (S1): rank-one rows generated in the row transform, rows of S stored compact),
+and other sizes (explicit images, tts_fft2d, gathered rows); host rows and full device
+frames; C = 1 with unit maps against the single-coil path; non-finite device frames skipped;
+argument errors."""
 from __future__ import annotations
 
 import dataclasses
@@ -49,7 +51,7 @@ def run_both(tts, Nx, Ny, R, C, T, device_full=False):
     return np.array(out), np.array(ref)
 
 
-@pytest.mark.parametrize("Nx,Ny,R,C", [(64, 64, 6, 4), (48, 40, 5, 3), (128, 128, 8, 8)])
+@pytest.mark.parametrize("Nx,Ny,R,C", [(64, 64, 6, 4), (48, 40, 5, 3), (128, 128, 8, 8), (96, 64, 7, 3), (64, 120, 6, 2)])
 def test_multicoil_matches_oracle(tts, Nx, Ny, R, C):
     out, ref = run_both(tts, Nx, Ny, R, C, 5)
     err = nrmse_per_frame(out, ref)
