@@ -41,6 +41,22 @@ struct Shape<128> {
   static constexpr int T = 8, R = 16, BAND = 16, NT = 128, MINB = 8;
 };
 template <>
+struct Shape<144> {
+  static constexpr int T = 16, R = 9, BAND = 16, NT = 256, MINB = 4;
+};
+template <>
+struct Shape<200> {
+  static constexpr int T = 8, R = 25, BAND = 16, NT = 128, MINB = 4;
+};
+template <>
+struct Shape<216> {
+  static constexpr int T = 8, R = 27, BAND = 16, NT = 128, MINB = 4;
+};
+template <>
+struct Shape<288> {
+  static constexpr int T = 16, R = 18, BAND = 16, NT = 256, MINB = 2;
+};
+template <>
 struct Shape<160> {
   static constexpr int T = 16, R = 10, BAND = 16, NT = 256, MINB = 4;
 };
@@ -67,8 +83,8 @@ struct Shape<384> {
 
 // the line lengths with a Shape
 __host__ __device__ constexpr bool supported(int N) {
-  return N == 64 || N == 96 || N == 120 || N == 128 || N == 160 || N == 192 || N == 240 || N == 256 || N == 320 ||
-         N == 384;
+  return N == 64 || N == 96 || N == 120 || N == 128 || N == 144 || N == 160 || N == 192 || N == 200 || N == 216 ||
+         N == 240 || N == 256 || N == 288 || N == 320 || N == 384;
 }
 
 // row regions in S: quarter-warp rows (T = 8) padded by 64 bytes

@@ -1,5 +1,5 @@
 // Batched unitary 2D DFT of Nx x Ny images with Nx != Ny, both line lengths among the band
-// shapes of tts_fft_band.cuh (64, 96, 120, 128, 160, 192, 240, 256, 320, 384): per group of
+// shapes of tts_fft_band.cuh (64 ... 384, see fftband::supported): per group of
 // images, one launch transforms every row band (rows of length Ny, from in to out,
 // unscaled) and a second one every column band of out in place (columns of length Nx,
 // scaled by 1 / sqrt(Nx Ny)). A group holds at most ~40 MB, so the row pass's output is still
@@ -101,10 +101,14 @@ int rows(const float2* in, float2* out, int nimg, int Nx, int Ny, const float2* 
     case 96: return rows_t<96, INV>(in, out, nimg, Nx, W, st);
     case 120: return rows_t<120, INV>(in, out, nimg, Nx, W, st);
     case 128: return rows_t<128, INV>(in, out, nimg, Nx, W, st);
+    case 144: return rows_t<144, INV>(in, out, nimg, Nx, W, st);
     case 160: return rows_t<160, INV>(in, out, nimg, Nx, W, st);
     case 192: return rows_t<192, INV>(in, out, nimg, Nx, W, st);
+    case 200: return rows_t<200, INV>(in, out, nimg, Nx, W, st);
+    case 216: return rows_t<216, INV>(in, out, nimg, Nx, W, st);
     case 240: return rows_t<240, INV>(in, out, nimg, Nx, W, st);
     case 256: return rows_t<256, INV>(in, out, nimg, Nx, W, st);
+    case 288: return rows_t<288, INV>(in, out, nimg, Nx, W, st);
     case 320: return rows_t<320, INV>(in, out, nimg, Nx, W, st);
     case 384: return rows_t<384, INV>(in, out, nimg, Nx, W, st);
     default: return TTS_EINVAL;
@@ -118,10 +122,14 @@ int cols(float2* data, int nimg, int Nx, int Ny, const float2* W, float scale, c
     case 96: return cols_t<96, INV>(data, nimg, Ny, W, scale, st);
     case 120: return cols_t<120, INV>(data, nimg, Ny, W, scale, st);
     case 128: return cols_t<128, INV>(data, nimg, Ny, W, scale, st);
+    case 144: return cols_t<144, INV>(data, nimg, Ny, W, scale, st);
     case 160: return cols_t<160, INV>(data, nimg, Ny, W, scale, st);
     case 192: return cols_t<192, INV>(data, nimg, Ny, W, scale, st);
+    case 200: return cols_t<200, INV>(data, nimg, Ny, W, scale, st);
+    case 216: return cols_t<216, INV>(data, nimg, Ny, W, scale, st);
     case 240: return cols_t<240, INV>(data, nimg, Ny, W, scale, st);
     case 256: return cols_t<256, INV>(data, nimg, Ny, W, scale, st);
+    case 288: return cols_t<288, INV>(data, nimg, Ny, W, scale, st);
     case 320: return cols_t<320, INV>(data, nimg, Ny, W, scale, st);
     case 384: return cols_t<384, INV>(data, nimg, Ny, W, scale, st);
     default: return TTS_EINVAL;

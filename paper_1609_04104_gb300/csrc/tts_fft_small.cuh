@@ -195,5 +195,13 @@ template <bool INV>
 struct Dft<20, INV> : Split<4, 5, INV> {};
 template <bool INV>
 struct Dft<24, INV> : Split<8, 3, INV> {};
+template <bool INV>
+struct Dft<9, INV> : Split<3, 3, INV> {};
+template <bool INV>
+struct Dft<18, INV> : Split<2, 9, INV> {};
+template <bool INV>
+struct Dft<25, INV> : Split<5, 5, INV> {};
+template <bool INV>
+struct Dft<27, INV> : Split<3, 9, INV> {};
 
 }  // namespace fftsmall

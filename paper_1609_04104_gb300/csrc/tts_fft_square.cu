@@ -1,4 +1,5 @@
-// Batched unitary 2D DFT for square N (64, 96, 128, 160, 192, 256, 320, 384) as one
+// Batched unitary 2D DFT for square N (64, 96, 128, 144, 160, 192, 256, 288, 320, 384; the
+// band length divides N) as one
 // persistent launch over band tasks, with the intermediate image kept in L2, so that HBM
 // sees about one read and one write of every image.
 //
@@ -189,7 +190,7 @@ int launch_n(const float2* in, float2* out, int batch, int inverse, const float2
 bool fft2d_square_ok(int Nx, int Ny) {
   if (Nx != Ny) return false;
   switch (Nx) {
-    case 64: case 96: case 128: case 160: case 192: case 256: case 320: case 384: return true;
+    case 64: case 96: case 128: case 144: case 160: case 192: case 256: case 288: case 320: case 384: return true;
     default: return false;
   }
 }
@@ -201,9 +202,11 @@ int launch_fft2d_square(const float2* in, float2* out, int batch, int N, int inv
     case 64: return launch_n<64>(in, out, batch, inverse, W, err, st);
     case 96: return launch_n<96>(in, out, batch, inverse, W, err, st);
     case 128: return launch_n<128>(in, out, batch, inverse, W, err, st);
+    case 144: return launch_n<144>(in, out, batch, inverse, W, err, st);
     case 160: return launch_n<160>(in, out, batch, inverse, W, err, st);
     case 192: return launch_n<192>(in, out, batch, inverse, W, err, st);
     case 256: return launch_n<256>(in, out, batch, inverse, W, err, st);
+    case 288: return launch_n<288>(in, out, batch, inverse, W, err, st);
     case 320: return launch_n<320>(in, out, batch, inverse, W, err, st);
     case 384: return launch_n<384>(in, out, batch, inverse, W, err, st);
     default: return TTS_EINVAL;

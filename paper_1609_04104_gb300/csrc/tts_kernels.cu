@@ -202,10 +202,14 @@ __device__ __forceinline__ bool sampler_scores_fast(int Nx, const float2* A, int
     case 96: sampler_scores_band<96>(A, R, no_fft, W, buf, rowacc, cols_for(8)); return true;
     case 120: sampler_scores_band<120>(A, R, no_fft, W, buf, rowacc, cols_for(8)); return true;
     case 128: sampler_scores_band<128>(A, R, no_fft, W, buf, rowacc, cols_for(8)); return true;
+    case 144: sampler_scores_band<144>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
     case 160: sampler_scores_band<160>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
     case 192: sampler_scores_band<192>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
+    case 200: sampler_scores_band<200>(A, R, no_fft, W, buf, rowacc, cols_for(8)); return true;
+    case 216: sampler_scores_band<216>(A, R, no_fft, W, buf, rowacc, cols_for(8)); return true;
     case 240: sampler_scores_band<240>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
     case 256: sampler_scores_band<256>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
+    case 288: sampler_scores_band<288>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
     case 320: sampler_scores_band<320>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
     case 384: sampler_scores_band<384>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
     default: return false;

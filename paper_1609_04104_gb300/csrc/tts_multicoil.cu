@@ -437,7 +437,8 @@ int phi_cols_t(const float2* Z, float2* Zs, const int* rowpos, int s, int Ny, in
   return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
 }
 
-#define TTS_BAND_CASES(X) X(64) X(96) X(120) X(128) X(160) X(192) X(240) X(256) X(320) X(384)
+#define TTS_BAND_CASES(X) \
+  X(64) X(96) X(120) X(128) X(144) X(160) X(192) X(200) X(216) X(240) X(256) X(288) X(320) X(384)
 
 // the transformed rank-one images on the rows of S into Zs; TTS_EINVAL for other sizes
 int launch_phi(const float2* H, const float2* A, const float2* B, int C, int R, int Nx, int Ny, int s,

@@ -28,7 +28,8 @@ def worst(got, ref):
     return float((np.linalg.norm(got - ref, axis=(1, 2)) / np.linalg.norm(ref, axis=(1, 2))).max())
 
 
-@pytest.mark.parametrize("Nx,Ny", [(192, 120), (120, 192), (96, 384), (256, 64), (160, 320), (120, 120), (240, 240)])
+@pytest.mark.parametrize("Nx,Ny", [(192, 120), (120, 192), (96, 384), (256, 64), (160, 320), (120, 120), (240, 240),
+                                   (200, 200), (216, 216), (144, 288), (200, 120)])
 @pytest.mark.parametrize("inverse", [False, True])
 def test_band_fft_rectangular(tts, Nx, Ny, inverse):
     import torch

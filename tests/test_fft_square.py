@@ -28,7 +28,7 @@ def check(tts, N, batch, inverse, inplace, seed):
         assert np.linalg.norm(got[b] - ref) / np.linalg.norm(ref) <= 1e-5, (N, batch, b)
 
 
-SIZES = [64, 96, 128, 160, 192, 256, 320, 384]   # line lengths T x R with R in 8, 10, 12, 16, 20, 24
+SIZES = [64, 96, 128, 144, 160, 192, 256, 288, 320, 384]   # line lengths T x R, R in 8 ... 24
 
 
 @pytest.mark.parametrize("N", SIZES)

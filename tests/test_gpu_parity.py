@@ -86,7 +86,7 @@ def test_line_draws_device_pointers(tts):
 # scores (probabilities) of the current subspace
 # ----------------------------------------------------------------------------------
 @pytest.mark.parametrize("Nx,Ny,R", [(64, 64, 8), (256, 256, 32), (192, 160, 48), (60, 45, 5), (384, 384, 64),
-                                    (120, 96, 16), (160, 128, 24)])
+                                    (120, 96, 16), (160, 128, 24), (216, 144, 16), (200, 64, 8)])
 def test_informative_probs_match_oracle(tts, Nx, Ny, R):
     rng = np.random.default_rng(Nx + R)
     A = cn(rng, Nx, R).astype(np.complex64)
