@@ -193,25 +193,23 @@ __device__ __forceinline__ void sampler_scores_band(const float2* __restrict__ A
   }
 }
 
+// scores for one band-shape length: up to blockDim / T columns per pass (T threads each)
+template <int N>
+__device__ __forceinline__ void sampler_scores_for(const float2* A, int R, int no_fft, const float2* W, float2* buf,
+                                                   float* rowacc, int fft_cols) {
+  const int cols = min(min((int)blockDim.x / fftband::Shape<N>::T, R), fft_cols);
+  sampler_scores_band<N>(A, R, no_fft, W, buf, rowacc, cols);
+}
+
 // the band-shape lengths: scores through sampler_scores_band; false for any other Nx
 __device__ __forceinline__ bool sampler_scores_fast(int Nx, const float2* A, int R, int no_fft, const float2* W,
                                                     float2* buf, float* rowacc, int fft_cols) {
-  auto cols_for = [&](int T) { return min(min((int)blockDim.x / T, R), fft_cols); };
   switch (Nx) {
-    case 64: sampler_scores_band<64>(A, R, no_fft, W, buf, rowacc, cols_for(8)); return true;
-    case 96: sampler_scores_band<96>(A, R, no_fft, W, buf, rowacc, cols_for(8)); return true;
-    case 120: sampler_scores_band<120>(A, R, no_fft, W, buf, rowacc, cols_for(8)); return true;
-    case 128: sampler_scores_band<128>(A, R, no_fft, W, buf, rowacc, cols_for(8)); return true;
-    case 144: sampler_scores_band<144>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
-    case 160: sampler_scores_band<160>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
-    case 192: sampler_scores_band<192>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
-    case 200: sampler_scores_band<200>(A, R, no_fft, W, buf, rowacc, cols_for(8)); return true;
-    case 216: sampler_scores_band<216>(A, R, no_fft, W, buf, rowacc, cols_for(8)); return true;
-    case 240: sampler_scores_band<240>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
-    case 256: sampler_scores_band<256>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
-    case 288: sampler_scores_band<288>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
-    case 320: sampler_scores_band<320>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
-    case 384: sampler_scores_band<384>(A, R, no_fft, W, buf, rowacc, cols_for(16)); return true;
+#define SCORES(N) \
+  case N: sampler_scores_for<N>(A, R, no_fft, W, buf, rowacc, fft_cols); return true;
+    SCORES(64) SCORES(96) SCORES(120) SCORES(128) SCORES(144) SCORES(160) SCORES(192) SCORES(200) SCORES(216)
+    SCORES(240) SCORES(256) SCORES(288) SCORES(320) SCORES(384)
+#undef SCORES
     default: return false;
   }
 }
