@@ -8,9 +8,11 @@ One round maps the counter (c0, c1, c2, c3) under key (k0, k1) to
 with the 32x32 -> 64-bit products split into high and low words; the key is bumped
 by the Weyl constants (W0, W1) between rounds; ten rounds make Philox4x32-10.
 
-Parity unpinned: the published known-answer vectors are not available here, so this
-generator is pinned only by its agreement with the independent CUDA implementation
-and by statistical checks (uniformity of the words), not by reference outputs.
+Parity unpinned for its outputs: the published known-answer vectors are not available
+here, so the generator's outputs are pinned only by agreement with the independent CUDA
+implementation and by statistical checks (uniformity of the words). Its parts are pinned
+where mathematics fixes them: the key-schedule increments against their definition (the
+golden ratio and sqrt 3 in 32-bit fixed point) and the round against its inverse.
 """
 from __future__ import annotations
 

@@ -353,6 +353,34 @@ def test_philox_words_uniform():
     assert philox.philox4x32_10((0, 0, 0, 0), (0, 0)) != philox.philox4x32_10((0, 0, 0, 0), (1, 0))
 
 
+def test_philox_key_schedule_constants_from_their_definition():
+    """The Weyl increments of the Philox key schedule are the fractional parts of the
+    golden ratio and of sqrt(3) in 32-bit fixed point (SC'11 definition); derived here in
+    exact integer arithmetic rather than copied."""
+    golden = (math.isqrt(5 << 64) - (1 << 32)) // 2        # floor(2^32 (sqrt 5 - 1) / 2)
+    sqrt3 = math.isqrt(3 << 64) - (1 << 32)                # floor(2^32 (sqrt 3 - 1))
+    assert philox.W0 == golden and philox.W1 == sqrt3
+    # the multipliers are odd, so each round is a bijection of the 128-bit block
+    assert philox.M0 % 2 == 1 and philox.M1 % 2 == 1
+
+
+def test_philox_round_is_invertible():
+    """One round inverted from its definition (odd multipliers have inverses mod 2^32):
+    c0 and c2 come back from the low product words, then c1 and c3 from the high words
+    and the key; a swapped output word or a hi/lo mix-up would break the round trip."""
+    inv0, inv1 = pow(philox.M0, -1, 1 << 32), pow(philox.M1, -1, 1 << 32)
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        c = tuple(int(v) for v in rng.integers(0, 1 << 32, 4, dtype=np.uint64))
+        k = tuple(int(v) for v in rng.integers(0, 1 << 32, 2, dtype=np.uint64))
+        o = philox.philox4x32_round(c, k)
+        c0 = (o[3] * inv0) & philox.MASK32
+        c2 = (o[1] * inv1) & philox.MASK32
+        c1 = o[0] ^ ((philox.M1 * c2) >> 32) ^ k[0]
+        c3 = o[2] ^ ((philox.M0 * c0) >> 32) ^ k[1]
+        assert (c0, c1, c2, c3) == c
+
+
 def test_line_draw_integer_cdf_boundaries():
     """With p_i = k_i 2^-52 the weights are the small integers k_i, so the draws hit
     the CDF boundaries constantly: zero-weight lines are never drawn and line i is
