@@ -82,3 +82,31 @@ def test_input_recipe_shapes_and_masks():
     A, B = inputs.init_factors(256, 192, 32)
     assert A.shape == (256, 32) and B.shape == (192, 32)
     assert abs(np.mean(np.abs(A) ** 2) - 1 / 256) < 0.1 / 256
+
+
+def test_transform_and_sampler_arguments_checked_before_any_cuda_call(lib):
+    """Argument errors of the standalone entry points come back as TTS_EINVAL (-1) with a
+    message, before the library touches the device (fake, never dereferenced addresses)."""
+    P = ctypes.c_void_p
+    lib.tts_fft2d.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+    lib.tts_dft2d_gemm.argtypes = [P, P, P] + [ctypes.c_int] * 5 + [P, P]
+    lib.tts_sample_lines_from_probs.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                                ctypes.c_uint64, ctypes.c_int, P, ctypes.c_int]
+    lib.tts_last_error.restype = ctypes.c_char_p
+    a, b, c = P(0x10000), P(0x20000), P(0x30000)
+    assert lib.tts_fft2d(None, b, 1, 64, 64, 0, None) == -1
+    assert lib.tts_fft2d(a, b, 1, 7, 64, 0, None) == -1            # prime factor 7
+    assert lib.tts_fft2d(a, b, 1, 64, 1024, 0, None) == -1          # beyond 512
+    assert lib.tts_fft2d(a, b, -1, 64, 64, 0, None) == -1
+    assert lib.tts_dft2d_gemm(a, b, c, 1, 48, 64, 0, 0, None, None) == -1   # 48: not a multiple of 32
+    assert lib.tts_dft2d_gemm(a, b, a, 1, 64, 64, 0, 0, None, None) == -1   # tmp aliases in
+    assert lib.tts_dft2d_gemm(P(0x10008), b, c, 1, 64, 64, 0, 0, None, None) == -1   # 8 bytes off 16
+    assert b"aligned" in lib.tts_last_error()
+    assert lib.tts_dft2d_gemm(a, b, c, 1, 64, 64, 0, 5, None, None) == -1   # unknown precision
+    p = (ctypes.c_double * 8)(*([0.125] * 8))
+    out = (ctypes.c_uint8 * 8)()
+    assert lib.tts_sample_lines_from_probs(None, 8, 2, 0, 1, 0, 0, out, 0) == -1
+    assert lib.tts_sample_lines_from_probs(p, 0, 2, 0, 1, 0, 0, out, 0) == -1
+    assert lib.tts_sample_lines_from_probs(p, 8, 2, 9, 1, 0, 0, out, 0) == -1   # central > Nx
+    bad = (ctypes.c_double * 8)(*([0.125] * 7 + [float("nan")]))
+    assert lib.tts_sample_lines_from_probs(bad, 8, 2, 0, 1, 0, 0, out, 0) == -1
