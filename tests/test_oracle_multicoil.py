@@ -1,7 +1,8 @@
 """Pins of the multi-coil oracle (Alg. 3 with C coils, §IV-B) against facts other than its
 own formulas: the single-coil tracker (C = 1, H = 1), the image-domain gradient of the
 data fit by finite differences (Theta), factor gradients by finite differences, the
-majoriser inequality, monotone MM, and exact recovery of noiseless multi-coil data."""
+majoriser inequality in both blocks, Phi against a brute-force DFT, monotone MM, and exact
+recovery of noiseless multi-coil data."""
 from __future__ import annotations
 
 import numpy as np
@@ -109,6 +110,56 @@ def test_majoriser_bounds_the_data_fit():
         D = cn(rng, Nx, R) * rng.uniform(0.01, 3.0)
         f1 = M.mc_objective_J(A + D, B, g, H, Y, rows, 0.0, rho)
         assert f1 <= f0 + float(np.vdot(gA, D).real) + 0.5 * alpha * float(np.vdot(D, D).real) + 1e-9
+
+
+def test_majoriser_bounds_the_data_fit_in_b():
+    """The B block's weight h_max sum_r |gamma_r|^2 ||a_r||^2 + rho majorises the data fit
+    along any direction of B (the mirror of the A-block pin)."""
+    rng = np.random.default_rng(6)
+    Nx, Ny, R, C = 5, 6, 3, 3
+    H = np.asarray(inputs.coil_maps(Nx, Ny, C, 2), complex)
+    rows = np.array([0, 2, 3])
+    Y = np.zeros((C, Nx, Ny), complex)
+    Y[:, rows, :] = cn(rng, C, len(rows), Ny)
+    A, B, g = cn(rng, Nx, R), cn(rng, Ny, R), 2 * cn(rng, R)
+    rho = 0.0
+    alpha = M.mc_lipschitz_B(A, g, rho, M.h_max(H))
+    f0 = M.mc_objective_J(A, B, g, H, Y, rows, 0.0, rho)
+    gB = M.mc_gradient_B(A, B, g, H, Y, rows, rho)
+    for _ in range(20):
+        D = cn(rng, Ny, R) * rng.uniform(0.01, 3.0)
+        f1 = M.mc_objective_J(A, B + D, g, H, Y, rows, 0.0, rho)
+        assert f1 <= f0 + float(np.vdot(gB, D).real) + 0.5 * alpha * float(np.vdot(D, D).real) + 1e-9
+
+
+def test_phi_against_a_brute_force_dft():
+    """Column r of Phi stacks, coil by coil, the acquired rows of the unitary 2D DFT of
+    H_c .* a_r b_r^T written as the quadruple sum over (n, m) (O(N^4), no matrix product
+    and no library transform); and mc_data stacks the acquired rows in the same order."""
+    rng = np.random.default_rng(8)
+    Nx, Ny, R, C = 4, 3, 2, 2
+    H = cn(rng, C, Nx, Ny)
+    A, B = cn(rng, Nx, R), cn(rng, Ny, R)
+    rows = np.array([1, 3])
+
+    def dft2_brute(X):
+        out = np.zeros_like(X)
+        for k in range(Nx):
+            for l in range(Ny):
+                acc = 0j
+                for n in range(Nx):
+                    for m in range(Ny):
+                        acc += X[n, m] * np.exp(-2j * np.pi * (k * n / Nx + l * m / Ny))
+                out[k, l] = acc / np.sqrt(Nx * Ny)
+        return out
+
+    Phi = M.mc_phi(A, B, H, rows)
+    assert Phi.shape == (C * len(rows) * Ny, R)
+    for r in range(R):
+        col = np.concatenate([dft2_brute(H[c] * np.outer(A[:, r], B[:, r]))[rows, :].reshape(-1) for c in range(C)])
+        np.testing.assert_allclose(Phi[:, r], col, rtol=0, atol=1e-12)
+    Yf = cn(rng, C, Nx, Ny)
+    np.testing.assert_array_equal(M.mc_data(Yf, rows), np.concatenate([Yf[c][rows, :].reshape(-1) for c in range(C)]))
 
 
 def test_normalised_coil_maps():
