@@ -353,6 +353,32 @@ def test_philox_words_uniform():
     assert philox.philox4x32_10((0, 0, 0, 0), (0, 0)) != philox.philox4x32_10((0, 0, 0, 0), (1, 0))
 
 
+def test_mm_step_minimises_its_surrogate():
+    """The MM step returns the minimiser of the quadratic surrogate
+    s(Z) = <grad, Z - X> + alpha/2 ||Z - X||^2 + lf abar/2 ||Z - X0||^2 (§III-A): its
+    gradient vanishes there (checked by central differences of s, not by the closed form),
+    and every random perturbation raises s."""
+    rng = np.random.default_rng(12)
+    X, X0, G = (rng.standard_normal((5, 3)) + 1j * rng.standard_normal((5, 3)) for _ in range(3))
+    alpha, abar, lf = 2.5, 7.0, 0.9
+
+    def surrogate(Z):
+        return float(np.vdot(G, Z - X).real) + 0.5 * alpha * float(np.vdot(Z - X, Z - X).real) \
+            + 0.5 * lf * abar * float(np.vdot(Z - X0, Z - X0).real)
+
+    Z = O.mm_step(X, X0, G, alpha, abar, lf)
+    h = 1e-6
+    for idx in np.ndindex(Z.shape):
+        for unit in (1.0, 1j):
+            E = np.zeros_like(Z)
+            E[idx] = unit * h
+            d = (surrogate(Z + E) - surrogate(Z - E)) / (2 * h)
+            assert abs(d) < 1e-6
+    for _ in range(20):
+        P = 1e-2 * (rng.standard_normal(Z.shape) + 1j * rng.standard_normal(Z.shape))
+        assert surrogate(Z + P) > surrogate(Z)
+
+
 def test_philox_key_schedule_constants_from_their_definition():
     """The Weyl increments of the Philox key schedule are the fractional parts of the
     golden ratio and of sqrt(3) in 32-bit fixed point (SC'11 definition); derived here in
