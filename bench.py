@@ -269,7 +269,7 @@ def run_tts(args, rank, world):
 
     # end to end through the C ABI with host buffers: per frame the drawn lines come back to
     # the host (the scanner needs them before it acquires the frame), the host frame goes in
-    # (the library gathers the acquired rows into its pinned staging and copies only those),
+    # (the library gathers the acquired rows into mapped pinned memory the kernels read),
     # and the image comes back to the host asynchronously on a copy stream (its copy overlaps
     # the next line draw and frame; every image is on the host when the step ends)
     e2e = None
@@ -310,7 +310,8 @@ def run_tts(args, rank, world):
         e2e = {"value": T * world / float(np.mean(e2e_s)), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h,
                "note": "host lines back every frame (synchronous); host frames in (the acquired rows "
-                       "gathered by the library, one copy); images out on a copy stream"}
+                       "gathered by the library into mapped pinned memory the kernels read); images out "
+                       "on a copy stream"}
 
     # roofline of the dominant kernel (the frame kernel), FP32 ALU bound
     kmean = float(np.mean(kern_ms)) * 1e-3

@@ -159,9 +159,9 @@ int tts_get_config(tts_handle* h, tts_config* cfg);
  * (TTS_ENONFINITE, nothing applied); with TTS_DEVICE_PTRS the check runs on the
  * device, the frame is skipped and tts_synchronize reports TTS_ENONFINITE.
  * With TTS_FULL_FRAME, y_rows is a full Nx x Ny frame of which only the acquired rows
- * are read. Host rows are gathered (and checked) into pinned memory of the handle and
- * copied to the device in one transfer, so y_rows may be pageable and is free again when
- * the call returns. Asynchronous with TTS_DEVICE_PTRS (the buffers must stay valid until the
+ * are read. Host rows are gathered (and checked) into pinned memory of the handle, which the
+ * kernels read in place (mapped) or which is copied in one transfer, so y_rows may be
+ * pageable and is free again when the call returns. Asynchronous with TTS_DEVICE_PTRS (the buffers must stay valid until the
  * stream passes this work). */
 int tts_push_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line_mask, int flags);
 

@@ -211,7 +211,17 @@ static int gather_host_rows(tts_handle* h, const float* y, const uint8_t* m, boo
   const int Nx = h->cfg.Nx, Ny = h->cfg.Ny;
   const int b = h->hstage_next;
   if (!h->hstage[b]) {
-    CK(cudaMallocHost((void**)&h->hstage[b], sizeof(float2) * (size_t)Nx * Ny));
+    const size_t bytes = sizeof(float2) * (size_t)Nx * Ny;
+    void* d = nullptr;
+    if (cudaHostAlloc((void**)&h->hstage[b], bytes, cudaHostAllocMapped) == cudaSuccess &&
+        cudaHostGetDevicePointer(&d, h->hstage[b], 0) == cudaSuccess) {
+      h->hstage_dev[b] = (float2*)d;
+    } else {   // no mapping: plain pinned memory and a copy per push
+      if (h->hstage[b]) cudaFreeHost(h->hstage[b]);
+      h->hstage[b] = nullptr;
+      cudaGetLastError();
+      CK(cudaMallocHost((void**)&h->hstage[b], bytes));
+    }
     CK(cudaEventCreateWithFlags(&h->hstage_done[b], cudaEventDisableTiming));
   } else {
     CK(cudaEventSynchronize(h->hstage_done[b]));
@@ -263,12 +273,18 @@ int handle_stage_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line
       float2* staged = nullptr;
       const int rg = gather_host_rows(h, (const float*)y_rows, m, (flags & TTS_FULL_FRAME) != 0, &staged);
       if (rg != TTS_OK) return rg;
+      const int b = h->hstage_next;
       if (line_mask) CK(cudaMemcpyAsync(h->dmask_push, m, Nx, cudaMemcpyHostToDevice, h->stream));
-      CK(cudaMemcpyAsync(h->ystage, staged, sizeof(float2) * (size_t)s * Ny, cudaMemcpyHostToDevice, h->stream));
-      CK(cudaEventRecord(h->hstage_done[h->hstage_next], h->stream));
+      if (h->hstage_dev[b]) {
+        p.yrows = h->hstage_dev[b];   // read in place by the frame's kernels
+        h->hstage_pending = b;        // its event follows their launches (tts_push_frame)
+      } else {
+        CK(cudaMemcpyAsync(h->ystage, staged, sizeof(float2) * (size_t)s * Ny, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaEventRecord(h->hstage_done[b], h->stream));
+        p.yrows = h->ystage;
+      }
       h->hstage_next ^= 1;
       p.mask = line_mask ? h->dmask_push : h->dmask_next;
-      p.yrows = h->ystage;
       p.full_frame = 0;   // compact rows on the device
       *pout = p;
       return TTS_OK;
@@ -433,15 +449,26 @@ int tts_push_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line_mas
   FrameParams p;
   const int rs = handle_stage_frame(h, y_rows, line_mask, flags, &p, true);
   if (rs != TTS_OK) return rs;
+  // a staging buffer the kernels read in place is free again once they are done
+  auto release_staging = [h]() {
+    if (h->hstage_pending >= 0) {
+      cudaEventRecord(h->hstage_done[h->hstage_pending], h->stream);
+      h->hstage_pending = -1;
+    }
+  };
   if (h->cfg.row_dft != TTS_ROWDFT_FFT) {
     // the acquired rows' transform on the tensor cores, straight into Yt
     const int rr = launch_row_dft(p.yrows, p.Yt, p.mask, h->cfg.Nx, h->cfg.Ny, p.full_frame,
                                   h->cfg.row_dft == TTS_ROWDFT_BF16X3 ? 1 : 0, p.status + 1 + TTS_MAX_CLUSTER,
                                   h->stream);
-    if (rr != TTS_OK) return fail(rr, "row transform launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    if (rr != TTS_OK) {
+      release_staging();
+      return fail(rr, "row transform launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    }
     p.yt_ready = 1;
   }
   const int rc = launch_frame(p, h->cfg.launch, h->stream);
+  release_staging();
   if (rc != TTS_OK) return fail(rc, "frame kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
   h->t += 1;
   return TTS_OK;

@@ -31,10 +31,13 @@ struct tts_handle {
   std::vector<uint8_t> next_host;
   MultiCoil* mc = nullptr;      // set by tts_set_coil_maps
   // pinned host staging of the acquired rows of host pushes (tts_push_frame): two buffers
-  // of Nx x Ny, each reused once the copy recorded by its event has completed
+  // of Nx x Ny, mapped into the device address space when possible (hstage_dev: the kernels
+  // read the rows in place), each reused once the work recorded by its event has completed
   float2* hstage[2] = {nullptr, nullptr};
+  float2* hstage_dev[2] = {nullptr, nullptr};
   cudaEvent_t hstage_done[2] = {nullptr, nullptr};
   int hstage_next = 0;
+  int hstage_pending = -1;      // staged buffer whose event follows the frame's launches
   // the drawn mask for host callers: mapped pinned memory the sampler writes directly
   // (mask_map on the host, mask_map_dev its device address), so no copy follows the draw
   uint8_t* mask_map = nullptr;
