@@ -1,5 +1,5 @@
 """Host frames through tts_push_frame: the library gathers the acquired rows into its pinned
-staging (checking them for NaN/Inf) and copies only those. A full host frame with the mask
+staging (checking them for NaN/Inf), which the kernels read in place. A full host frame with the mask
 of the last draw (line_mask NULL, read from the device copy) must give bit-identical results
 to the acquired rows gathered by the caller with the mask given; a NaN/Inf in a row that was
 not acquired is never read; one in an acquired row refuses the frame with nothing applied;
