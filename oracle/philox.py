@@ -8,11 +8,13 @@ One round maps the counter (c0, c1, c2, c3) under key (k0, k1) to
 with the 32x32 -> 64-bit products split into high and low words; the key is bumped
 by the Weyl constants (W0, W1) between rounds; ten rounds make Philox4x32-10.
 
-Parity unpinned for its outputs: the published known-answer vectors are not available
-here, so the generator's outputs are pinned only by agreement with the independent CUDA
-implementation and by statistical checks (uniformity of the words). Its parts are pinned
-where mathematics fixes them: the key-schedule increments against their definition (the
-golden ratio and sqrt 3 in 32-bit fixed point) and the round against its inverse.
+Pinned against an independent implementation of the same generator: cuRAND's host-side
+PHILOX4_32_10 generator (run on the CPU through ctypes by the tests) gives, word for word, the
+outputs of this function for its counters (block k of the stream for seed s is the output for
+counter (k div 65536 in c0:c1, k mod 65536 in c2, 0) and key (lo32 s, hi32 s)). Its parts are
+also pinned where mathematics fixes them: the key-schedule increments against their definition
+(the golden ratio and sqrt 3 in 32-bit fixed point), the round against its inverse, and the
+uniformity of the words.
 """
 from __future__ import annotations
 
