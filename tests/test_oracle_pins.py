@@ -421,3 +421,31 @@ def test_line_draw_integer_cdf_boundaries():
     freq = counts / n
     expect = k / k.sum()
     assert np.all(np.abs(freq - expect) < 5 * np.sqrt(expect * (1 - expect) / n) + 1e-12)
+
+
+@pytest.mark.parametrize("update,K", [("gauss_seidel", 1), ("gauss_seidel", 3), ("jacobi", 2)])
+def test_frame_without_lines_is_the_data_free_step(update, K):
+    """A frame with no acquired line (S empty) has no data term: Phi has no rows, so the
+    ridge gives gamma = 0 and the image is zero. What is left of each block's objective is
+    the forgotten past surrogates plus the factor penalty, lf abar / 2 ||X - X[t-1]||^2 +
+    rho / 2 ||X||^2, whose minimiser is X[t-1] lf abar / (lf abar + rho): the frame shrinks
+    both factors by that ratio at any K, and the surrogate weights grow by rho = mu / w."""
+    rng = np.random.default_rng(41)
+    Nx, Ny, R, lf, mu = 12, 10, 3, 0.9, 0.05
+    A = rng.standard_normal((Nx, R)) + 1j * rng.standard_normal((Nx, R))
+    B = rng.standard_normal((Ny, R)) + 1j * rng.standard_normal((Ny, R))
+    tr = O.Tracker(Nx, Ny, R, lf, mu, mm_iters=K, update=update, A=A, B=B)
+    for t in range(3):
+        m = (rng.random(Nx) < 0.5).astype(np.uint8)
+        m[0] = 1
+        Y = rng.standard_normal((Nx, Ny)) + 1j * rng.standard_normal((Nx, Ny))
+        tr.push_frame(Y[np.flatnonzero(m)], m)
+    A1, B1, aA, aB, w = tr.A.copy(), tr.B.copy(), tr.abar_A, tr.abar_B, tr.w
+    x = tr.push_frame(np.zeros((0, Ny), np.complex128), np.zeros(Nx, np.uint8))
+    rho = mu / (lf * w + 1.0)
+    assert np.all(x == 0) and np.all(tr.gamma == 0)
+    np.testing.assert_allclose(tr.A, A1 * (lf * aA / (lf * aA + rho)), rtol=1e-13, atol=0)
+    np.testing.assert_allclose(tr.B, B1 * (lf * aB / (lf * aB + rho)), rtol=1e-13, atol=0)
+    assert tr.abar_A == pytest.approx(lf * aA + rho, rel=1e-15)
+    assert tr.abar_B == pytest.approx(lf * aB + rho, rel=1e-15)
+    assert tr.w == pytest.approx(lf * w + 1.0, rel=1e-15)
