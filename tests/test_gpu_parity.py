@@ -355,3 +355,55 @@ def test_full_frame_push_equals_row_push(tts):
             else:
                 tts.tts_push_frame(trk.h, np.ascontiguousarray(Y[t]), masks[t], full_frame=True)
             np.testing.assert_array_equal(trk.image(t), ref[t])
+
+
+def test_frame_without_lines_device_mask(tts):
+    """A device line mask may select no line (a host mask with none is refused with
+    TTS_EINVAL): the frame then runs with |S| = 0, so gamma_t = 0, the image is exactly zero
+    and the factors take the data-free MM step; the frames after it stay within the image
+    bound of the oracle run through the same masks."""
+    import torch
+    w = inputs.scaled(SMALL, T=8)
+    L, Y, A0, B0 = workload_inputs(w, w.T)
+    masks = inputs.uniform_line_masks(w)[: w.T].copy()
+    masks[3] = 0
+    ref, _, _ = run_oracle(w, w.T, Y, A0, B0, masks=masks)
+    trk = tts.Tracker(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, mm_iters=w.mm_iters, central_lines=w.central_lines)
+    trk.set_factors(A0, B0)
+    out = torch.empty((w.Nx, w.Ny), dtype=torch.complex64, device="cuda")
+    got = []
+    for t in range(w.T):
+        rows = inputs.observed_rows(Y[t], masks[t])
+        if len(rows) == 0:
+            rows = np.zeros((1, w.Ny), np.complex64)         # never read
+        yd = torch.from_numpy(np.ascontiguousarray(rows, np.complex64)).cuda()
+        md = torch.from_numpy(masks[t]).cuda()
+        tts.tts_push_frame(trk.h, yd, md)
+        tts.tts_image(trk.h, t, out)
+        torch.cuda.synchronize()
+        got.append(out.cpu().numpy())
+        if t == 3:
+            assert np.all(trk.gamma() == 0)
+    got = np.array(got)
+    assert np.all(ref[3] == 0) and np.all(got[3] == 0)
+    keep = [t for t in range(w.T) if t != 3]
+    assert nrmse_per_frame(got[keep], ref[keep]).max() < NRMSE_TOL
+    with pytest.raises(tts.TtsError) as e:
+        trk.push_frame(np.zeros((0, w.Ny), np.complex64), masks[3])
+    assert e.value.code == tts.TTS_EINVAL
+    trk.close()
+
+
+@pytest.mark.parametrize("Nx,Ny,R,K,C,T", [(512, 32, 64, 2, 8, 3), (32, 512, 64, 2, 16, 3), (512, 512, 8, 1, 16, 3)])
+def test_maximum_sizes(tts, Nx, Ny, R, K, C, T):
+    """The largest layouts: Nx or Ny = 512 (the maximum line length) with R = 64 (the
+    maximum rank), 128 acquired lines (several chunks of m), and a 512 x 512 frame on a
+    16-CTA cluster."""
+    w = inputs.Workload(name="maximum", Nx=Nx, Ny=Ny, R=R, T=T, n_ellipses=4, sigma=0.01, lambda_forget=0.9,
+                        mu=1e-2, mm_iters=K, policy="uniform", rate=0.25, central_lines=8, seed=5)
+    L, Y, A0, B0 = workload_inputs(w, w.T)
+    masks = inputs.uniform_line_masks(w)
+    ref, _, _ = run_oracle(w, w.T, Y, A0, B0, masks=masks)
+    trk, got = run_gpu(tts, w, w.T, Y, A0, B0, masks, cluster_ctas=C)
+    assert tts.tts_get_config(trk.h).cluster_ctas == C
+    assert nrmse_per_frame(got, ref).max() < NRMSE_TOL
