@@ -54,7 +54,7 @@ struct Shape<216> {
 };
 template <>
 struct Shape<288> {
-  static constexpr int T = 16, R = 18, BAND = 16, NT = 256, MINB = 2;
+  static constexpr int T = 16, R = 18, BAND = 16, NT = 256, MINB = 3;
 };
 template <>
 struct Shape<160> {
@@ -74,11 +74,11 @@ struct Shape<256> {
 };
 template <>
 struct Shape<320> {
-  static constexpr int T = 16, R = 20, BAND = 16, NT = 256, MINB = 2;
+  static constexpr int T = 16, R = 20, BAND = 16, NT = 256, MINB = 3;
 };
 template <>
 struct Shape<384> {
-  static constexpr int T = 16, R = 24, BAND = 16, NT = 256, MINB = 2;
+  static constexpr int T = 16, R = 24, BAND = 16, NT = 256, MINB = 3;
 };
 
 // the line lengths with a Shape
