@@ -63,8 +63,16 @@ __device__ __forceinline__ int decode(int q, int NB, int L, int batch, int* band
   return mid_imgs + qq / NB;
 }
 
+// CTAs per SM the square kernel is compiled for: above the band shape's default for 96, 160
+// and 192, whose registers still fit the tighter budget without spills (more warps in flight
+// to cover the memory latency)
+template <int N>
+constexpr int square_minb() {
+  return N == 96 ? 8 : (N == 160 ? 5 : (N == 192 ? 4 : Shape<N>::MINB));
+}
+
 template <int N, bool INV>
-__global__ void __launch_bounds__(Shape<N>::NT, Shape<N>::MINB)
+__global__ void __launch_bounds__(Shape<N>::NT, square_minb<N>())
     fft2d_square_kernel(const float2* in, float2* out, int batch, int L, const float2* __restrict__ Wg, float scale,
                         int* ctrl, int* err) {
   constexpr int BAND = Shape<N>::BAND, NT = Shape<N>::NT, NB = N / BAND;
