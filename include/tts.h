@@ -158,6 +158,10 @@ int tts_get_config(tts_handle* h, tts_config* cfg);
  * surrogate statistics). With host pointers the frame is checked for NaN/Inf first
  * (TTS_ENONFINITE, nothing applied); with TTS_DEVICE_PTRS the check runs on the
  * device, the frame is skipped and tts_synchronize reports TTS_ENONFINITE.
+ * A host mask that selects no line is refused (TTS_EINVAL); a device mask is not read on
+ * the host, and one that selects no line runs the frame without data: gamma_t = 0, a zero
+ * image, and both factors scaled by lf abar / (lf abar + rho), the minimiser of the
+ * forgotten surrogates plus the factor penalty.
  * With TTS_FULL_FRAME, y_rows is a full Nx x Ny frame of which only the acquired rows
  * are read. Host rows are gathered (and checked) into pinned memory of the handle, which the
  * kernels read in place (mapped) or which is copied in one transfer, so y_rows may be
