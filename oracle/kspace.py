@@ -25,8 +25,10 @@ from . import tracker as T
 
 def ks_phi(A1: np.ndarray, A2: np.ndarray, rows: np.ndarray) -> np.ndarray:
     """Phi of Alg. 2 (S1): row l = (i, j) in Omega (rows x [Ny], row by row) holds
-    A1[i, r] A2[j, r]. Shape (|S| Ny) x R."""
-    return np.concatenate([A1[i][None, :] * A2 for i in rows], axis=0)
+    A1[i, r] A2[j, r]. Shape (|S| Ny) x R (no rows when S is empty)."""
+    rows = np.asarray(rows, dtype=np.int64)
+    Ny, R = A2.shape
+    return (A1[rows][:, None, :] * A2[None, :, :]).reshape(len(rows) * Ny, R)
 
 
 def ks_residual(A1, A2, gamma, Y, rows) -> np.ndarray:

@@ -113,3 +113,24 @@ def test_scores_on_k_space_rows():
     p = K.ks_line_probs(A1, 8)
     assert abs(p.sum() - 1.0) < 1e-14
     assert p[3] > p[4] and np.allclose(np.delete(p, 3), p[0])
+
+
+@pytest.mark.parametrize("update", ["gauss_seidel", "jacobi"])
+def test_frame_without_lines_is_the_data_free_step(update):
+    """No acquired line: gamma = 0, the interpolated frame and its image are zero, and the
+    k-space factors take the data-free step A[t-1] lf abar / (lf abar + rho) (the minimiser of
+    the forgotten surrogates plus the factor penalty)."""
+    rng = np.random.default_rng(23)
+    Nx, Ny, R, lf, mu = 10, 8, 3, 0.9, 0.02
+    tr = K.KspaceTracker(Nx, Ny, R, lf, mu, 2, update=update, A1=0.4 * cn(rng, Nx, R), A2=0.4 * cn(rng, Ny, R))
+    for t in range(3):
+        mask = np.zeros(Nx, np.uint8)
+        mask[rng.choice(Nx, 4, replace=False)] = 1
+        Y = O.fft2(cn(rng, Nx, 2) @ cn(rng, 2, Ny))
+        tr.push_frame(Y[np.flatnonzero(mask)], mask)
+    P1, Q1, aA, aB, w = tr.A1.copy(), tr.A2.copy(), tr.abar_A, tr.abar_B, tr.w
+    x = tr.push_frame(np.zeros((0, Ny)), np.zeros(Nx, np.uint8))
+    rho = mu / (lf * w + 1.0)
+    assert np.all(x == 0) and np.all(tr.gamma == 0)
+    np.testing.assert_allclose(tr.A1, P1 * (lf * aA / (lf * aA + rho)), rtol=1e-13, atol=0)
+    np.testing.assert_allclose(tr.A2, Q1 * (lf * aB / (lf * aB + rho)), rtol=1e-13, atol=0)

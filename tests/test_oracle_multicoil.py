@@ -198,3 +198,26 @@ def test_exact_recovery_noiseless_multicoil():
         X = As @ np.diag(cn(rng, R)) @ Bs.T
         x = tr.push_frame(np.stack([O.fft2(H[c] * X) for c in range(C)]), full)
     assert O.nrmse(x, X) < 1e-8
+
+
+def test_frame_without_lines_is_the_data_free_step():
+    """No acquired line in any coil: the data term is empty, so gamma = 0, the image is zero,
+    and what is left of each block's objective, lf abar / 2 ||X - X[t-1]||^2 + rho / 2 ||X||^2,
+    is minimised by X[t-1] lf abar / (lf abar + rho), whatever the coil maps."""
+    rng = np.random.default_rng(17)
+    Nx, Ny, R, C, lf, mu = 10, 8, 3, 4, 0.85, 0.03
+    H = cn(rng, C, Nx, Ny)
+    tr = M.MultiCoilTracker(Nx, Ny, R, H, lf, mu, 2, A=0.4 * cn(rng, Nx, R), B=0.4 * cn(rng, Ny, R))
+    for t in range(3):
+        mask = np.zeros(Nx, np.uint8)
+        mask[rng.choice(Nx, 4, replace=False)] = 1
+        Y = cn(rng, C, Nx, Ny)
+        tr.push_frame(Y[:, np.flatnonzero(mask), :], mask)
+    A1, B1, aA, aB, w = tr.A.copy(), tr.B.copy(), tr.abar_A, tr.abar_B, tr.w
+    x = tr.push_frame(np.zeros((C, 0, Ny)), np.zeros(Nx, np.uint8))
+    rho = mu / (lf * w + 1.0)
+    assert np.all(x == 0) and np.all(tr.gamma == 0)
+    np.testing.assert_allclose(tr.A, A1 * (lf * aA / (lf * aA + rho)), rtol=1e-13, atol=0)
+    np.testing.assert_allclose(tr.B, B1 * (lf * aB / (lf * aB + rho)), rtol=1e-13, atol=0)
+    assert tr.abar_A == pytest.approx(lf * aA + rho, rel=1e-15)
+    assert tr.abar_B == pytest.approx(lf * aB + rho, rel=1e-15)
