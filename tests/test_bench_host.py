@@ -76,3 +76,28 @@ def test_frame_flops_grow_with_the_line_count(s):
     k1, k2 = bench.frame_flops(256, 256, 32, 1, s), bench.frame_flops(256, 256, 32, 2, s)
     assert b > a > 0
     assert abs((a - k2) - (k2 - k1)) < 1e-6 * a
+
+
+def _profile_bench_commands():
+    import glob
+    import re
+    cmds = []
+    for path in sorted(glob.glob(os.path.join(bench.ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            m = re.search(r"python bench\.py([^\"`\n]*)", line)
+            if m:
+                cmds.append((os.path.basename(path), m.group(1).strip()))
+    return cmds
+
+
+def test_profile_commands_parse_with_the_bench(monkeypatch):
+    """Every `python bench.py ...` command recorded in profiles/ is accepted by bench.py's own
+    argument parser (a renamed or removed flag would leave a summary that cannot be re-run)."""
+    import shlex
+    cmds = _profile_bench_commands()
+    assert len(cmds) >= 6
+    for name, args in cmds:
+        argv = [a for a in shlex.split(args) if not a.startswith("$")]
+        argv = [a.replace("N", "256").replace("B", "512") if a in ("N", "B") else a for a in argv]
+        monkeypatch.setattr("sys.argv", ["bench.py", *argv])
+        bench.parse()
