@@ -1,6 +1,7 @@
 """The oracle's Philox4x32-10 against an independent implementation of the same generator:
 cuRAND's host-side PHILOX4_32_10 generator (libcurand, which runs on the CPU without a
-device), called through ctypes. No GPU is needed.
+device), called through ctypes with its legacy ordering (the one cuRAND keeps fixed across
+releases). No GPU is needed.
 
 cuRAND's host generator with a 64-bit seed s uses the key (lo32(s), hi32(s)); its pseudo-
 random stream is made of 4-word blocks, block k being the output for the counter
@@ -19,6 +20,7 @@ import pytest
 from oracle import philox
 
 CURAND_RNG_PSEUDO_PHILOX4_32_10 = 161
+CURAND_ORDERING_PSEUDO_LEGACY = 103   # the ordering cuRAND keeps the same across its releases
 SUBSEQUENCES = 65536
 
 
@@ -38,6 +40,7 @@ class HostPhilox:
         st = lib.curandCreateGeneratorHost(ctypes.byref(self.g), CURAND_RNG_PSEUDO_PHILOX4_32_10)
         if st != 0:
             pytest.skip(f"curandCreateGeneratorHost returned {st}")
+        assert lib.curandSetGeneratorOrdering(self.g, CURAND_ORDERING_PSEUDO_LEGACY) == 0
         assert lib.curandSetPseudoRandomGeneratorSeed(self.g, ctypes.c_ulonglong(seed)) == 0
 
     def words(self, block, nblocks):
