@@ -32,7 +32,8 @@ def ks_phi(A1: np.ndarray, A2: np.ndarray, rows: np.ndarray) -> np.ndarray:
 
 
 def ks_residual(A1, A2, gamma, Y, rows) -> np.ndarray:
-    """E = P_Omega(Y - A1 diag(gamma) A2^T), zero off Omega."""
+    """E = P_Omega(Y - A1 diag(gamma) A2^T), zero off Omega: the residual of the trilinear
+    k-space model of §IV-A on the sampled entries."""
     X = A1 @ np.diag(gamma) @ A2.T
     E = np.zeros_like(Y)
     E[rows, :] = Y[rows, :] - X[rows, :]
@@ -40,17 +41,21 @@ def ks_residual(A1, A2, gamma, Y, rows) -> np.ndarray:
 
 
 def ks_objective_J(A1, A2, gamma, Y, rows, mu, rho) -> float:
+    """f_t of §III-A for the k-space model of §IV-A (Alg. 2): data fit on Omega, ridge on
+    gamma, factor penalty rho / 2 on A1 and A2."""
     E = ks_residual(A1, A2, gamma, Y, rows)
     return 0.5 * float(np.vdot(E, E).real) + 0.5 * mu * float(np.vdot(gamma, gamma).real) \
         + 0.5 * rho * float(np.vdot(A1, A1).real + np.vdot(A2, A2).real)
 
 
 def ks_gradient_A1(A1, A2, gamma, Y, rows, rho) -> np.ndarray:
+    """Gradient of f_t in A1 (Alg. 2 (S2), the row updates of §IV-A)."""
     E = ks_residual(A1, A2, gamma, Y, rows)
     return rho * A1 - E @ np.conj(A2) @ np.diag(np.conj(gamma))
 
 
 def ks_gradient_A2(A1, A2, gamma, Y, rows, rho) -> np.ndarray:
+    """Gradient of f_t in A2 (Alg. 2 (S2), the row updates of §IV-A)."""
     E = ks_residual(A1, A2, gamma, Y, rows)
     return rho * A2 - E.T @ np.conj(A1) @ np.diag(np.conj(gamma))
 
@@ -124,14 +129,16 @@ class KspaceTracker:
         return self.A1 @ np.diag(self.gamma) @ self.A2.T
 
     def image(self) -> np.ndarray:
-        """F^{-1}(X_t); the paper's image is its magnitude."""
+        """F^{-1}(X_t) (§IV-A); the paper's image is its magnitude."""
         return T.ifft2(self.kspace())
 
     def line_probs(self) -> np.ndarray:
+        """Line scores of §V-B (eq. score) on the k-space factor A1, marginalised (§VI-C)."""
         return ks_line_probs(self.A1, self.Ny)
 
     def next_mask(self, k_lines: int, central: int, seed: int, stream_id: int = 0,
                   with_replacement: bool = False) -> np.ndarray:
+        """The lines of the next frame drawn from line_probs (Alg. 4)."""
         ctr = T.line_draw_counter(self.t, stream_id)
         return T.sample_lines_from_probs(self.line_probs(), k_lines, central, seed, ctr, with_replacement)
 

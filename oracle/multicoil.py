@@ -40,13 +40,14 @@ def mc_phi(A: np.ndarray, B: np.ndarray, H: np.ndarray, rows: np.ndarray) -> np.
 
 
 def mc_data(Y: np.ndarray, rows: np.ndarray) -> np.ndarray:
-    """The stacked observations y = [y_1; ...; y_C] from zero-filled coil frames
-    Y (C x Nx x Ny)."""
+    """The stacked observations y = [y_1; ...; y_C] of the coils (§IV-B data model) from
+    zero-filled coil frames Y (C x Nx x Ny)."""
     return np.concatenate([Y[c][rows, :].reshape(-1) for c in range(Y.shape[0])])
 
 
 def mc_residual(A, B, gamma, H, Y, rows) -> np.ndarray:
-    """Xi_c = P_Omega(Y_c - F(H_c .* (A diag(gamma) B^T))), zero off Omega; C x Nx x Ny."""
+    """Xi_c = P_Omega(Y_c - F(H_c .* (A diag(gamma) B^T))), zero off Omega; C x Nx x Ny: each
+    coil's k-space residual of Alg. 3 (S2) (§IV-B)."""
     X = A @ np.diag(gamma) @ B.T
     E = np.zeros_like(Y)
     for c in range(H.shape[0]):
@@ -61,32 +62,38 @@ def mc_theta(E: np.ndarray, H: np.ndarray) -> np.ndarray:
 
 def mc_objective_J(A, B, gamma, H, Y, rows, mu, rho) -> float:
     """J = 1/2 sum_c ||P_Omega(y_c - F(H_c .* (A diag gamma B^T)))||^2 + mu/2 ||gamma||^2
-    + rho/2 (||A||^2 + ||B||^2)."""
+    + rho/2 (||A||^2 + ||B||^2): f_t of §III-A for the coil model of §IV-B."""
     E = mc_residual(A, B, gamma, H, Y, rows)
     return 0.5 * float(np.vdot(E, E).real) + 0.5 * mu * float(np.vdot(gamma, gamma).real) \
         + 0.5 * rho * float(np.vdot(A, A).real + np.vdot(B, B).real)
 
 
 def mc_gradient_A(A, B, gamma, H, Y, rows, rho) -> np.ndarray:
+    """grad_A = rho A - Theta conj(B) diag(conj gamma), Theta from every coil (Alg. 3 (S2))."""
     Theta = mc_theta(mc_residual(A, B, gamma, H, Y, rows), H)
     return rho * A - Theta @ np.conj(B) @ np.diag(np.conj(gamma))
 
 
 def mc_gradient_B(A, B, gamma, H, Y, rows, rho) -> np.ndarray:
+    """grad_B = rho B - Theta^T conj(A) diag(conj gamma) (Alg. 3 (S2))."""
     Theta = mc_theta(mc_residual(A, B, gamma, H, Y, rows), H)
     return rho * B - Theta.T @ np.conj(A) @ np.diag(np.conj(gamma))
 
 
 def h_max(H: np.ndarray) -> float:
-    """max over pixels of sum_c |H_c|^2."""
+    """max over pixels of sum_c |H_c|^2: the factor by which the coil operator can scale the
+    majoriser of a factor block (the reading stated in this module's header)."""
     return float(np.max(np.sum(np.abs(H) ** 2, axis=0)))
 
 
 def mc_lipschitz_A(B, gamma, rho, hmax) -> float:
+    """alpha_A = h_max sum_r |gamma_r|^2 ||b_r||^2 + rho: the A-block Hessian bound of §III-A
+    under the coil operator."""
     return float(hmax * np.sum(np.abs(gamma) ** 2 * np.sum(np.abs(B) ** 2, axis=0)) + rho)
 
 
 def mc_lipschitz_B(A, gamma, rho, hmax) -> float:
+    """alpha_B = h_max sum_r |gamma_r|^2 ||a_r||^2 + rho (B block, as mc_lipschitz_A)."""
     return float(hmax * np.sum(np.abs(gamma) ** 2 * np.sum(np.abs(A) ** 2, axis=0)) + rho)
 
 
@@ -151,4 +158,5 @@ class MultiCoilTracker:
         return self.image()
 
     def image(self) -> np.ndarray:
+        """X_t = A[t] diag(gamma_t) B[t]^T, the image the coils share (§IV-B)."""
         return self.A @ np.diag(self.gamma) @ self.B.T

@@ -26,6 +26,8 @@ W1 = 0xBB67AE85
 
 
 def philox4x32_round(c, k):
+    """One Philox-4x32 round (Salmon et al., SC'11): two 32 x 32 -> 64-bit products, their
+    high words XORed with the other counter words and the round key, the words permuted."""
     c0, c1, c2, c3 = c
     k0, k1 = k
     p0 = M0 * c0

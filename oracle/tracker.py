@@ -47,7 +47,8 @@ from . import philox
 
 
 def dft_matrix(N: int) -> np.ndarray:
-    """Unitary, symmetric DFT matrix of size N (complex128)."""
+    """Unitary, symmetric DFT matrix of size N (complex128): the F_l, F_r of the 2D DFT in
+    matrix form F(X) = F_l X F_r (§IV)."""
     k = np.arange(N)
     kn = np.outer(k, k) % N            # exact integer phase index before the angle
     return np.exp(-2j * np.pi * kn / N) / math.sqrt(N)
@@ -82,7 +83,8 @@ def phi_matrix(A: np.ndarray, B: np.ndarray, rows: np.ndarray) -> np.ndarray:
 
 
 def ridge_gram(Phi: np.ndarray, y: np.ndarray, mu: float) -> tuple[np.ndarray, np.ndarray]:
-    """G = Phi^H Phi + mu I and h = Phi^H y (the normal equations of (S1))."""
+    """G = Phi^H Phi + mu I and h = Phi^H y: the normal equations of the ridge step (S1) of
+    Alg. 3 (closed form of §III-A)."""
     R = Phi.shape[1]
     G = Phi.conj().T @ Phi + mu * np.eye(R)
     h = Phi.conj().T @ y
@@ -90,13 +92,15 @@ def ridge_gram(Phi: np.ndarray, y: np.ndarray, mu: float) -> tuple[np.ndarray, n
 
 
 def cholesky_solve(G: np.ndarray, h: np.ndarray) -> np.ndarray:
-    """gamma = G^{-1} h via the Cholesky factor G = L L^H (LAPACK)."""
+    """gamma = G^{-1} h via the Cholesky factor G = L L^H (LAPACK); solves the (S1) system of
+    §III-A, G Hermitian positive definite for mu > 0."""
     c = scipy.linalg.cho_factor(G, lower=True)
     return scipy.linalg.cho_solve(c, h)
 
 
 def ridge_gamma(Phi: np.ndarray, y: np.ndarray, mu: float) -> np.ndarray:
-    """(S1): gamma = (Phi^H Phi + mu I)^{-1} Phi^H y."""
+    """(S1) of Alg. 3: gamma = (Phi^H Phi + mu I)^{-1} Phi^H y (the ridge closed form of
+    §III-A)."""
     G, h = ridge_gram(Phi, y, mu)
     return cholesky_solve(G, h)
 
@@ -114,7 +118,8 @@ def ridge_gamma_svd(Phi: np.ndarray, y: np.ndarray, mu: float) -> np.ndarray:
 
 
 def zero_filled(y_rows: np.ndarray, rows: np.ndarray, Nx: int) -> np.ndarray:
-    """P_Omega^T y: the observed rows placed in an Nx x Ny array of zeros."""
+    """P_Omega^T y: the observed rows placed in an Nx x Ny array of zeros (the sampling
+    operator of the subsampled data model, §II-B, with Omega = S x [Ny])."""
     Y = np.zeros((Nx, y_rows.shape[1]), np.complex128)
     Y[rows, :] = y_rows
     return Y
@@ -130,7 +135,8 @@ def residual(A, B, gamma, Y, rows) -> np.ndarray:
 
 def objective_J(A, B, gamma, Y, rows, mu, rho) -> float:
     """J = 1/2 ||P_Omega(y - F(A diag gamma B^T))||^2 + mu/2 ||gamma||^2
-    + rho/2 (||A||^2 + ||B||^2)."""
+    + rho/2 (||A||^2 + ||B||^2): the instantaneous cost f_t of §III-A with the factor
+    penalty weight rho = mu / w of the forgetting reading."""
     E = residual(A, B, gamma, Y, rows)
     return 0.5 * float(np.vdot(E, E).real) + 0.5 * mu * float(np.vdot(gamma, gamma).real) \
         + 0.5 * rho * float(np.vdot(A, A).real + np.vdot(B, B).real)
@@ -151,12 +157,14 @@ def gradient_B(A, B, gamma, Y, rows, rho) -> np.ndarray:
 
 
 def lipschitz_A(B, gamma, rho) -> float:
-    """alpha_A = sum_r |gamma_r|^2 ||b_r||^2 + rho."""
+    """alpha_A = sum_r |gamma_r|^2 ||b_r||^2 + rho: an upper bound of the A-block Hessian of
+    f_t (§III-A), Frobenius over spectral norm."""
     return float(np.sum(np.abs(gamma) ** 2 * np.sum(np.abs(B) ** 2, axis=0)) + rho)
 
 
 def lipschitz_B(A, gamma, rho) -> float:
-    """alpha_B = sum_r |gamma_r|^2 ||a_r||^2 + rho."""
+    """alpha_B = sum_r |gamma_r|^2 ||a_r||^2 + rho: the B-block counterpart of lipschitz_A
+    (§III-A)."""
     return float(np.sum(np.abs(gamma) ** 2 * np.sum(np.abs(A) ** 2, axis=0)) + rho)
 
 
@@ -273,6 +281,7 @@ class Tracker:
 
     # -- S0: the next frame's lines ------------------------------------------------
     def line_probs(self) -> np.ndarray:
+        """The line scores of §V-B (eq. score) for the next frame, marginalised (§VI-C)."""
         return informative_line_probs(self.A, self.Ny)
 
     def next_mask(self, k_lines: int, central: int, seed: int, stream_id: int = 0,
@@ -307,6 +316,8 @@ def informative_line_probs(A: np.ndarray, Ny: int) -> np.ndarray:
 
 
 def uniform_line_probs(Nx: int) -> np.ndarray:
+    """Uniform random phase-encode lines: the masks of the small-cine workload (the paper
+    itself compares its scores with the variable-density policy, §VI-C)."""
     return np.full(Nx, 1.0 / Nx)
 
 
@@ -329,12 +340,14 @@ PURPOSE_LINES = 1
 
 
 def line_draw_counter(t: int, stream_id: int = 0) -> int:
-    """64-bit draw context of frame t of a stream: (stream_id << 40) | t."""
+    """64-bit draw context of frame t of a stream: (stream_id << 40) | t. The paper leaves
+    the random source of the draws of Alg. 4 open; this counter layout is this oracle's."""
     return ((int(stream_id) & 0xFFFFFF) << 40) | (int(t) & ((1 << 40) - 1))
 
 
 def central_lines(Nx: int, central: int) -> list[int]:
-    """{-c/2, ..., c/2 - 1} mod Nx."""
+    """{-c/2, ..., c/2 - 1} mod Nx: the always-acquired low-frequency lines (DC at index 0) of
+    the Cartesian masks of §VI."""
     c = min(central, Nx)
     return sorted(((k - c // 2) % Nx) for k in range(c))
 
@@ -397,7 +410,8 @@ def sample_lines_from_probs(p, k_lines: int, central: int, seed: int, ctr: int,
 
 
 def _upper_bound(Q: list[int], x: int) -> int:
-    """First index k with Q[k] > x (binary search)."""
+    """First index k with Q[k] > x (binary search): inverts the integer CDF for one draw of
+    Alg. 4."""
     lo, hi = 0, len(Q)
     while lo < hi:
         mid = (lo + hi) // 2
@@ -414,5 +428,5 @@ def expected_distinct_lines(p_cand: np.ndarray, n_draws: int) -> float:
 
 
 def nrmse(x: np.ndarray, ref: np.ndarray) -> float:
-    """||x - ref||_F / ||ref||_F."""
+    """||x - ref||_F / ||ref||_F: the square root of the per-frame NMSE of §VI-A."""
     return float(np.linalg.norm(np.asarray(x) - ref) / np.linalg.norm(ref))
