@@ -78,7 +78,7 @@ class KspaceTracker:
 
     def push_frame(self, y_rows: np.ndarray, mask: np.ndarray, record=False) -> np.ndarray:
         """Frame t: y_rows (|S| x Ny) the acquired k-space rows in increasing row order.
-        Returns the image F^{-1}(A1[t] diag(gamma_t) A2[t]^T)."""
+        Returns the image F^{-1}(A1[t] diag(gamma_t) A2[t]^T) (Alg. 2, §IV-A)."""
         rows = np.flatnonzero(np.asarray(mask))
         Y = T.zero_filled(np.asarray(y_rows, np.complex128), rows, self.Nx)
         y = Y[rows, :].reshape(-1)

@@ -118,7 +118,7 @@ class MultiCoilTracker:
 
     def push_frame(self, y_rows: np.ndarray, mask: np.ndarray, record=False) -> np.ndarray:
         """Frame t: y_rows (C x |S| x Ny) are each coil's acquired rows in increasing row
-        order. Returns X_t = A[t] diag(gamma_t) B[t]^T."""
+        order. Returns X_t = A[t] diag(gamma_t) B[t]^T (Alg. 3 with C coils, §IV-B)."""
         rows = np.flatnonzero(np.asarray(mask))
         Y = np.zeros((self.C, self.Nx, self.Ny), np.complex128)
         Y[:, rows, :] = np.asarray(y_rows, np.complex128)

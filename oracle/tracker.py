@@ -215,7 +215,9 @@ class Tracker:
     def push_frame(self, y_rows: np.ndarray, mask: np.ndarray, record=False) -> np.ndarray:
         """Process frame t: y_rows are the acquired rows (|S| x Ny, increasing row
         order) and mask the Nx-byte line mask with S = flatnonzero(mask).
-        Returns the reconstructed image X_t = A[t] diag(gamma_t) B[t]^T."""
+        Returns the reconstructed image X_t = A[t] diag(gamma_t) B[t]^T. The steps are those of
+        Alg. 3 with one coil ((S1) ridge, (S2) majorised factor steps, §III-A surrogates),
+        repeated mm_iters times."""
         rows = np.flatnonzero(np.asarray(mask))
         Y = zero_filled(np.asarray(y_rows, np.complex128), rows, self.Nx)
         y = Y[rows, :].reshape(-1)
