@@ -144,7 +144,8 @@ int tts_get_factors(tts_handle* h, tts_c64* A, tts_c64* B, int flags);
  * tts_get_stats waits for queued work. */
 int tts_get_stats(tts_handle* h, double* abar_A, double* abar_B, double* w, int64_t* t);
 int tts_set_stats(tts_handle* h, double abar_A, double abar_B, double w, int64_t t);
-/* gamma_t of the most recent frame (R values, host). Waits. */
+/* gamma_t of the most recent frame (R values, host): the solution of the ridge step (S1)
+ * of Alg. 3 in the last MM iteration. Waits. */
 int tts_get_gamma(tts_handle* h, tts_c64* gamma);
 /* The handle's configuration as it runs: cluster_ctas is the size the library chose (or
  * the engine assigned), cuda_stream the stream its work is ordered on. */
@@ -169,7 +170,8 @@ int tts_get_config(tts_handle* h, tts_config* cfg);
  * stream passes this work). */
 int tts_push_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line_mask, int flags);
 
-/* Reconstructed frame X_t = A[t] diag(gamma_t) B[t]^T (Nx x Ny, row-major). Only the
+/* Reconstructed frame X_t = A[t] diag(gamma_t) B[t]^T (Nx x Ny, row-major; the
+ * image-domain counterpart of the interpolated frame of §IV-A). Only the
  * most recent frame is available: any other t gives TTS_ERANGE. With a host pointer
  * the call waits for the image. */
 int tts_image(tts_handle* h, int64_t t, tts_c64* out, int flags);
@@ -198,10 +200,13 @@ int tts_set_coil_maps(tts_handle* h, const tts_c64* maps, int C, int flags);
  * rate must lie in (0, 1]. */
 int tts_next_mask(tts_handle* h, double rate, uint64_t seed, uint8_t* line_mask_out, int flags);
 
-/* The line probabilities p (Nx doubles) that tts_next_mask would draw from now. */
+/* The line probabilities p (Nx doubles) that tts_next_mask would draw from now: the
+ * marginalised scores of §V-B / §VI-C under the informative policy, the fixed policy's
+ * weights otherwise. Host p waits; device p (TTS_DEVICE_PTRS) is asynchronous. */
 int tts_line_probs(tts_handle* h, double* p, int flags);
 
-/* The line draw of tts_next_mask on given probabilities p (Nx doubles, sum 1): the
+/* The line draw of tts_next_mask (Alg. 4, with or without replacement as in §V-B) on
+ * given probabilities p (Nx doubles, sum 1): the
  * central lines are kept; the other lines carry integer weights q_i = floor(p_i 2^52)
  * with inclusive prefix sums Q; draw d takes the Philox4x32-10 block at counter
  * (d, 1, ctr_lo, ctr_hi) under key (seed_lo, seed_hi), u = word0 | word1 << 32,
@@ -214,8 +219,8 @@ int tts_line_probs(tts_handle* h, double* p, int flags);
 int tts_sample_lines_from_probs(const double* p, int Nx, int k_lines, int central, uint64_t seed,
                                 uint64_t ctr, int with_replacement, uint8_t* out, int flags);
 
-/* Checkpoint: the full tracker state (configuration, factors, gamma, surrogate
- * statistics, frame counter, last mask) as an opaque host byte string. With buf NULL
+/* Checkpoint: the full tracker state (configuration, factors, gamma, the forgotten
+ * surrogate statistics of §III-A, frame counter, last mask) as an opaque host byte string. With buf NULL
  * *len receives the size needed. tts_load restores it into a handle created with the
  * same Nx, Ny, R. */
 int tts_save(tts_handle* h, void* buf, size_t* len);
@@ -237,8 +242,8 @@ int tts_launches_per_frame(tts_handle* h);
  * hold R complex128 values. Host pointers; runs on the current device, synchronously. */
 int tts_ridge_solve(const double* G, const double* h, int R, double* gamma);
 
-/* Batched unitary 2D DFT (forward: F_Nx X F_Ny; inverse: conj(F_Nx) X conj(F_Ny))
- * of `batch` row-major Nx x Ny complex images, device pointers, on `cuda_stream`
+/* Batched unitary 2D DFT (forward: F_Nx X F_Ny; inverse: conj(F_Nx) X conj(F_Ny); the
+ * 2D transform in the matrix form of §IV) of `batch` row-major Nx x Ny complex images, device pointers, on `cuda_stream`
  * (NULL = default stream). in == out is allowed; any float2-aligned pointers. Nx, Ny in
  * [1, 512] with prime factors in {2, 3, 5}. Asynchronous. */
 int tts_fft2d(const tts_c64* in, tts_c64* out, int batch, int Nx, int Ny, int inverse, void* cuda_stream);
