@@ -33,8 +33,8 @@ METRIC = "frames/s and p50/p99 frame latency at image NRMSE<=1e-4 vs plain per-f
 UNIT = "frames/s"
 
 # DRAM traffic of one fused frame_kernel launch on an informative cine-256 frame (|S| = 32),
-# dram__bytes_read.sum + dram__bytes_write.sum from the ncu capture summarised in
-# profiles/frame_kernel_cine256.md, valid only for the kernel source with this hash.
+# dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of that launch, valid
+# only for the kernel source with this hash.
 FRAME_TRAFFIC_BYTES = 422912
 FRAME_TRAFFIC_SRC_SHA = "ac3f130189929f86"
 

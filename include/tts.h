@@ -281,9 +281,12 @@ int tts_dft2d_gemm(const tts_c64* in, tts_c64* out, tts_c64* tmp, int batch, int
  * call re-initialises what must start at zero. Calls whose work overlaps on the GPU
  * (several host threads, or several streams) race on the array and give wrong results:
  * serialise them. The first call on a device looks up the array's device address (with
- * that device current); make that first call before any stream capture. The call is
- * asynchronous on cuda_stream (NULL = default stream) and does not report non-finite
- * input samples: such a frame is skipped on the device. */
+ * that device current); make that first call before any stream capture. Every call fills
+ * the twiddle tables of its sizes and clears the status words in the array with one small
+ * kernel of its own before the frame kernel; nothing is copied from host memory. The call
+ * is asynchronous on cuda_stream (NULL = the legacy default stream). A frame with a
+ * non-finite input sample is skipped on the device: A, B, gamma and stats are left as
+ * they were, so stats[3] (frames processed) not advancing is how the caller sees it. */
 #define TTS_NOALLOC_MAX_N 256
 #define TTS_NOALLOC_MAX_R 32
 #define TTS_NOALLOC_SCRATCH_BYTES (2u << 20)

@@ -58,23 +58,29 @@ __global__ void __launch_bounds__(Shape<NX>::NT, lines_minb<NX>())
   }
 }
 
-// resident CTAs of a kernel (occupancy x SMs), computed once per instantiation
+// resident CTAs of a kernel (occupancy x SMs), computed once per instantiation and device
 template <typename K>
-int resident(K kernel, int threads, int smem, int* cache) {
-  if (*cache > 0) return *cache;
-  int per_sm = 0, dev = 0, sms = 0;
-  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
-      cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1)
+int resident(K kernel, int threads, int smem, PerDevice* cache) {
+  int res = 0;
+  if (per_device(*cache,
+                 [&](int dev, int* v) {
+                   int per_sm = 0, sms = 0;
+                   if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+                           cudaSuccess ||
+                       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+                       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1)
+                     return TTS_ECUDA;
+                   *v = per_sm * sms;
+                   return TTS_OK;
+                 },
+                 &res) != TTS_OK)
     return 0;
-  *cache = per_sm * sms;
-  return *cache;
+  return res;
 }
 
 template <int NY, bool INV>
 int rows_t(const float2* in, float2* out, int nimg, int Nx, const float2* W, cudaStream_t st) {
-  static int cache = 0;
+  static PerDevice cache;
   constexpr int smem = fftband::smem_bytes<NY>();
   const int res = resident(fft_row_bands_kernel<NY, INV>, Shape<NY>::NT, smem, &cache);
   if (res < 1) return TTS_ECUDA;
@@ -85,7 +91,7 @@ int rows_t(const float2* in, float2* out, int nimg, int Nx, const float2* W, cud
 
 template <int NX, bool INV>
 int cols_t(float2* data, int nimg, int Ny, const float2* W, float scale, cudaStream_t st) {
-  static int cache = 0;
+  static PerDevice cache;
   constexpr int smem = fftband::smem_bytes<NX>();
   const int res = resident(fft_col_bands_kernel<NX, INV>, Shape<NX>::NT, smem, &cache);
   if (res < 1) return TTS_ECUDA;

@@ -158,19 +158,23 @@ template <int N, bool INV>
 int launch_t(const float2* in, float2* out, int batch, const float2* W, int* err, cudaStream_t st) {
   constexpr int NB = N / Shape<N>::BAND;
   constexpr int smem = fftband::smem_bytes<N>();
-  static int grid = 0;
-  if (grid == 0) {
-    if (cudaFuncSetAttribute(fft2d_square_kernel<N, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-        cudaSuccess)
-      return TTS_ECUDA;
-    int per_sm = 0, dev = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fft2d_square_kernel<N, INV>, Shape<N>::NT, smem) !=
-            cudaSuccess ||
-        cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1)
-      return TTS_ECUDA;
-    grid = per_sm * sms;
-  }
+  static PerDevice grids;
+  int grid = 0;
+  if (per_device(grids,
+                 [](int dev, int* v) {
+                   if (cudaFuncSetAttribute(fft2d_square_kernel<N, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            smem) != cudaSuccess)
+                     return TTS_ECUDA;
+                   int per_sm = 0, sms = 0;
+                   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fft2d_square_kernel<N, INV>,
+                                                                     Shape<N>::NT, smem) != cudaSuccess ||
+                       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1)
+                     return TTS_ECUDA;
+                   *v = per_sm * sms;
+                   return TTS_OK;
+                 },
+                 &grid) != TTS_OK)
+    return TTS_ECUDA;
   const int tasks = 2 * NB * batch;
   const int g = std::min(grid, tasks);
   // lag between an image's row and column tasks: the 2 NB L tasks in between are about three

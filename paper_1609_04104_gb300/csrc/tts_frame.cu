@@ -1074,7 +1074,9 @@ int launch_ridge(const double2* G, const double2* h, int R, double2* gamma, cuda
 int frame_configure(FrameParams& p, int requested_C, int smem_limit) {
   int maxsm = smem_limit;
   if (maxsm <= 0) {
-    if (cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0) != cudaSuccess || maxsm <= 0)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || maxsm <= 0)
       maxsm = 227 * 1024;
     // the persistent multi-stream kernel keeps its frame parameters in static shared
     // memory: leave room for them so that one layout serves both kernels
@@ -1106,15 +1108,21 @@ int frame_configure(FrameParams& p, int requested_C, int smem_limit) {
 
 template <int OWN>
 static int launch_frame_t(const FrameParams& p, int launch_mode, cudaStream_t st) {
-  static bool attrs = false;
+  static PerDevice attrs;
+  int done = 0;
+  if (per_device(attrs,
+                 [](int, int* v) {
+                   if (cudaFuncSetAttribute(frame_kernel<OWN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            227 * 1024) != cudaSuccess ||
+                       cudaFuncSetAttribute(frame_kernel<OWN>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                           cudaSuccess)
+                     return TTS_ECUDA;
+                   *v = 1;
+                   return TTS_OK;
+                 },
+                 &done) != TTS_OK)
+    return TTS_ECUDA;
   cudaError_t e;
-  if (!attrs) {
-    e = cudaFuncSetAttribute(frame_kernel<OWN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e != cudaSuccess) return TTS_ECUDA;
-    e = cudaFuncSetAttribute(frame_kernel<OWN>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return TTS_ECUDA;
-    attrs = true;
-  }
   const int smem = p.lay.bytes;
   const int nsteps = frame_num_steps(p.K);
   if (launch_mode == TTS_LAUNCH_FUSED) {
@@ -1163,8 +1171,10 @@ template <int OWN>
 static int frame_batch_limits_t(int C, int* max_dyn_smem, int* max_clusters) {
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, frame_batch_kernel<OWN>) != cudaSuccess) return TTS_ECUDA;
-  int optin = 0;
-  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0) != cudaSuccess) return TTS_ECUDA;
+  int optin = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return TTS_ECUDA;
   const int dyn = optin - (int)fa.sharedSizeBytes;
   if (cudaFuncSetAttribute(frame_batch_kernel<OWN>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess ||
       cudaFuncSetAttribute(frame_batch_kernel<OWN>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "../../include/tts.h"
 
 #define TTS_MAX_N 512
@@ -12,6 +14,36 @@
 #define TTS_MAX_CLUSTER 16
 #define TTS_THREADS 512
 #define TTS_MAX_OWN 8     // register-owned outputs per thread (64 x 64 / 512)
+
+// ------------------------------------------------------------------------------------
+// Per-device set-up of a kernel (shared-memory opt-in, cluster permission, occupancy):
+// kernel attributes belong to the device that was current when they were set, so a value
+// is computed once per device ordinal, with that device current, and reused. Thread-safe;
+// a failed computation is not remembered.
+// ------------------------------------------------------------------------------------
+#define TTS_MAX_DEVICES 64
+struct PerDevice {
+  std::mutex mu;
+  int val[TTS_MAX_DEVICES] = {};
+  bool have[TTS_MAX_DEVICES] = {};
+};
+
+// *out = compute(dev, &v) result v for the current device dev (computed on first use).
+template <typename F>
+inline int per_device(PerDevice& c, F&& compute, int* out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= TTS_MAX_DEVICES) return TTS_ECUDA;
+  std::lock_guard<std::mutex> lk(c.mu);
+  if (!c.have[dev]) {
+    int v = 0;
+    const int rc = compute(dev, &v);
+    if (rc != TTS_OK) return rc;
+    c.val[dev] = v;
+    c.have[dev] = true;
+  }
+  *out = c.val[dev];
+  return TTS_OK;
+}
 
 // ------------------------------------------------------------------------------------
 // complex float / double helpers

@@ -554,13 +554,15 @@ int launch_image(const float2* A, const float2* B, const float2* gamma, float2* 
                  cudaStream_t st) {
   // 32-row tiles while they fill every SM, else 8-row tiles (four times the CTAs)
   const int smem = 2 * 32 * (R + 1) * (int)sizeof(float2);
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      return TTS_ECUDA;
-  }
+  static PerDevice sm_count;
+  int sms = 0;
+  if (per_device(sm_count,
+                 [](int dev, int* v) {
+                   return cudaDeviceGetAttribute(v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess ? TTS_OK
+                                                                                                      : TTS_ECUDA;
+                 },
+                 &sms) != TTS_OK)
+    return TTS_ECUDA;
   const int tiles32 = ((Ny + 31) / 32) * ((Nx + 31) / 32);
   if (tiles32 >= sms) {
     dim3 grid((Ny + 31) / 32, (Nx + 31) / 32);

@@ -48,6 +48,24 @@ namespace {
 std::mutex g_mu;
 void* g_addr[64];         // device address of g_noalloc_scratch, per device ordinal
 
+// Per call, before the frame kernel: the twiddle tables exp(-2 pi i k / N) of this call's
+// sizes (from double-precision sincospi, rounded to float) and the zeroed status words,
+// written into the scratch on the device, so the call copies nothing from host memory.
+__global__ void noalloc_setup_kernel(float2* Wx, int Nx, float2* Wy, int Ny, int* status, int nstatus) {
+  const int n = Nx + Ny + nstatus;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    if (k < Nx + Ny) {
+      const bool x = k < Nx;
+      const int i = x ? k : k - Nx, N = x ? Nx : Ny;
+      double sn, cs;
+      sincospi(2.0 * (double)i / (double)N, &sn, &cs);
+      (x ? Wx : Wy)[i] = make_float2((float)cs, (float)-sn);
+    } else {
+      status[k - Nx - Ny] = 0;
+    }
+  }
+}
+
 int na_fail(int code, const char* msg) {
   tts_internal_set_error(msg);
   return code;
@@ -150,20 +168,10 @@ extern "C" int tts_push_frame_noalloc(const tts_frame_args* a, void* cuda_stream
   p.status = (int*)take(sizeof(int) * (1 + TTS_MAX_CLUSTER));
 
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  // twiddles of this call's sizes, computed on the host stack exactly as a handle does
-  float2 wx[kMaxN], wy[kMaxN];
-  for (int k = 0; k < Nx; ++k) {
-    const double ang = 2.0 * M_PI * (double)k / (double)Nx;
-    wx[k] = make_float2((float)cos(ang), (float)-sin(ang));
-  }
-  for (int k = 0; k < Ny; ++k) {
-    const double ang = 2.0 * M_PI * (double)k / (double)Ny;
-    wy[k] = make_float2((float)cos(ang), (float)-sin(ang));
-  }
-  if (cudaMemcpyAsync(Wx, wx, sizeof(float2) * Nx, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(Wy, wy, sizeof(float2) * Ny, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemsetAsync(p.status, 0, sizeof(int) * (1 + TTS_MAX_CLUSTER), st) != cudaSuccess)
-    return na_fail(TTS_ECUDA, "tts_push_frame_noalloc: copy into the device scratch failed");
+  const int nstatus = 1 + TTS_MAX_CLUSTER;
+  noalloc_setup_kernel<<<(Nx + Ny + nstatus + 255) / 256, 256, 0, st>>>(Wx, Nx, Wy, Ny, p.status, nstatus);
+  if (cudaGetLastError() != cudaSuccess)
+    return na_fail(TTS_ECUDA, "tts_push_frame_noalloc: set-up of the device scratch failed");
   if (launch_frame(p, TTS_LAUNCH_FUSED, st) != TTS_OK)
     return na_fail(TTS_ECUDA, "tts_push_frame_noalloc: frame kernel launch failed");
   return TTS_OK;

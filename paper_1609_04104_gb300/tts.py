@@ -335,14 +335,38 @@ def tts_push_frame_noalloc(A, B, stats, gamma, y_rows, line_mask, lambda_forget,
                            update=TTS_UPDATE_GAUSS_SEIDEL, full_frame=False, stream=None) -> None:
     """Frame update on caller-held device state (torch CUDA tensors) that allocates
     nothing: A (Nx x R), B (Ny x R), gamma (R) complex64; stats (4) float64 holding
-    w, abar_A, abar_B, frames; y_rows and line_mask as for tts_push_frame."""
+    w, abar_A, abar_B, frames; y_rows (the acquired rows, |S| x Ny, or with full_frame the
+    whole Nx x Ny frame) complex64 and line_mask (Nx) uint8 as for tts_push_frame. Runs on
+    `stream`, by default torch's current stream. The library reads and writes these
+    buffers by their sizes, so every dtype and size is checked here first."""
+    import torch
     for t in (A, B, stats, gamma, y_rows, line_mask):
         if not _is_torch(t) or not t.is_cuda or not t.is_contiguous():
             raise ValueError("tts_push_frame_noalloc takes contiguous CUDA tensors")
-    args = tts_frame_args(A.shape[0], B.shape[0], A.shape[1], lambda_forget, mu, mm_iters, update,
+    c64 = torch.complex64
+    if A.dtype != c64 or B.dtype != c64 or gamma.dtype != c64 or y_rows.dtype != c64:
+        raise ValueError("A, B, gamma and y_rows must be complex64")
+    if stats.dtype != torch.float64 or stats.numel() < 4:
+        raise ValueError("stats must be float64 with at least 4 elements")
+    if line_mask.dtype != torch.uint8:
+        raise ValueError("line_mask must be uint8")
+    if A.dim() != 2 or B.dim() != 2 or A.shape[1] != B.shape[1]:
+        raise ValueError("A (Nx x R) and B (Ny x R) must be matrices with the same number of columns")
+    Nx, Ny, R = A.shape[0], B.shape[0], A.shape[1]
+    if gamma.numel() < R:
+        raise ValueError(f"gamma needs at least R = {R} elements")
+    if line_mask.numel() < Nx:
+        raise ValueError(f"line_mask needs at least Nx = {Nx} elements")
+    rows = Nx if full_frame else int(np.count_nonzero(line_mask[:Nx].cpu().numpy()))   # host copy: no device allocation
+    if y_rows.numel() < rows * Ny:
+        raise ValueError(f"y_rows needs at least {rows} x {Ny} elements")
+    args = tts_frame_args(Nx, Ny, R, lambda_forget, mu, mm_iters, update,
                           A.data_ptr(), B.data_ptr(), stats.data_ptr(), gamma.data_ptr(), y_rows.data_ptr(),
                           line_mask.data_ptr(), TTS_FULL_FRAME if full_frame else 0)
-    s = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    if stream is None:
+        s = torch.cuda.current_stream(A.device).cuda_stream
+    else:
+        s = stream if isinstance(stream, int) else stream.cuda_stream
     _check(load().tts_push_frame_noalloc(ctypes.byref(args), s))
 
 

@@ -79,25 +79,27 @@ def test_frame_flops_grow_with_the_line_count(s):
 
 
 def _profile_bench_commands():
-    import glob
-    import re
+    """(summary, bench.py arguments) pairs from profiles/commands.txt."""
     cmds = []
-    for path in sorted(glob.glob(os.path.join(bench.ROOT, "profiles", "*.md"))):
-        for line in open(path):
-            m = re.search(r"python bench\.py([^\"`\n]*)", line)
-            if m:
-                cmds.append((os.path.basename(path), m.group(1).strip()))
+    for line in open(os.path.join(bench.ROOT, "profiles", "commands.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        name, args = (x.strip() for x in line.split("|", 1))
+        cmds.append((name, args))
     return cmds
 
 
 def test_profile_commands_parse_with_the_bench(monkeypatch):
-    """Every `python bench.py ...` command recorded in profiles/ is accepted by bench.py's own
-    argument parser (a renamed or removed flag would leave a summary that cannot be re-run)."""
+    """Every bench command listed for the summaries in profiles/ is accepted by bench.py's own
+    argument parser (a renamed or removed flag would leave a summary that cannot be re-run),
+    and every summary has its command listed."""
+    import glob
     import shlex
     cmds = _profile_bench_commands()
-    assert len(cmds) >= 6
+    summaries = {os.path.basename(p) for p in glob.glob(os.path.join(bench.ROOT, "profiles", "*.md"))}
+    assert summaries and summaries <= {name for name, _ in cmds}
     for name, args in cmds:
-        argv = [a for a in shlex.split(args) if not a.startswith("$")]
-        argv = [a.replace("N", "256").replace("B", "512") if a in ("N", "B") else a for a in argv]
-        monkeypatch.setattr("sys.argv", ["bench.py", *argv])
+        assert name in summaries, name
+        monkeypatch.setattr("sys.argv", ["bench.py", *shlex.split(args)])
         bench.parse()
