@@ -70,7 +70,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
-    ap.add_argument("--cpu-sample-frames", type=int, default=8)
+    ap.add_argument("--cpu-sample-frames", type=int, default=None,
+                    help="frames of the oracle's CPU-baseline run (default: the whole sequence)")
+    ap.add_argument("--ref-sample-frames", type=int, default=8,
+                    help="frames the reference arm (the oracle) times per step")
     ap.add_argument("--batched", action="store_true",
                     help="64 uneven streams through the multi-stream engine vs one stream at a time")
     ap.add_argument("--streams", type=int, default=64)
@@ -154,6 +157,29 @@ class ClockSampler:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def measure_fp32_peak(dev: int, clocks: bool = True) -> dict:
+    """The GPU's FP32 FMA throughput, measured live by the library's calibration kernel
+    (every SM filled, eight independent FMA chains per thread, best of three timed launches),
+    with the SM clock sampled while it runs: the denominator of the ALU rooflines."""
+    import torch
+
+    from paper_1609_04104_gb300 import tts
+    sampler = ClockSampler(dev, enabled=clocks)
+    tflops, ms = tts.tts_fp32_fma_rate(2_000_000, 3)
+    clk = sampler.stop()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clk or {}).get("sm_mhz")
+    return {"tflops": tflops, "best_launch_ms": ms, "sms": sms, "sm_mhz_median": mhz,
+            "note": f"measured: FP32 FMA throughput of this GPU (tts_fp32_fma_rate: {sms} SMs filled, 8 FMA "
+                    f"chains per thread, best of 3 launches of {ms:.0f} ms)"
+                    + (f" at a median SM clock of {mhz:.0f} MHz" if mhz else "")}
+
+
+PRECISION = ("FP32 transforms and factor steps; every sum of the ridge normal equations (S1) in float-float "
+             "(FP64 grade), the readout sums of the last MM iteration's system included, and gamma refined "
+             "to FP64 grade against it (TTS_RIDGE_FF_LAST)")
 
 
 def aggregate_ranks(ms: float, frames: int, world: int, device: str = "cpu") -> tuple[float, int]:
@@ -249,6 +275,12 @@ def run_tts(args, rank, world):
     total_ms, frames_total = aggregate_ranks(float(np.sum(step_ms)), T * args.steps, world, f"cuda:{dev}")
     value = frames_total / (total_ms / 1e3)
 
+    # the same trajectory once more, untimed, keeping every image, drawn mask and line score
+    # for the parity check against the oracle (cpu_baseline leg)
+    record = None
+    if rank == 0 and not args.no_cpu_baseline:
+        record = record_trajectory(trk, w, T, Yd, ones, mask, seed, reset, stream, dev)
+
     # plain per-frame path (one launch per phase) on the same inputs: image agreement
     nrmse_plain = None
     if args.launch == "fused":
@@ -320,8 +352,8 @@ def run_tts(args, rank, world):
     nfull = min(w.warmup_frames, T)
     flops = [frame_flops(Nx, Ny, R, K, Nx if t < w.warmup_frames else S) for t in range(T)]
     flops_per_launch = float(np.mean(flops))
-    sm_mhz = (clk or {}).get("sm_max_mhz", 2070.0) if clk else 2070.0
-    peak_tflops = 152 * 128 * 2 * 2070e6 / 1e12
+    peak = measure_fp32_peak(dev, clocks=not args.no_clocks)
+    peak_tflops = peak["tflops"]
     achieved = flops_per_launch / kmean / 1e12
     bytes_per_launch = float(np.mean([(Nx if t < nfull else S) * Ny * 8 + Nx + 2 * K * (Nx + Ny) * R * 8
                                       for t in range(T)]))
@@ -330,12 +362,12 @@ def run_tts(args, rank, world):
             "traffic_note": "DRAM bytes per fused launch on an informative frame (|S|=32), ncu",
             "flops_per_launch": flops_per_launch, "algorithmic_bytes_per_launch": bytes_per_launch,
             "achieved_gbs": bytes_per_launch / kmean / 1e9, "avg_launch_us": kmean * 1e6,
-            "peak_note": "FP32 SIMT peak 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived, not measured)"}
+            "peak_note": peak["note"], "peak_measured": peak}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 ridge solve)", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "precision": PRECISION, "data": "synthetic",
         "config": {"workload": w.name, "Nx": Nx, "Ny": Ny, "R": R, "T": T, "mm_iters": K,
                    "lambda_forget": w.lambda_forget, "mu": w.mu, "rate": w.rate, "k_lines": S,
                    "warmup_frames": w.warmup_frames, "launch": args.launch,
@@ -354,15 +386,43 @@ def run_tts(args, rank, world):
     if args.launch == "phases":
         out["gpu_launches"] = args.steps * (T * tts.tts_launches_per_frame(trk.h) + T + max(0, T - w.warmup_frames))
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args, tts_images=True, trk_factory=(trk, Yh, A0, B0))
+        out["cpu_baseline"] = cpu_baseline(args, T, record, launch, args.cluster)
     trk.close()
     return out
+
+
+def record_trajectory(trk, w, T, Yd, ones, mask, seed, reset, stream, dev):
+    """One pass of the timed per-frame sequence (same calls, same stream) that keeps every
+    frame's image, drawn mask and the line scores the draw used."""
+    import torch
+
+    from paper_1609_04104_gb300 import tts
+    imgs = torch.empty((T, w.Nx, w.Ny), dtype=torch.complex64, device=f"cuda:{dev}")
+    masks = torch.empty((T, w.Nx), dtype=torch.uint8, device=f"cuda:{dev}")
+    probs = torch.zeros((T, w.Nx), dtype=torch.float64, device=f"cuda:{dev}")
+    reset()
+    with torch.cuda.stream(stream):
+        for t in range(T):
+            if t < w.warmup_frames:
+                m = ones
+            else:
+                tts.tts_line_probs(trk.h, probs[t])
+                tts.tts_next_mask(trk.h, w.rate, seed, mask)
+                m = mask
+            masks[t].copy_(m)
+            tts.tts_push_frame(trk.h, Yd[t], m, full_frame=True)
+            tts.tts_image(trk.h, t, imgs[t])
+    torch.cuda.synchronize()
+    return {"images": imgs.cpu().numpy(), "masks": masks.cpu().numpy(), "probs": probs.cpu().numpy()}
 
 
 # ------------------------------------------------------------------------------------
 # the FP64 oracle on the host cores (bounded sample)
 # ------------------------------------------------------------------------------------
-def oracle_sample(n_frames):
+def oracle_sample(n_frames, probs=False):
+    """The FP64 oracle on the first n_frames of the cine-256 sequence with its own line draws
+    (Alg. 5 order). Returns (seconds spent in its frame updates and draws, images, masks,
+    line scores of each draw, Y, A0, B0)."""
     from oracle import tracker as O
     from paper_1609_04104_gb300 import inputs
     w = inputs.CINE256
@@ -370,37 +430,80 @@ def oracle_sample(n_frames):
     Y = inputs.kspace(w, L)
     A0, B0 = inputs.init_factors(w.Nx, w.Ny, w.R, w.seed)
     tr = O.Tracker(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, w.mm_iters, A=A0, B=B0)
-    t0 = time.perf_counter()
-    imgs, masks = [], []
+    el = 0.0
+    imgs, masks, ps = [], [], []
     for t in range(n_frames):
+        if t >= w.warmup_frames and probs:
+            ps.append(tr.line_probs())       # untimed: the scores the draw below uses
+        else:
+            ps.append(np.zeros(w.Nx))
+        t0 = time.perf_counter()
         m = np.ones(w.Nx, np.uint8) if t < w.warmup_frames else tr.next_mask(w.k_lines, w.central_lines, seed=w.seed)
         imgs.append(tr.push_frame(inputs.observed_rows(Y[t], m), m))
+        el += time.perf_counter() - t0
         masks.append(m)
-    el = time.perf_counter() - t0
-    return el, imgs, masks, Y, A0, B0
+    return el, imgs, masks, ps, Y, A0, B0
 
 
-def cpu_baseline(args, tts_images=False, trk_factory=None):
-    n = args.cpu_sample_frames
-    el, imgs, masks, Y, A0, B0 = oracle_sample(n)
+def image_errors(x, ref):
+    """Per-frame NRMSE and worst-element error max|x - ref| / max|ref|."""
+    return (float(np.linalg.norm(x - ref) / np.linalg.norm(ref)),
+            float(np.max(np.abs(x - ref)) / np.max(np.abs(ref))))
+
+
+def error_summary(errs):
+    e = np.array(errs) if errs else np.zeros((0, 2))
+    if len(e) == 0:
+        return {"frames": 0}
+    return {"frames": int(len(e)), "nrmse_max": float(e[:, 0].max()), "nrmse_median": float(np.median(e[:, 0])),
+            "worst_element_max": float(e[:, 1].max()), "worst_frame": int(np.argmax(e[:, 0]))}
+
+
+def cpu_baseline(args, T, record=None, launch=0, cluster=0):
+    """The FP64 oracle on the host cores over the sequence (by default all T frames), timed,
+    and the parity of the CUDA path with it over those frames in two modes: (a) the oracle's
+    line masks fed to a fresh tracker of the timed configuration; (b) the timed trajectory
+    with its own draws (record), compared until the first frame whose mask differs from the
+    oracle's, with the line-score gap at that frame."""
+    from paper_1609_04104_gb300 import inputs, tts
+    w = inputs.CINE256
+    n = min(T, args.cpu_sample_frames or T)
+    el, imgs, masks, ps, Y, A0, B0 = oracle_sample(n, probs=record is not None)
     res = {"value": n / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-           "sample": f"frames 0-{n - 1} of the 200-frame 256x256 R=32 sequence "
-                     f"({min(n, 5)} fully sampled warm-up frames, the rest at 32/256 lines); "
-                     f"numpy FP64, dense DFT matrices, BLAS on all host cores"}
-    if tts_images and trk_factory is not None:
-        # image agreement of the CUDA path with the oracle on the oracle's masks
-        from paper_1609_04104_gb300 import inputs, tts
-        _, _, A, B = trk_factory
-        w = inputs.CINE256
-        g = tts.Tracker(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, mm_iters=w.mm_iters, central_lines=w.central_lines)
-        g.set_factors(A0, B0)
-        worst = 0.0
+           "sample": f"frames 0-{n - 1} of the {w.T}-frame 256x256 R=32 sequence ({min(n, w.warmup_frames)} "
+                     f"fully sampled warm-up frames, the rest at 32/256 lines drawn by the oracle); numpy FP64, "
+                     f"dense DFT matrices, BLAS on all host cores; timed: frame updates and draws"}
+    # (a) the oracle's masks fed to both sides
+    g = tts.Tracker(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, mm_iters=w.mm_iters, central_lines=w.central_lines,
+                    launch=launch, cluster_ctas=cluster)
+    g.set_factors(A0, B0)
+    errs = []
+    for t in range(n):
+        g.push_frame(inputs.observed_rows(Y[t], masks[t]), masks[t])
+        errs.append(image_errors(g.image(t), imgs[t]))
+    g.close()
+    parity = {"bound": 1e-4, "oracle_masks": error_summary(errs)}
+    res["image_nrmse_vs_oracle"] = parity["oracle_masks"]["nrmse_max"]
+    # (b) the timed trajectory's own draws
+    if record is not None:
+        own, div = [], None
+        gap = 0.0
         for t in range(n):
-            g.push_frame(inputs.observed_rows(Y[t], masks[t]), masks[t])
-            x = g.image(t)
-            worst = max(worst, float(np.linalg.norm(x - imgs[t]) / np.linalg.norm(imgs[t])))
-        g.close()
-        res["image_nrmse_vs_oracle"] = worst
+            if t >= w.warmup_frames:
+                po, pg = ps[t], record["probs"][t]
+                gap = max(gap, float(np.max(np.abs(pg - po) / po)))
+            if not np.array_equal(record["masks"][t], masks[t]):
+                div = {"frame": t,
+                       "lines_only_gpu": [int(i) for i in np.flatnonzero(record["masks"][t] & ~masks[t])],
+                       "lines_only_oracle": [int(i) for i in np.flatnonzero(masks[t] & ~record["masks"][t])],
+                       "max_rel_score_gap": gap}
+                break
+            own.append(image_errors(record["images"][t], imgs[t]))
+        parity["own_draws"] = error_summary(own)
+        parity["own_draws"]["masks_identical_frames"] = len(own)
+        parity["own_draws"]["max_rel_score_gap"] = gap
+        parity["own_draws"]["first_mask_divergence"] = div
+    res["parity"] = parity
     return res
 
 
@@ -409,7 +512,7 @@ def run_reference(args, rank, world):
         return None
     from paper_1609_04104_gb300 import inputs
     w = inputs.CINE256
-    n = args.cpu_sample_frames
+    n = args.ref_sample_frames
     for _ in range(args.warmup):
         oracle_sample(min(n, 2))
     times = [oracle_sample(n)[0] for _ in range(args.steps)]
@@ -630,12 +733,13 @@ def run_batched(args):
     flops_step = float(np.mean([sum(frame_flops(w.Nx, w.Ny, w.R, w.mm_iters, w.Nx if t < w.warmup_frames else
                                                 w.k_lines) for w in ws) for t in range(T)]))
     mean_s = float(np.mean(step_ms)) * 1e-3
-    peak_tflops = 152 * 128 * 2 * 2070e6 / 1e12
+    peak = measure_fp32_peak(torch.cuda.current_device(), clocks=not args.no_clocks)
+    peak_tflops = peak["tflops"]
     achieved = flops_step / mean_s / 1e12
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": T, "warmup": max(3, args.warmup),
         "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 (FP64 ridge solve)", "data": "synthetic",
+        "dtype": "f32", "precision": PRECISION, "data": "synthetic",
         "config": {"workload": f"uneven_streams_{n}", "streams": n, "T": T,
                    "sizes": sorted({(w.Nx, w.Ny) for w in ws}), "ranks": sorted({w.R for w in ws}),
                    "rates": sorted({round(w.rate, 4) for w in ws}), "mm_iters": 3, "cluster_ctas": C,
@@ -656,8 +760,7 @@ def run_batched(args):
         "cpu_baseline": cpu,
         "roofline": {"bound": "alu", "kernel": "engine step (frame_batch_kernel + image + sampler)",
                      "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                     "traffic": None, "flops_per_step": flops_step,
-                     "peak_note": "FP32 SIMT peak 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived)"},
+                     "traffic": None, "flops_per_step": flops_step, "peak_note": peak["note"]},
         "clocks": clk,
     }
 
@@ -812,7 +915,7 @@ def run_serve(args):
     return {
         "metric": METRIC, "value": frames_done / wall, "unit": UNIT, "n_gpus": 1, "steps": len(step_sizes),
         "warmup": 0, "ms_per_step": busy / max(1, len(step_sizes)) * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 ridge solve)", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "precision": PRECISION, "data": "synthetic",
         "config": {"workload": "serving_poisson" if not args.preload else "serving_preloaded",
                    "streams": len(arr), "arrival_rate_per_s": None if args.preload else args.serve_rate,
                    "frames_per_stream": args.serve_frames, "fps_range": [20, 50],
@@ -959,7 +1062,7 @@ def precision_cpu_baseline(args, w, Y, A0, B0, masks, images):
     lines (timed on the host cores), and every form's per-frame image NRMSE against it."""
     from oracle import tracker as O
     from paper_1609_04104_gb300 import inputs
-    n = min(len(masks), args.cpu_sample_frames * 5)
+    n = min(len(masks), (args.cpu_sample_frames or 8) * 5)
     tr = O.Tracker(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, w.mm_iters, A=A0, B=B0)
     t0 = time.perf_counter()
     ref = [tr.push_frame(inputs.observed_rows(Y[t], masks[t]), masks[t]) for t in range(n)]
@@ -1045,7 +1148,10 @@ def run_multicoil(args):
     achieved = frame_bytes / (float(np.mean(lat)) * 1e-3) / 1e9
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": float(np.sum(lat)) / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32 (FP64 ridge solve)", "data": "synthetic",
+           "vs_baseline": None, "dtype": "f32",
+           "precision": "FP32 coil transforms and factor steps; the stacked-coil Gram and right-hand side reduced "
+                        "across rows in FP64, gamma solved to FP64 grade (FP32 inverse, float-float refinement)",
+           "data": "synthetic",
            "config": {"workload": w.name, "Nx": w.Nx, "Ny": w.Ny, "R": w.R, "coils": C, "T": T,
                       "mm_iters": w.mm_iters, "lines": s_lines, "masks": "8 central + uniform, fixed per frame",
                       "l2": "256 MiB buffer written before every timed step"},

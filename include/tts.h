@@ -94,6 +94,21 @@ enum {
 
 typedef struct tts_handle tts_handle;
 
+/* Precision of the ridge step (S1 of Alg. 3, closed form of §III-A). The normal equations
+ * (Phi^H Phi + mu I) gamma = Phi^H y are formed from the frame's FP32 operands (the rows of the
+ * transformed factors and frame) with every sum accumulated in float-float arithmetic (exact
+ * products, error-free additions: about 48 significant bits, FP64 grade), and solved by an FP32
+ * Gauss-Jordan inverse refined against that float-float system (FP64-grade gamma). The sums over
+ * the readout axis (B^H B and Yt conj(B), |S| Ny R products) are the costly part:
+ * TTS_RIDGE_FF_ALL accumulates them in float-float in every MM iteration; TTS_RIDGE_FF_LAST only
+ * for the last MM iteration's system, whose solution is the frame's gamma_t (the earlier MM
+ * iterations' ridge steps, which only steer the FP32 factor steps, then take those two sums in
+ * FP32; every other sum, the Gram product and the solve stay float-float). */
+enum {
+  TTS_RIDGE_FF_ALL = 0,
+  TTS_RIDGE_FF_LAST = 1
+};
+
 typedef struct {
   int Nx, Ny, R;            /* grid and PARAFAC rank; 1 <= Nx, Ny <= 512 with prime factors in {2,3,5}; 1 <= R <= 64 */
   double lambda_forget;     /* forgetting factor in (0, 1] of the surrogate statistics */
@@ -111,6 +126,7 @@ typedef struct {
   void* cuda_stream;        /* cudaStream_t to enqueue on; NULL = a stream the handle creates */
   int row_dft;              /* TTS_ROWDFT_*: how the acquired rows are transformed each frame */
   int kspace;               /* 0: image-domain factors (Alg. 3); 1: k-space factors (Alg. 2) */
+  int ridge_precision;      /* TTS_RIDGE_*: which MM iterations accumulate their readout sums in float-float */
 } tts_config;
 
 /* Fill cfg with defaults: mm_iters 1, central_lines 8, TTS_POLICY_INFORMATIVE, vd_alpha -1,
@@ -147,6 +163,16 @@ int tts_set_stats(tts_handle* h, double abar_A, double abar_B, double w, int64_t
 /* gamma_t of the most recent frame (R values, host): the solution of the ridge step (S1)
  * of Alg. 3 in the last MM iteration. Waits. */
 int tts_get_gamma(tts_handle* h, tts_c64* gamma);
+/* The same gamma_t at the accuracy the ridge step solved it to (its float-float value
+ * hi + lo, summed in FP64; see TTS_RIDGE_*): 2R host doubles (re, im interleaved). Waits. */
+int tts_get_gamma_fp64(tts_handle* h, double* gamma);
+/* Test hook: the FP32 operands of the first MM iteration's ridge step of the most recent
+ * frame (the only one when mm_iters = 1), from which the separable form builds
+ * Phi^H Phi = (Ahat_S^H Ahat_S) .* (B^H B) and Phi^H y = colsum(conj(Ahat_S) .* (Yt conj(B)))
+ * with B = B[t-1]: Ahat_S = (F_Nx A[t-1])[S, :] (|S| x R, row-major; with kspace, the rows S of
+ * A1), Yt = y_S conj(F_Ny) (|S| x Ny; with kspace, y_S), and S (increasing row indices).
+ * Host buffers of at least Nx x R, Nx x Ny and Nx elements; *nrows receives |S|. Waits. */
+int tts_get_ridge_operands(tts_handle* h, tts_c64* Ahat_S, tts_c64* Yt, int* rows, int* nrows);
 /* The handle's configuration as it runs: cluster_ctas is the size the library chose (or
  * the engine assigned), cuda_stream the stream its work is ordered on. */
 int tts_get_config(tts_handle* h, tts_config* cfg);
@@ -289,7 +315,7 @@ int tts_dft2d_gemm(const tts_c64* in, tts_c64* out, tts_c64* tmp, int batch, int
  * they were, so stats[3] (frames processed) not advancing is how the caller sees it. */
 #define TTS_NOALLOC_MAX_N 256
 #define TTS_NOALLOC_MAX_R 32
-#define TTS_NOALLOC_SCRATCH_BYTES (2u << 20)
+#define TTS_NOALLOC_SCRATCH_BYTES (4u << 20)
 
 typedef struct {
   int Nx, Ny, R;
@@ -405,6 +431,14 @@ int tts_engine_info(tts_engine* e, tts_engine_stats* stats);
  * candidate run at their next larger size that fits, as in an engine). Synchronous; allocates the
  * temporary engines and frames on the current device and frees them before returning. */
 int tts_engine_autotune(const tts_config* cfgs, int n, int steps, int* best_C, double* step_ms);
+
+/* Calibration (no counterpart in the paper): the device's FP32 fused multiply-add rate,
+ * the denominator of the frame kernel's ALU roofline. A kernel fills every SM (the largest
+ * number of 256-thread CTAs that fit) and each thread runs eight independent chains of
+ * 16 x iters FMAs; one untimed launch, then `reps` launches timed with CUDA events on the
+ * legacy default stream. *tflops = 2 x FMAs / best time (TFLOP/s), *ms = best time (NULL
+ * allowed). Synchronous; no allocation. */
+int tts_fp32_fma_rate(int iters, int reps, double* tflops, double* ms);
 
 const char* tts_last_error(void);
 

@@ -68,8 +68,11 @@ std::vector<Piece> handle_pieces(tts_handle* h, int Nx, int Ny, int R, int C) {
       {(void**)&p.AhS[0], sizeof(float2) * Nx * R},     {(void**)&p.AhS[1], sizeof(float2) * Nx * R},
       {(void**)&p.nA[0], sizeof(float) * R},            {(void**)&p.nA[1], sizeof(float) * R},
       {(void**)&p.MB, sizeof(float2) * R * R},          {(void**)&p.P, sizeof(float2) * Nx * R},
+      {(void**)&p.MBlo, sizeof(float2) * R * R},        {(void**)&p.Plo, sizeof(float2) * Nx * R},
+      {(void**)&p.MA, sizeof(float2) * R * R},          {(void**)&p.MAlo, sizeof(float2) * R * R},
       {(void**)&p.partA, sizeof(float2) * C * Nx * R},  {(void**)&p.partNA, sizeof(float) * C * R},
-      {(void**)&p.partMB, sizeof(float2) * C * R * R},  {(void**)&p.partP, sizeof(float2) * C * Nx * R},
+      {(void**)&p.partMB, sizeof(float4) * C * R * R},  {(void**)&p.partP, sizeof(float4) * C * Nx * R},
+      {(void**)&p.partMA, sizeof(float4) * C * R * R},
       {(void**)&p.sc, sizeof(double) * SC_COUNT},
       {(void**)&p.sf, sizeof(double) * SF_COUNT},       {(void**)&p.gamma, sizeof(float2) * R},
       {(void**)&p.gamma_d, sizeof(double2) * R},        {(void**)&p.status, sizeof(int) * (2 + TTS_MAX_CLUSTER)},
@@ -101,6 +104,8 @@ int handle_check_config(const tts_config* c) {
   if (!isfinite(c->vd_alpha)) return fail(TTS_EINVAL, "vd_alpha must be finite%s");
   if (c->row_dft < TTS_ROWDFT_FFT || c->row_dft > TTS_ROWDFT_BF16) return fail(TTS_EINVAL, "unknown row_dft%s");
   if (c->kspace != 0 && c->kspace != 1) return fail(TTS_EINVAL, "kspace must be 0 or 1%s");
+  if (c->ridge_precision != TTS_RIDGE_FF_ALL && c->ridge_precision != TTS_RIDGE_FF_LAST)
+    return fail(TTS_EINVAL, "unknown ridge_precision%s");
   if (c->kspace && c->row_dft != TTS_ROWDFT_FFT) return fail(TTS_EINVAL, "the k-space tracker transforms no rows%s");
   if (c->row_dft != TTS_ROWDFT_FFT && !dft_gemm_size_ok(c->Ny))
     return fail(TTS_EINVAL, "the tensor-core row transform needs Ny a multiple of 32 in [32, 256]%s");
@@ -173,7 +178,8 @@ int handle_create(const tts_config* cfg, void* mem, tts_handle** out) {
     off += align_up(pc.bytes);
   }
   p.K = cfg->mm_iters;
-  p.refine = 4;
+  p.refine = 5;
+  p.ridge_ff_all = cfg->ridge_precision == TTS_RIDGE_FF_ALL ? 1 : 0;
   p.jacobi = cfg->update == TTS_UPDATE_JACOBI;
   p.lf = cfg->lambda_forget;
   p.mu = cfg->mu;
@@ -339,6 +345,7 @@ void tts_config_init(tts_config* c, int Nx, int Ny, int R, double lambda_forget,
   c->cuda_stream = nullptr;
   c->row_dft = TTS_ROWDFT_FFT;
   c->kspace = 0;
+  c->ridge_precision = TTS_RIDGE_FF_LAST;
 }
 
 int tts_create(int Nx, int Ny, int R, double lambda_forget, double mu, tts_handle** out) {
@@ -410,6 +417,29 @@ int tts_set_stats(tts_handle* h, double abar_A, double abar_B, double w, int64_t
 int tts_get_gamma(tts_handle* h, tts_c64* gamma) {
   if (!h || !gamma) return fail(TTS_EINVAL, "NULL argument%s");
   CK(cudaMemcpyAsync(gamma, h->fp.gamma, sizeof(float2) * h->cfg.R, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return TTS_OK;
+}
+
+int tts_get_gamma_fp64(tts_handle* h, double* gamma) {
+  if (!h || !gamma) return fail(TTS_EINVAL, "NULL argument%s");
+  CK(cudaMemcpyAsync(gamma, h->fp.gamma_d, sizeof(double2) * h->cfg.R, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return TTS_OK;
+}
+
+int tts_get_ridge_operands(tts_handle* h, tts_c64* Ahat_S, tts_c64* Yt, int* rows, int* nrows) {
+  if (!h || !Ahat_S || !Yt || !rows || !nrows) return fail(TTS_EINVAL, "NULL argument%s");
+  if (h->mc) return fail(TTS_EINVAL, "the multi-coil tracker has no separable operands%s");
+  int s = 0;
+  CK(cudaMemcpyAsync(&s, h->fp.nrows, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (s < 0 || s > h->cfg.Nx) return fail(TTS_ESTATE, "no frame processed yet%s");
+  *nrows = s;
+  CK(cudaMemcpyAsync(Ahat_S, h->fp.AhS[0], sizeof(float2) * (size_t)s * h->cfg.R, cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaMemcpyAsync(Yt, h->fp.Yt, sizeof(float2) * (size_t)s * h->cfg.Ny, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(rows, h->fp.rows, sizeof(int) * (size_t)s, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return TTS_OK;
 }

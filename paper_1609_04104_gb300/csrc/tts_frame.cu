@@ -47,9 +47,9 @@ struct SM {
   int* misc;  // [0] |S|, [1] non-finite flag
   float* red;
   float2 *A, *A0, *B, *B0;  // this CTA's rows (rA x R, rB x R)
-  float2 *Gf;               // R x R
-  float2 *GJa, *GJb;        // Rp x Rp (R padded to a multiple of 16)
-  float2 *Pk, *Tk;          // 16 x 16 block inverse, 16 x Rp block row
+  float2 *Gf;               // R x R ridge matrix (hi)
+  float2 *GJa, *GJb;        // the ridge inverse (32 x 40 or 64 x 72) / R x R products
+  float2* Pk;               // pivot rows of the inverse and the refinement flags
   float2 *gam, *glo, *h, *rr, *tmpv;  // R each
   double* ds;               // 8 doubles
   float* fs;                // 8 floats
@@ -74,7 +74,6 @@ __device__ SM carve(const FrameParams& p, unsigned char* base) {
   s.GJa = (float2*)(base + L.GJa);
   s.GJb = (float2*)(base + L.GJb);
   s.Pk = (float2*)(base + L.gjx);
-  s.Tk = s.Pk + 256;
   float2* v = (float2*)(base + L.vec);
   const int R = p.R;
   s.gam = v;
@@ -120,156 +119,208 @@ __device__ __forceinline__ void ff_add_ff(float& hi, float& lo, float h2, float 
   fast_two_sum(s, e, hi, lo);
 }
 
-// ---------------------------------------------------------------------------------
-// Ridge solve (S1): (G_hi + G_lo) gamma = h_hi + h_lo. FP32 Gauss-Jordan inverse of G_hi
-// (pivots on the diagonal; G is Hermitian positive definite), then `iters` refinement
-// sweeps gamma += Ginv (h - G gamma) with the residual in float-float arithmetic and
-// gamma held as a float-float pair (gam + glo); the sweeps stop once every correction is
-// below sqrt(tol2) relative. G_hi in sm.Gf, h_hi in sm.h.
-// ---------------------------------------------------------------------------------
-// Inverse of the 16 x 16 diagonal block at [kb, kb+16) of M (row stride ld), by one warp:
-// Gauss-Jordan in registers, lane = column (lane & 15) of rows 8 (lane >> 4) + 0..7;
-// rows and columns of the pivot are exchanged with shuffles. Result into P (16 x 16).
-__device__ __forceinline__ void warp_inverse16(const float2* M, int ld, int kb, float2* P) {
-  const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31, c = lane & 15, h = lane >> 4;
-  float2 m[8];
+// Float-float accumulation of sums of products of FP32 numbers (the ridge system's sums):
+// every product exact (two_prod), every addition error-free (two_sum), the low part
+// renormalised after each pair of products, so the sum carries about 48 significant bits.
+// hi + lo += a1 b1 + a2 b2
+__device__ __forceinline__ void ff_acc2(float& hi, float& lo, float a1, float b1, float a2, float b2) {
+  float p, pe, s, e;
+  two_prod(a1, b1, p, pe);
+  two_sum(hi, p, s, e);
+  lo = lo + (e + pe);
+  two_prod(a2, b2, p, pe);
+  two_sum(s, p, hi, e);
+  lo = lo + (e + pe);
+  fast_two_sum(hi, lo, hi, lo);
+}
+// complex float-float accumulator (re: rh + rl, im: ih + il)
+struct CFF {
+  float rh, rl, ih, il;
+};
+__device__ __forceinline__ CFF cff_zero() { return CFF{0.f, 0.f, 0.f, 0.f}; }
+// acc += conj(a) b
+__device__ __forceinline__ void cff_macc(CFF& c, float2 a, float2 b) {
+  ff_acc2(c.rh, c.rl, a.x, b.x, a.y, b.y);
+  ff_acc2(c.ih, c.il, a.x, b.y, -a.y, b.x);
+}
+// acc += conj(a) (b + bl): the product with the hi part exact, with the lo part rounded
+__device__ __forceinline__ void cff_macc_ff(CFF& c, float2 a, float2 b, float2 bl) {
+  cff_macc(c, a, b);
+  const float2 t = cmulc(a, bl);
+  float s, e;
+  two_sum(c.rh, t.x, s, e);
+  c.rh = s;
+  c.rl = c.rl + e;
+  two_sum(c.ih, t.y, s, e);
+  c.ih = s;
+  c.il = c.il + e;
+}
+__device__ __forceinline__ float4 cff_pack(const CFF& c) {
+  float rh, rl, ih, il;
+  fast_two_sum(c.rh, c.rl, rh, rl);
+  fast_two_sum(c.ih, c.il, ih, il);
+  return make_float4(rh, ih, rl, il);
+}
+// float-float sum of n float4 partials (hi.x, hi.y, lo.x, lo.y) `stride` apart
+__device__ __forceinline__ float4 ff_sum_partials(const float4* src, size_t stride, int n) {
+  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+  for (int c = 0; c < n; c += 4) {
+    float4 v[4];
 #pragma unroll
-  for (int e = 0; e < 8; ++e) m[e] = M[(kb + 8 * h + e) * ld + kb + c];
+    for (int u = 0; u < 4; ++u) v[u] = c + u < n ? src[(c + u) * stride] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int qe = q & 7, qh = q >> 3;
-    float2 d, rq, cq[8];
-    d.x = __shfl_sync(FULL, m[qe].x, q + 16 * qh);
-    d.y = __shfl_sync(FULL, m[qe].y, q + 16 * qh);
-    rq.x = __shfl_sync(FULL, m[qe].x, c + 16 * qh);
-    rq.y = __shfl_sync(FULL, m[qe].y, c + 16 * qh);
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      cq[e].x = __shfl_sync(FULL, m[e].x, q + 16 * h);
-      cq[e].y = __shfl_sync(FULL, m[e].y, q + 16 * h);
-    }
-    const float inv = __frcp_rn(cabs2(d));
-    const float2 piv = make_float2(d.x * inv, -d.y * inv);
-    const float2 rqp = cmul(rq, piv);
-    // branch-free update (the row and column of the pivot are lane dependent)
-    const bool colq = (c == q);
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const bool rowq = (h == qh) && (e == qe);
-      float2 gen = m[e];
-      cfms(gen, cq[e], rqp);
-      const float2 t = cmul(cq[e], piv);
-      const float2 colv = make_float2(-t.x, -t.y);
-      const float2 rv = colq ? piv : rqp;
-      const float2 ov = colq ? colv : gen;
-      m[e] = rowq ? rv : ov;
+    for (int u = 0; u < 4; ++u) {
+      ff_add_ff(rh, rl, v[u].x, v[u].z);
+      ff_add_ff(ih, il, v[u].y, v[u].w);
     }
   }
-#pragma unroll
-  for (int e = 0; e < 8; ++e) P[(8 * h + e) * 16 + c] = m[e];
+  return make_float4(rh, ih, rl, il);
+}
+// (q, r), q <= r, of entry idx of the row-major upper triangle of an R x R matrix
+__device__ __forceinline__ void tri_pair(int idx, int R, int& q, int& r) {
+  const float b = 2.f * (float)R + 1.f;
+  int qq = (int)((b - sqrtf(b * b - 8.f * (float)idx)) * 0.5f);
+  qq = max(0, min(R - 1, qq));
+  while (qq > 0 && qq * R - qq * (qq - 1) / 2 > idx) --qq;
+  while (qq + 1 < R && (qq + 1) * R - (qq + 1) * qq / 2 <= idx) ++qq;
+  q = qq;
+  r = qq + (idx - (qq * R - qq * (qq - 1) / 2));
 }
 
-template <int OWN>
-__device__ void ridge_solve(SM& sm, int R, const float2* Glo, const float2* hlo, int iters, float tol2) {
-  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
-  const int Rp = (R + 15) & ~15;
-  const int RP2 = Rp * Rp;
-  int oi[OWN], oj[OWN];
+// ---------------------------------------------------------------------------------
+// Ridge solve (S1): (G_hi + G_lo) gamma = h_hi + h_lo, G Hermitian positive definite.
+// An FP32 Gauss-Jordan inverse of G_hi (diagonal pivots: each is a Schur complement of a
+// positive-definite matrix), gamma_0 = Ginv h_hi, then refinement sweeps
+// gamma += Ginv (h - G gamma) with the residual formed in float-float arithmetic and gamma
+// held as a float-float pair (gam + glo). Each sweep multiplies the error by about
+// kappa(G) u_32, so two sweeps reach the float-float accuracy of the system; the sweeps
+// stop once every correction is below sqrt(tol2) relative.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void bar_named(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Gauss-Jordan inverse of G (R x R, row stride R; padded with the identity to RP x RP) into
+// Gi (row stride RP + 8) by warps 0 .. RP/8 - 1: warp w keeps rows 8w .. 8w+7 in registers,
+// lane l the columns l + 32q. Each pivot step publishes the scaled pivot row through `prow`
+// (two slots, 2 RP float2) and the warps meet at named barrier 1; the pivot column comes
+// from the lane that holds it by shuffles. The pivot loop is not unrolled (the kernel's
+// phases run once per MM iteration, so compact code matters more than loop overhead):
+// registers of the pivot row and column are picked by selects. Other warps return at once.
+template <int RP>
+__device__ void gj_inverse_warps(const float2* G, int R, float2* Gi, float2* prow) {
+  constexpr int NW = RP / 8, CPL = RP / 32, LD = RP + 8;
+  const unsigned FULL = 0xffffffffu;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp >= NW) return;
+  float2 M[8][CPL];
 #pragma unroll
-  for (int o = 0; o < OWN; ++o) {
-    const int e = tid + o * nth;
-    oi[o] = e / Rp;
-    oj[o] = e - oi[o] * Rp;
-  }
-  // G padded with the identity to Rp x Rp
+  for (int r = 0; r < 8; ++r)
 #pragma unroll
-  for (int o = 0; o < OWN; ++o) {
-    const int e = tid + o * nth;
-    if (e < RP2) {
-      const int i = oi[o], j = oj[o];
-      sm.GJa[e] = (i < R && j < R) ? sm.Gf[i * R + j] : make_float2(i == j ? 1.f : 0.f, 0.f);
+    for (int q = 0; q < CPL; ++q) {
+      const int i = warp * 8 + r, j = lane + 32 * q;
+      M[r][q] = (i < R && j < R) ? G[i * R + j] : make_float2(i == j ? 1.f : 0.f, 0.f);
     }
-  }
-  __syncthreads();
-  // blocked Gauss-Jordan inverse with 16 x 16 pivot blocks (Hermitian positive definite:
-  // every pivot block is a Schur complement and invertible)
-  float2* M = sm.GJa;
-  float2* N = sm.GJb;
-  for (int kb = 0; kb < Rp; kb += 16) {
-    if (warp == 0) warp_inverse16(M, Rp, kb, sm.Pk);
-    __syncthreads();
-    // block row k of the update: T = P M[kb:kb+16, :]
-    for (int e = tid; e < 16 * Rp; e += nth) {
-      const int t = e / Rp, cc = e - t * Rp;
-      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll 1
+  for (int k = 0; k < RP; ++k) {
+    const int ow = k >> 3, kr = k & 7, kl = k & 31, kq = k >> 5;
+    float2* pr = prow + (k & 1) * RP;
+    if (warp == ow) {
+      float2 rowk[CPL];
 #pragma unroll
-      for (int u = 0; u < 16; u += 2) {
-        cfma(a0, sm.Pk[t * 16 + u], M[(kb + u) * Rp + cc]);
-        cfma(a1, sm.Pk[t * 16 + u + 1], M[(kb + u + 1) * Rp + cc]);
+      for (int q = 0; q < CPL; ++q) {
+        rowk[q] = M[0][q];
+#pragma unroll
+        for (int r = 1; r < 8; ++r) rowk[q] = r == kr ? M[r][q] : rowk[q];
       }
-      sm.Tk[e] = cadd(a0, a1);
-    }
-    __syncthreads();
+      float2 dk = rowk[0];
 #pragma unroll
-    for (int o = 0; o < OWN; ++o) {
-      const int e = tid + o * nth;
-      if (e < RP2) {
-        const int i = oi[o], cc = oj[o];
-        const bool bi = (i >= kb) && (i < kb + 16), bc = (cc >= kb) && (cc < kb + 16);
-        float2 v;
-        if (bi) {
-          v = bc ? sm.Pk[(i - kb) * 16 + (cc - kb)] : sm.Tk[(i - kb) * Rp + cc];
-        } else {
-          // column source: the block inverse for pivot-block columns, else T (no divergence)
-          const float2* src = bc ? sm.Pk + (cc - kb) : sm.Tk + cc;
-          const int ld = bc ? 16 : Rp;
-          float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+      for (int q = 1; q < CPL; ++q) dk = q == kq ? rowk[q] : dk;
+      float2 d;
+      d.x = __shfl_sync(FULL, dk.x, kl);
+      d.y = __shfl_sync(FULL, dk.y, kl);
+      const float inv = __frcp_rn(cabs2(d));
+      const float2 piv = make_float2(d.x * inv, -d.y * inv);   // 1 / d
 #pragma unroll
-          for (int u = 0; u < 16; u += 2) {
-            cfma(a0, M[i * Rp + kb + u], src[u * ld]);
-            cfma(a1, M[i * Rp + kb + u + 1], src[(u + 1) * ld]);
-          }
-          const float2 a = cadd(a0, a1);
-          const float2 base = bc ? make_float2(0.f, 0.f) : M[e];
-          v = csub(base, a);
-        }
-        N[e] = v;
+      for (int q = 0; q < CPL; ++q) {
+        const float2 v = (lane + 32 * q == k) ? piv : cmul(rowk[q], piv);
+        pr[lane + 32 * q] = v;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) M[r][q] = r == kr ? v : M[r][q];
       }
     }
-    __syncthreads();
-    float2* t = M;
-    M = N;
-    N = t;
+    bar_named(1, NW * 32);
+    float2 rk[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) rk[q] = pr[lane + 32 * q];
+    const float2 piv = pr[k];
+    const bool own = warp == ow;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      float2 src = M[r][0];
+#pragma unroll
+      for (int q = 1; q < CPL; ++q) src = q == kq ? M[r][q] : src;
+      float2 c;
+      c.x = __shfl_sync(FULL, src.x, kl);
+      c.y = __shfl_sync(FULL, src.y, kl);
+      const float2 col = cmul(c, piv);
+      const bool skip = own && r == kr;   // the pivot row itself
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        float2 gen = M[r][q];
+        cfms(gen, c, rk[q]);
+        const float2 v = (lane + 32 * q == k) ? make_float2(-col.x, -col.y) : gen;
+        M[r][q] = skip ? M[r][q] : v;
+      }
+    }
   }
-  const float2* Gi = M;   // inverse, row stride Rp
-  // gamma_0 = Ginv h (one warp per row)
-  for (int i = warp; i < R; i += nwarp) {
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) Gi[(warp * 8 + r) * LD + lane + 32 * q] = M[r][q];
+}
+
+// sum over the 8 lanes of a row group (lanes 8g .. 8g+7) of a float2
+__device__ __forceinline__ float2 sum8(float2 v) {
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+// Refinement against G_hi (sm.Gf, row stride R) + Glo and h_hi (sm.h) + hlo with the inverse
+// Gi (row stride RP + 8): 8 threads per row (all R <= 64 rows in one pass of 512 threads).
+// The result is gamma = sm.gam + sm.glo. Ends with a block barrier.
+template <int RP>
+__device__ void ridge_refine(SM& sm, int R, const float2* Gi, const float2* Glo, const float2* hlo, int iters,
+                             float tol2) {
+  constexpr int LD = RP + 8;
+  const int tid = threadIdx.x, i = tid >> 3, u = tid & 7;
+  const bool row = i < R;
+  // three (max |delta|^2, max |gamma|^2) pairs used in turn: sweep `it` reads pair it % 3
+  // after its last barrier and clears pair (it + 1) % 3, last read two sweeps earlier
+  unsigned* flags = (unsigned*)(sm.Pk + 128);
+  if (tid < 6) flags[tid] = 0u;
+  // gamma_0 = Ginv h_hi
+  {
     float2 acc = make_float2(0.f, 0.f);
-    for (int j = lane; j < R; j += 32) cfma(acc, Gi[i * Rp + j], sm.h[j]);
-    for (int o = 16; o > 0; o >>= 1) {
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-    }
-    if (lane == 0) {
+    if (row)
+      for (int j = u; j < R; j += 8) cfma(acc, Gi[i * LD + j], sm.h[j]);
+    acc = sum8(acc);
+    if (row && u == 0) {
       sm.gam[i] = acc;
       sm.glo[i] = make_float2(0.f, 0.f);
     }
   }
   __syncthreads();
-  // convergence: max_i |delta_i|^2 <= tol2 max_i |gamma_i|^2 (float bits of non-negative
-  // floats order like unsigned integers)
-  unsigned* dmax = (unsigned*)(sm.tmpv);
-  unsigned* gmax = dmax + 1;
   for (int it = 0; it < iters; ++it) {
-    if (tid == 0) {
-      *dmax = 0u;
-      *gmax = 0u;
-    }
-    // r = h - G gamma in float-float (warp per row)
-    for (int i = warp; i < R; i += nwarp) {
-      float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-      for (int j = lane; j < R; j += 32) {
+    unsigned* fl = flags + 2 * (it % 3);
+    // r = h - G gamma, every product exact (two_prod), sums in float-float
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    if (row)
+      for (int j = u; j < R; j += 8) {
         const float2 g = sm.Gf[i * R + j];
         const float2 x = sm.gam[j], xl = sm.glo[j];
         float pp, e;
@@ -283,46 +334,57 @@ __device__ void ridge_solve(SM& sm, int R, const float2* Glo, const float2* hlo,
         ff_add_ff(ih, il, pp, e);
         float2 cc = cmul(g, xl);
         if (Glo) cfma(cc, Glo[i * R + j], x);
-        const float cr = cc.x, ci = cc.y;
-        ff_add_f(rh, rl, cr);
-        ff_add_f(ih, il, ci);
+        ff_add_f(rh, rl, cc.x);
+        ff_add_f(ih, il, cc.y);
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        const float a = __shfl_xor_sync(0xffffffffu, rh, o), b = __shfl_xor_sync(0xffffffffu, rl, o);
-        const float c = __shfl_xor_sync(0xffffffffu, ih, o), d = __shfl_xor_sync(0xffffffffu, il, o);
-        ff_add_ff(rh, rl, a, b);
-        ff_add_ff(ih, il, c, d);
-      }
-      if (lane == 0) {
-        float sh = sm.h[i].x, sl = hlo ? hlo[i].x : 0.f;
-        ff_add_ff(sh, sl, -rh, -rl);
-        float th = sm.h[i].y, tl = hlo ? hlo[i].y : 0.f;
-        ff_add_ff(th, tl, -ih, -il);
-        sm.rr[i] = make_float2(sh + sl, th + tl);
-      }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      const float a = __shfl_xor_sync(0xffffffffu, rh, o), b = __shfl_xor_sync(0xffffffffu, rl, o);
+      const float c = __shfl_xor_sync(0xffffffffu, ih, o), d = __shfl_xor_sync(0xffffffffu, il, o);
+      ff_add_ff(rh, rl, a, b);
+      ff_add_ff(ih, il, c, d);
     }
+    if (row && u == 0) {
+      float sh = sm.h[i].x, sl = hlo ? hlo[i].x : 0.f;
+      ff_add_ff(sh, sl, -rh, -rl);
+      float th = sm.h[i].y, tl = hlo ? hlo[i].y : 0.f;
+      ff_add_ff(th, tl, -ih, -il);
+      sm.rr[i] = make_float2(sh + sl, th + tl);
+    }
+    if (tid < 2) flags[2 * ((it + 1) % 3) + tid] = 0u;   // the next sweep's pair
     __syncthreads();
     // gamma += Ginv r
-    for (int i = warp; i < R; i += nwarp) {
-      float2 acc = make_float2(0.f, 0.f);
-      for (int j = lane; j < R; j += 32) cfma(acc, Gi[i * Rp + j], sm.rr[j]);
-      for (int o = 16; o > 0; o >>= 1) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-      }
-      if (lane == 0) {
-        float2 g = sm.gam[i], gl = sm.glo[i];
-        atomicMax(dmax, __float_as_uint(cabs2(acc)));
-        atomicMax(gmax, __float_as_uint(cabs2(g)));
-        ff_add_ff(g.x, gl.x, acc.x, 0.f);
-        ff_add_ff(g.y, gl.y, acc.y, 0.f);
-        sm.gam[i] = g;
-        sm.glo[i] = gl;
-      }
+    float2 acc = make_float2(0.f, 0.f);
+    if (row)
+      for (int j = u; j < R; j += 8) cfma(acc, Gi[i * LD + j], sm.rr[j]);
+    acc = sum8(acc);
+    if (row && u == 0) {
+      float2 g = sm.gam[i], gl = sm.glo[i];
+      atomicMax(fl, __float_as_uint(cabs2(acc)));
+      atomicMax(fl + 1, __float_as_uint(cabs2(g)));
+      ff_add_ff(g.x, gl.x, acc.x, 0.f);
+      ff_add_ff(g.y, gl.y, acc.y, 0.f);
+      sm.gam[i] = g;
+      sm.glo[i] = gl;
     }
     __syncthreads();
-    if (__uint_as_float(*dmax) <= tol2 * __uint_as_float(*gmax)) break;
+    // float bits of non-negative floats order like unsigned integers
+    if (__uint_as_float(fl[0]) <= tol2 * __uint_as_float(fl[1])) break;
+  }
+}
+
+// The whole solve; G_hi in sm.Gf, h_hi in sm.h. Uses sm.GJa (64 x 72 float2 at most) for the
+// inverse and sm.Pk (136 float2) for the pivot rows and the sweep flags. Ends with a block
+// barrier.
+__device__ void ridge_solve(SM& sm, int R, const float2* Glo, const float2* hlo, int iters, float tol2) {
+  if (R <= 32) {
+    gj_inverse_warps<32>(sm.Gf, R, sm.GJa, sm.Pk);
     __syncthreads();
+    ridge_refine<32>(sm, R, sm.GJa, Glo, hlo, iters, tol2);
+  } else {
+    gj_inverse_warps<64>(sm.Gf, R, sm.GJa, sm.Pk);
+    __syncthreads();
+    ridge_refine<64>(sm, R, sm.GJa, Glo, hlo, iters, tol2);
   }
 }
 
@@ -402,34 +464,50 @@ __device__ __forceinline__ void load_yb(const FrameParams& p, float2* YB, int m0
   }
 }
 
-// (B^H B)[q][r] and P[m][r] = sum over this CTA's rows j of Yt[m][j] conj(B[j][r])
+// (B^H B)[q][r] and P[m][r] = sum over this CTA's rows j of Yt[m][j] conj(B[j][r]), as float4
+// partials (hi, lo). With ff, the sums are accumulated in float-float (B^H B on its upper
+// triangle, mirrored); else in FP32 (lo = 0).
 template <int OWN>
-__device__ void partials_B(const FrameParams& p, SM& sm, int cta, bool do_mb, bool do_p) {
+__device__ void partials_B(const FrameParams& p, SM& sm, int cta, bool do_mb, bool do_p, bool ff) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int Nx = p.Nx, R = p.R, MC = p.MC, RR = R * R;
   const int s = sm.misc[0];
   const Slice bs = slice_of(p.Ny, p.C, cta);
   const int nb = bs.hi - bs.lo;
   if (do_mb) {
-    float2* pmb = p.partMB + (size_t)cta * RR;
+    float4* pmb = p.partMB + (size_t)cta * RR;
+    if (ff) {
+      const int RT = R * (R + 1) / 2;
+      for (int idx = tid; idx < RT; idx += nth) {
+        int q, r;
+        tri_pair(idx, R, q, r);
+        CFF acc = cff_zero();
+        for (int jl = 0; jl < nb; ++jl) cff_macc(acc, sm.B[jl * R + q], sm.B[jl * R + r]);
+        const float4 v = cff_pack(acc);
+        pmb[q * R + r] = v;
+        if (q != r) pmb[r * R + q] = make_float4(v.x, -v.y, v.z, -v.w);
+      }
+    } else {
 #pragma unroll
-    for (int o = 0; o < OWN; ++o) {
-      const int e = tid + o * nth;
-      if (e < RR) {
-        const int q = e / R, r = e - q * R;
-        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-        int jl = 0;
-        for (; jl + 1 < nb; jl += 2) {
-          cfmac(a0, sm.B[jl * R + q], sm.B[jl * R + r]);
-          cfmac(a1, sm.B[(jl + 1) * R + q], sm.B[(jl + 1) * R + r]);
+      for (int o = 0; o < OWN; ++o) {
+        const int e = tid + o * nth;
+        if (e < RR) {
+          const int q = e / R, r = e - q * R;
+          float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+          int jl = 0;
+          for (; jl + 1 < nb; jl += 2) {
+            cfmac(a0, sm.B[jl * R + q], sm.B[jl * R + r]);
+            cfmac(a1, sm.B[(jl + 1) * R + q], sm.B[(jl + 1) * R + r]);
+          }
+          if (jl < nb) cfmac(a0, sm.B[jl * R + q], sm.B[jl * R + r]);
+          const float2 v = cadd(a0, a1);
+          pmb[e] = make_float4(v.x, v.y, 0.f, 0.f);
         }
-        if (jl < nb) cfmac(a0, sm.B[jl * R + q], sm.B[jl * R + r]);
-        pmb[e] = cadd(a0, a1);
       }
     }
   }
   if (!do_p) return;
-  float2* pp = p.partP + (size_t)cta * Nx * R;
+  float4* pp = p.partP + (size_t)cta * Nx * R;
   float2* YB = s <= MC ? sm.yb : sm.chunk;
   for (int m0 = 0; m0 < s; m0 += MC) {
     const int mc = min(MC, s - m0);
@@ -438,14 +516,22 @@ __device__ void partials_B(const FrameParams& p, SM& sm, int cta, bool do_mb, bo
     if (s <= MC) sm.yb_ready = true;
     for (int e = tid; e < mc * R; e += nth) {
       const int mm = e / R, r = e - mm * R;
-      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-      int jl = 0;
-      for (; jl + 1 < nb; jl += 2) {
-        cfma(a0, YB[mm * nb + jl], cconj(sm.B[jl * R + r]));
-        cfma(a1, YB[mm * nb + jl + 1], cconj(sm.B[(jl + 1) * R + r]));
+      if (ff) {
+        // Yt[m][j] conj(B[j][r]) = conj(B[j][r]) Yt[m][j]
+        CFF acc = cff_zero();
+        for (int jl = 0; jl < nb; ++jl) cff_macc(acc, sm.B[jl * R + r], YB[mm * nb + jl]);
+        pp[(m0 + mm) * R + r] = cff_pack(acc);
+      } else {
+        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+        int jl = 0;
+        for (; jl + 1 < nb; jl += 2) {
+          cfma(a0, YB[mm * nb + jl], cconj(sm.B[jl * R + r]));
+          cfma(a1, YB[mm * nb + jl + 1], cconj(sm.B[(jl + 1) * R + r]));
+        }
+        if (jl < nb) cfma(a0, YB[mm * nb + jl], cconj(sm.B[jl * R + r]));
+        const float2 v = cadd(a0, a1);
+        pp[(m0 + mm) * R + r] = make_float4(v.x, v.y, 0.f, 0.f);
       }
-      if (jl < nb) cfma(a0, YB[mm * nb + jl], cconj(sm.B[jl * R + r]));
-      pp[(m0 + mm) * R + r] = cadd(a0, a1);
     }
     __syncthreads();
   }
@@ -510,7 +596,7 @@ __device__ void step_ingest(const FrameParams& p, SM& sm, int cta) {
   for (int e = as.lo * R + tid; e < as.hi * R; e += nth) p.A0[e] = p.A[e];
   for (int e = bs.lo * R + tid; e < bs.hi * R; e += nth) p.B0[e] = p.B[e];
   partials_A(p, sm, cta, sm.chunk, false);
-  partials_B<OWN>(p, sm, cta, true, false);
+  partials_B<OWN>(p, sm, cta, true, false, p.ridge_ff_all || p.K == 1);
   __syncthreads();
   if (tid == 0) p.status[1 + cta] = sm.misc[1];
   if (cta == 0 && tid == 0) {
@@ -573,60 +659,76 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
     orow[o] = e / R;
     ocol[o] = e - orow[o] * R;
   }
-  // Gram of the masked rank-one DFTs (all R x R entries) and the right-hand side;
-  // two accumulators per output (even / odd m)
-  float2 g0[OWN], g1[OWN], h0 = make_float2(0.f, 0.f), h1 = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int o = 0; o < OWN; ++o) g0[o] = g1[o] = make_float2(0.f, 0.f);
-  float2* MBs = sm.GJb;   // B^H B staged for the Gram (GJb is free until the solve)
-  for (int e = tid; e < RR; e += nth) MBs[e] = p.MB[e];
-  for (int m0 = 0; m0 < s; m0 += MC) {
-    const int mc = min(MC, s - m0);
-    for (int e = tid; e < mc * R; e += nth) {
-      AH[e] = AhS[m0 * R + e];
-      PC[e] = p.P[m0 * R + e];
-    }
-    __syncthreads();
-    int ir[OWN], ic[OWN];
-#pragma unroll
-    for (int o = 0; o < OWN; ++o) {
-      const bool v = tid + o * nth < RR;
-      ir[o] = v ? orow[o] : 0;
-      ic[o] = v ? ocol[o] : 0;
-    }
-    int mm = 0;
-    for (; mm + 1 < mc; mm += 2) {
-#pragma unroll
-      for (int o = 0; o < OWN; ++o) {
-        cfmac(g0[o], AH[mm * R + ir[o]], AH[mm * R + ic[o]]);
-        cfmac(g1[o], AH[(mm + 1) * R + ir[o]], AH[(mm + 1) * R + ic[o]]);
+  // The ridge system (S1) in float-float: G = (Ahat_S^H Ahat_S) .* (B^H B) + mu I, the Gram of
+  // the masked DFTs of the rank-one images (separable form), from the reduced float-float
+  // sums; h = sum_m conj(Ahat_S[m][r]) P[m][r] = (Phi^H y)_r with P = hi + lo.
+  float2* Glo = sm.GJb;   // low parts of G (GJb holds B^H B again after the solve)
+  float2* hlo = sm.tmpv;
+  {
+    const float mu_hi = (float)p.mu, mu_lo = (float)(p.mu - (double)mu_hi);
+    for (int e = tid; e < RR; e += nth) {
+      const float2 ah = p.MA[e], al = p.MAlo[e], bh = p.MB[e], bl = p.MBlo[e];
+      // (ah + al)(bh + bl): ah bh exactly, ah bl + al bh rounded
+      float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+      ff_acc2(rh, rl, ah.x, bh.x, -ah.y, bh.y);
+      ff_acc2(ih, il, ah.x, bh.y, ah.y, bh.x);
+      const float2 c1 = cmul(ah, bl), c2 = cmul(al, bh);
+      float t, u;
+      two_sum(rh, c1.x + c2.x, t, u);
+      rh = t;
+      rl = rl + u;
+      two_sum(ih, c1.y + c2.y, t, u);
+      ih = t;
+      il = il + u;
+      const int q = e / R, r = e - q * R;
+      if (q == r) {
+        ff_add_ff(rh, rl, mu_hi, mu_lo);
+        ih = il = 0.f;
       }
-      if (tid < R) {
-        cfmac(h0, AH[mm * R + tid], PC[mm * R + tid]);
-        cfmac(h1, AH[(mm + 1) * R + tid], PC[(mm + 1) * R + tid]);
-      }
-    }
-    if (mm < mc) {
-#pragma unroll
-      for (int o = 0; o < OWN; ++o) cfmac(g0[o], AH[mm * R + ir[o]], AH[mm * R + ic[o]]);
-      if (tid < R) cfmac(h0, AH[mm * R + tid], PC[mm * R + tid]);
-    }
-    __syncthreads();
-  }
-  const float fmu = (float)p.mu;
-#pragma unroll
-  for (int o = 0; o < OWN; ++o) {
-    const int e = tid + o * nth;
-    if (e < RR) {
-      float2 v = cmul(cadd(g0[o], g1[o]), MBs[e]);
-      if (orow[o] == ocol[o]) v = make_float2(v.x + fmu, 0.f);
-      sm.Gf[e] = v;
+      two_sum(rh, rl, rh, rl);
+      two_sum(ih, il, ih, il);
+      sm.Gf[e] = make_float2(rh, ih);
+      Glo[e] = make_float2(rl, il);
     }
   }
-  if (tid < R) sm.h[tid] = cadd(h0, h1);
+  {
+    // T threads per output r (T a power of two dividing 32), m strided over them
+    int T = 32;
+    while (T * R > nth) T >>= 1;
+    const int r = tid / T, u = tid - r * T;
+    const bool valid = r < R;
+    CFF hacc = cff_zero();
+    float2* QL = QC;   // low parts of P, staged
+    for (int m0 = 0; m0 < s; m0 += MC) {
+      const int mc = min(MC, s - m0);
+      for (int e = tid; e < mc * R; e += nth) {
+        AH[e] = AhS[m0 * R + e];
+        PC[e] = p.P[m0 * R + e];
+        QL[e] = p.Plo[m0 * R + e];
+      }
+      __syncthreads();
+      if (valid)
+        for (int mm = u; mm < mc; mm += T) cff_macc_ff(hacc, AH[mm * R + r], PC[mm * R + r], QL[mm * R + r]);
+      if (m0 + MC < s) __syncthreads();
+    }
+    for (int o = T >> 1; o > 0; o >>= 1) {
+      const float a = __shfl_xor_sync(0xffffffffu, hacc.rh, o), b = __shfl_xor_sync(0xffffffffu, hacc.rl, o);
+      const float c = __shfl_xor_sync(0xffffffffu, hacc.ih, o), d = __shfl_xor_sync(0xffffffffu, hacc.il, o);
+      ff_add_ff(hacc.rh, hacc.rl, a, b);
+      ff_add_ff(hacc.ih, hacc.il, c, d);
+    }
+    if (valid && u == 0) {
+      const float4 v = cff_pack(hacc);
+      sm.h[r] = make_float2(v.x, v.y);
+      hlo[r] = make_float2(v.z, v.w);
+    }
+  }
   __syncthreads();
-  ridge_solve<OWN>(sm, R, nullptr, nullptr, p.refine, 1e-20f);
-  // B^H B again in shared memory (the solve overwrote GJb)
+  const bool ffk = p.ridge_ff_all || k == p.K - 1;   // readout sums of this system in float-float
+  // stop once the corrections fall below the accuracy of the system: ~1e-13 relative for the
+  // float-float sums, ~1e-6 for FP32 readout sums
+  ridge_solve(sm, R, Glo, hlo, p.refine, ffk ? 1e-26f : 1e-12f);
+  // B^H B (hi) in shared memory for the factor step, over the solve's low parts
   float2* MBt = sm.GJb;
   for (int e = tid; e < RR; e += nth) MBt[e] = p.MB[e];
   __syncthreads();
@@ -652,7 +754,7 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
 #pragma unroll
   for (int o = 0; o < OWN; ++o) t0[o] = t1[o] = make_float2(0.f, 0.f);
   const int NO = na * R;
-  const bool one_chunk = s <= MC;   // AH and PC still hold the whole of Ahat_S and P
+  const bool one_chunk = s <= MC;   // AH and PC still hold the whole of Ahat_S and P (staged for h)
   for (int m0 = 0; m0 < s; m0 += MC) {
     const int mc = min(MC, s - m0);
     if (!one_chunk)
@@ -728,27 +830,66 @@ __device__ __forceinline__ float2 sum_partials(const float2* src, size_t stride,
   return acc;
 }
 
-// reduce the per-CTA partials of Ahat'_S and ||a'||^2 (this CTA's slice of the entries)
-__device__ void step_reduce_A(const FrameParams& p, SM& sm, int cta, int k) {
-  const int R = p.R, C = p.C, Nx = p.Nx;
+// Reduce the per-CTA partials of Ahat_S by rows: this CTA sums the rows m of its slice of
+// [0, |S|) (all R columns) into AhS[dst]; with ma, it then accumulates (Ahat_S^H Ahat_S) over
+// those rows in float-float (upper triangle, mirrored) into its float4 partial partMA[cta],
+// so that the Gram's other factor needs only one more cross-CTA reduction. It also reduces
+// ||a_r||^2 for r in its slice of [0, R) into nA[dst].
+__device__ void reduce_A_rows(const FrameParams& p, SM& sm, int cta, int dst, bool ma) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int R = p.R, C = p.C, Nx = p.Nx, RR = R * R;
   const int s = sm.misc[0];
-  const int E = s * R + R;
-  const Slice es = slice_of(E, C, cta);
-  float2* out = p.AhS[(k + 1) & 1];
-  float* nout = p.nA[(k + 1) & 1];
-  for (int e = es.lo + threadIdx.x; e < es.hi; e += blockDim.x) {
-    if (e < s * R) {
-      out[e] = sum_partials(p.partA + e, (size_t)Nx * R, C);
-    } else {
-      const int r = e - s * R;
-      float acc = 0.f;
-      for (int c = 0; c < C; c += 4) {
-        float v[4];
+  const Slice rs = slice_of(R, C, cta);
+  for (int r = rs.lo + tid; r < rs.hi; r += nth) {
+    float acc = 0.f;
+    for (int c = 0; c < C; c += 4) {
+      float v[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = c + u < C ? p.partNA[(c + u) * R + r] : 0.f;
-        acc += (v[0] + v[1]) + (v[2] + v[3]);
+      for (int u = 0; u < 4; ++u) v[u] = c + u < C ? p.partNA[(c + u) * R + r] : 0.f;
+      acc += (v[0] + v[1]) + (v[2] + v[3]);
+    }
+    p.nA[dst][r] = acc;
+  }
+  const Slice ms = slice_of(s, C, cta);
+  float2* out = p.AhS[dst];
+  float2* rowbuf = sm.chunk;
+  const int cap = max(1, min(ms.hi - ms.lo, p.lay.chunk_f2 / R));
+  const int RT = R * (R + 1) / 2;
+  constexpr int NI = (TTS_MAX_R * (TTS_MAX_R + 1) / 2 + TTS_THREADS - 1) / TTS_THREADS;
+  CFF acc[NI];
+#pragma unroll
+  for (int u = 0; u < NI; ++u) acc[u] = cff_zero();
+  for (int m0 = ms.lo; m0 < ms.hi; m0 += cap) {
+    const int mc = min(cap, ms.hi - m0);
+    for (int e = tid; e < mc * R; e += nth) {
+      const float2 v = sum_partials(p.partA + (size_t)m0 * R + e, (size_t)Nx * R, C);
+      out[(size_t)m0 * R + e] = v;
+      if (ma) rowbuf[e] = v;
+    }
+    if (!ma) continue;
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < NI; ++u) {
+      const int idx = tid + u * nth;
+      if (idx < RT) {
+        int q, r;
+        tri_pair(idx, R, q, r);
+        for (int mm = 0; mm < mc; ++mm) cff_macc(acc[u], rowbuf[mm * R + q], rowbuf[mm * R + r]);
       }
-      nout[r] = acc;
+    }
+    __syncthreads();
+  }
+  if (!ma) return;
+  float4* pma = p.partMA + (size_t)cta * RR;
+#pragma unroll
+  for (int u = 0; u < NI; ++u) {
+    const int idx = tid + u * nth;
+    if (idx < RT) {
+      int q, r;
+      tri_pair(idx, R, q, r);
+      const float4 v = cff_pack(acc[u]);
+      pma[q * R + r] = v;
+      if (q != r) pma[r * R + q] = make_float4(v.x, -v.y, v.z, -v.w);
     }
   }
 }
@@ -862,45 +1003,33 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) 
     return;
   }
   __syncthreads();
-  // partials over this CTA's rows: B'^H B' and Yt conj(B')
-  partials_B<OWN>(p, sm, cta, true, true);
+  // partials over this CTA's rows: B'^H B' and Yt conj(B'), in float-float for the last
+  // MM iteration's ridge system (every iteration's with ridge_ff_all)
+  partials_B<OWN>(p, sm, cta, true, true, p.ridge_ff_all || k + 1 == p.K - 1);
 }
 
-// reduce every partial of the ingest: Ahat_S, ||a||^2, B^H B, P
-__device__ void step_reduce_all(const FrameParams& p, SM& sm, int cta) {
-  const int R = p.R, C = p.C, Nx = p.Nx;
+// Reduce the float-float per-CTA partials of B^H B, P and (with ma) Ahat_S^H Ahat_S, each CTA a
+// slice of the entries, into their hi / lo arrays.
+__device__ void reduce_sums(const FrameParams& p, SM& sm, int cta, bool ma) {
+  const int R = p.R, C = p.C, Nx = p.Nx, RR = R * R;
   const int s = sm.misc[0];
-  const int E1 = s * R, E2 = E1 + R, E3 = E2 + R * R, E = E3 + s * R;
+  const int E1 = RR, E2 = E1 + s * R, E = E2 + (ma ? RR : 0);
   const Slice es = slice_of(E, C, cta);
   for (int e = es.lo + threadIdx.x; e < es.hi; e += blockDim.x) {
+    const float4* src;
+    size_t stride;
+    float2 *hi, *lo;
+    int o;
     if (e < E1) {
-      p.AhS[0][e] = sum_partials(p.partA + e, (size_t)Nx * R, C);
+      src = p.partMB + e, stride = (size_t)RR, hi = p.MB, lo = p.MBlo, o = e;
     } else if (e < E2) {
-      const int r = e - E1;
-      float acc = 0.f;
-      for (int c = 0; c < C; ++c) acc += p.partNA[c * R + r];
-      p.nA[0][r] = acc;
-    } else if (e < E3) {
-      p.MB[e - E2] = sum_partials(p.partMB + (e - E2), (size_t)R * R, C);
+      src = p.partP + (e - E1), stride = (size_t)Nx * R, hi = p.P, lo = p.Plo, o = e - E1;
     } else {
-      p.P[e - E3] = sum_partials(p.partP + (e - E3), (size_t)Nx * R, C);
+      src = p.partMA + (e - E2), stride = (size_t)RR, hi = p.MA, lo = p.MAlo, o = e - E2;
     }
-  }
-}
-
-// reduce the per-CTA partials of B^H B and P
-__device__ void step_reduce_B(const FrameParams& p, SM& sm, int cta) {
-  const int R = p.R, C = p.C, Nx = p.Nx;
-  const int s = sm.misc[0];
-  const int E = R * R + s * R;
-  const Slice es = slice_of(E, C, cta);
-  for (int e = es.lo + threadIdx.x; e < es.hi; e += blockDim.x) {
-    const bool mb = e < R * R;
-    const float2* src = mb ? p.partMB + e : p.partP + (e - R * R);
-    const size_t stride = mb ? (size_t)R * R : (size_t)Nx * R;
-    const float2 acc = sum_partials(src, stride, C);
-    if (mb) p.MB[e] = acc;
-    else p.P[e - R * R] = acc;
+    const float4 v = ff_sum_partials(src, stride, C);
+    hi[o] = make_float2(v.x, v.y);
+    lo[o] = make_float2(v.z, v.w);
   }
 }
 
@@ -964,20 +1093,23 @@ __device__ __forceinline__ void frame_run(const FrameParams& p, unsigned char* s
       continue;
     }
     if (step == 1) {
-      partials_B<OWN>(p, sm, cta, false, true);
+      // Ahat_S of A[t-1] by rows (and its Gram partial); P of B[t-1] over this CTA's rows
+      reduce_A_rows(p, sm, cta, 0, true);
+      __syncthreads();
+      partials_B<OWN>(p, sm, cta, false, true, p.ridge_ff_all || p.K == 1);
       __syncthreads();
       continue;
     }
     if (step == 2) {
-      step_reduce_all(p, sm, cta);
+      reduce_sums(p, sm, cta, true);
       __syncthreads();
       continue;
     }
     const int k = (step - 3) / 4, sub = (step - 3) % 4;
     if (sub == 0) step_solve_A<OWN>(p, sm, cta, k);
-    else if (sub == 1) step_reduce_A(p, sm, cta, k);
+    else if (sub == 1) reduce_A_rows(p, sm, cta, (k + 1) & 1, k + 1 < p.K);
     else if (sub == 2) step_B<OWN>(p, sm, cta, k, k == p.K - 1);
-    else step_reduce_B(p, sm, cta);
+    else reduce_sums(p, sm, cta, true);
     __syncthreads();
   }
 }
@@ -1028,19 +1160,15 @@ __global__ void __launch_bounds__(TTS_THREADS, 1) ridge_kernel(const double2* G,
   SM sm;
   float2* base = (float2*)smem_raw;
   const int RR = R * R;
-  const int Rp = (R + 15) & ~15;
   sm.Gf = base;
   float2* Glo = base + RR;
   sm.GJa = base + 2 * RR;
-  sm.GJb = sm.GJa + Rp * Rp;
-  sm.Pk = sm.GJb + Rp * Rp;
-  sm.Tk = sm.Pk + 256;
-  sm.gam = sm.Tk + 16 * Rp;
+  sm.Pk = sm.GJa + 64 * 72;
+  sm.gam = sm.Pk + 136;
   sm.glo = sm.gam + R;
   sm.h = sm.gam + 2 * R;
   sm.rr = sm.gam + 3 * R;
   float2* hlo = sm.gam + 4 * R;
-  sm.tmpv = sm.gam + 5 * R;   // refinement convergence flag
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
     const double2 g = G[e];
     const float hx = (float)g.x, hy = (float)g.y;
@@ -1054,7 +1182,7 @@ __global__ void __launch_bounds__(TTS_THREADS, 1) ridge_kernel(const double2* G,
     hlo[e] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
   }
   __syncthreads();
-  ridge_solve<TTS_MAX_OWN>(sm, R, Glo, hlo, iters, 1e-28f);
+  ridge_solve(sm, R, Glo, hlo, iters, 1e-28f);
   for (int e = threadIdx.x; e < R; e += blockDim.x)
     gamma[e] = make_double2((double)sm.gam[e].x + (double)sm.glo[e].x, (double)sm.gam[e].y + (double)sm.glo[e].y);
 }
@@ -1062,8 +1190,7 @@ __global__ void __launch_bounds__(TTS_THREADS, 1) ridge_kernel(const double2* G,
 }  // namespace
 
 int launch_ridge(const double2* G, const double2* h, int R, double2* gamma, cudaStream_t st) {
-  const int Rp = (R + 15) & ~15;
-  const int smem = (int)(sizeof(float2) * (2 * R * R + 2 * Rp * Rp + 256 + 16 * Rp + 6 * R));
+  const int smem = (int)(sizeof(float2) * (2 * R * R + 64 * 72 + 136 + 5 * R));
   if (cudaFuncSetAttribute(ridge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return TTS_ECUDA;
   ridge_kernel<<<1, TTS_THREADS, smem, st>>>(G, h, R, 12, gamma);

@@ -355,11 +355,11 @@ __host__ __device__ inline FrameLayout frame_layout(int Nx, int Ny, int R, int r
   L.myA0 = take(f2 * rA * R);
   L.myB = take(f2 * rB * R);
   L.myB0 = take(f2 * rB * R);
-  const int Rp = (R + 15) & ~15;   // ridge system padded to 16 x 16 blocks
+  const int Rq = R <= 32 ? 32 : 64;   // ridge inverse padded to 32 or 64, row stride + 8
   L.Gf = take(f2 * R * R);
-  L.GJa = take(f2 * Rp * Rp);
-  L.GJb = take(f2 * Rp * Rp);
-  L.gjx = take(f2 * (256 + 16 * Rp));
+  L.GJa = take(f2 * Rq * (Rq + 8));
+  L.GJb = take(f2 * R * R);        // low parts of the ridge matrix; B^H B for the factor step
+  L.gjx = take(f2 * 136);
   L.vec = take(f2 * (6 * R + 16));
   L.yb = take(f2 * MC * rB);       // Yt block of this CTA's B rows, kept when |S| <= MC
   const int rmax = rA > rB ? rA : rB;
@@ -376,6 +376,7 @@ struct FrameParams {
   int rA, rB, MC;                 // rows of A / B per CTA, m-chunk length
   int jacobi;
   int refine;                     // refinement sweeps of the ridge solve
+  int ridge_ff_all;               // every MM iteration's readout sums in float-float (else the last one's)
   double lf, mu;
   float isx, isy;                 // 1/sqrt(Nx), 1/sqrt(Ny)
   FrameLayout lay;
@@ -394,12 +395,19 @@ struct FrameParams {
   int* nrows;                     // |S|
   float2* AhS[2];                 // (F_Nx A)[S,:]  (|S| x R), ping-pong over iterations
   float* nA[2];                   // ||a_r||^2
-  float2* MB;                     // B^H B (R x R)
-  float2* P;                      // Yt conj(B) (|S| x R)
+  // The ridge system's sums in float-float: value = hi + lo (the hi array alone is the FP32
+  // value the factor steps use)
+  float2* MB;                     // B^H B (R x R), hi
+  float2* MBlo;                   //   lo
+  float2* P;                      // Yt conj(B) (|S| x R), hi
+  float2* Plo;                    //   lo
+  float2* MA;                     // Ahat_S^H Ahat_S (R x R), hi
+  float2* MAlo;                   //   lo
   float2* partA;                  // [C][Nx][R] partial sums of AhS over row slices
   float* partNA;                  // [C][R]
-  float2* partMB;                 // [C][R][R]
-  float2* partP;                  // [C][Nx][R]
+  float4* partMB;                 // [C][R][R]  float-float partials (hi.x, hi.y, lo.x, lo.y)
+  float4* partP;                  // [C][Nx][R]
+  float4* partMA;                 // [C][R][R]
   double* sc;                     // SC_* (persistent)
   double* sf;                     // SF_* (frame in flight)
   float2* gamma;                  // R
@@ -410,9 +418,10 @@ struct FrameParams {
 };
 
 // Steps of one frame: 0 = ingest (row transforms, anchors, partial sums over the rows of
-// A and of B), 1 = partial sums of P, 2 = reduce all partials; then per MM iteration k:
-// 3 + 4k + {0: ridge solve and A step, 1: reduce the A partials, 2: B step, 3: reduce the
-// B partials}; the last iteration has no step 3.
+// A and of B^H B), 1 = Ahat_S by rows with its Gram partials, partial sums of P, 2 = reduce
+// the float-float sums; then per MM iteration k: 3 + 4k + {0: ridge solve and A step,
+// 1: Ahat'_S by rows with its Gram partials, 2: B step, 3: reduce the float-float sums};
+// the last iteration has no step 3.
 __host__ __device__ inline int frame_num_steps(int K) { return 4 * K + 2; }
 
 // One line-sampler call (probabilities, then the draw) as a job of a batched launch.

@@ -688,3 +688,64 @@ int launch_fft2d(const float2* in, float2* out, int batch, int Nx, int Ny, int i
   }
   return TTS_OK;
 }
+
+// ---------------------------------------------------------------------------------
+// FP32 fused multiply-add throughput of the device, the denominator of the frame kernel's
+// ALU roofline (a calibration; the paper has no counterpart). Every thread runs eight
+// independent chains a <- a b + c (b < 1, so the values stay bounded); the sum of the chains
+// is stored only if it equals -1, which it never does, so no chain is dead code.
+// ---------------------------------------------------------------------------------
+namespace {
+__device__ float g_fma_sink;
+
+__global__ void __launch_bounds__(256) fma_rate_kernel(int iters, float b, float c) {
+  float a[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) a[u] = (float)(threadIdx.x + u) * 1e-3f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = fmaf(a[u], b, c);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = fmaf(a[u], b, c);
+  }
+  const float s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+  if (s == -1.0f) g_fma_sink = s;
+}
+}  // namespace
+
+extern "C" int tts_fp32_fma_rate(int iters, int reps, double* tflops, double* ms) {
+  if (!tflops || iters < 1 || reps < 1) {
+    tts_internal_set_error("tts_fp32_fma_rate: NULL output or non-positive iters / reps");
+    return TTS_EINVAL;
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fma_rate_kernel, 256, 0) != cudaSuccess || per_sm < 1) {
+    tts_internal_set_error("tts_fp32_fma_rate: no device");
+    return TTS_ECUDA;
+  }
+  const int grid = sms * per_sm;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TTS_ECUDA;
+  float best = 0.f;
+  int rc = TTS_OK;
+  for (int r = 0; r <= reps && rc == TTS_OK; ++r) {   // the first launch is a warm-up
+    cudaEventRecord(e0, 0);
+    fma_rate_kernel<<<grid, 256>>>(iters, 0.99999f, 1e-5f);
+    cudaEventRecord(e1, 0);
+    float t = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) rc = TTS_ECUDA;
+    if (r > 0 && (best == 0.f || t < best)) best = t;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != TTS_OK || best <= 0.f) {
+    tts_internal_set_error("tts_fp32_fma_rate: kernel failed");
+    return TTS_ECUDA;
+  }
+  const double flops = 2.0 * 16.0 * (double)iters * (double)grid * 256.0;
+  *tflops = flops / (best * 1e-3) / 1e12;
+  if (ms) *ms = best;
+  return TTS_OK;
+}

@@ -29,9 +29,11 @@ size_t scratch_bytes(int Nx, int Ny, int R, int C) {
   b += up(sizeof(float2) * (size_t)Nx * Ny);                              // Yt
   b += up(sizeof(int) * Nx) + up(sizeof(int) * 4);                        // rows, |S|
   b += 2 * up(sizeof(float2) * Nx * R) + 2 * up(sizeof(float) * R);       // AhS, nA
-  b += up(sizeof(float2) * R * R) + up(sizeof(float2) * Nx * R);          // MB, P
+  b += 2 * (up(sizeof(float2) * R * R) + up(sizeof(float2) * Nx * R));    // MB, P (hi, lo)
+  b += 2 * up(sizeof(float2) * R * R);                                     // MA (hi, lo)
   b += up(sizeof(float2) * (size_t)C * Nx * R) + up(sizeof(float) * C * R);  // partials of A
-  b += up(sizeof(float2) * (size_t)C * R * R) + up(sizeof(float2) * (size_t)C * Nx * R);  // partials of B
+  b += up(sizeof(float4) * (size_t)C * R * R) + up(sizeof(float4) * (size_t)C * Nx * R);  // partials of B
+  b += up(sizeof(float4) * (size_t)C * R * R);                             // partials of MA
   b += up(sizeof(double) * SF_COUNT) + up(sizeof(double2) * R);           // frame scalars, gamma (FP64)
   b += up(sizeof(int) * (1 + TTS_MAX_CLUSTER));                           // status words
   return b;
@@ -120,7 +122,8 @@ extern "C" int tts_push_frame_noalloc(const tts_frame_args* a, void* cuda_stream
   if (scratch_bytes(Nx, Ny, R, p.C) > sizeof(g_noalloc_scratch))
     return na_fail(TTS_EINVAL, "tts_push_frame_noalloc: problem exceeds the fixed scratch");
   p.K = a->mm_iters;
-  p.refine = 4;
+  p.refine = 5;
+  p.ridge_ff_all = 1;
   p.jacobi = a->update == TTS_UPDATE_JACOBI;
   p.lf = a->lambda_forget;
   p.mu = a->mu;
@@ -159,10 +162,15 @@ extern "C" int tts_push_frame_noalloc(const tts_frame_args* a, void* cuda_stream
   p.nA[1] = (float*)take(sizeof(float) * R);
   p.MB = (float2*)take(sizeof(float2) * R * R);
   p.P = (float2*)take(sizeof(float2) * Nx * R);
+  p.MBlo = (float2*)take(sizeof(float2) * R * R);
+  p.Plo = (float2*)take(sizeof(float2) * Nx * R);
+  p.MA = (float2*)take(sizeof(float2) * R * R);
+  p.MAlo = (float2*)take(sizeof(float2) * R * R);
   p.partA = (float2*)take(sizeof(float2) * (size_t)p.C * Nx * R);
   p.partNA = (float*)take(sizeof(float) * p.C * R);
-  p.partMB = (float2*)take(sizeof(float2) * (size_t)p.C * R * R);
-  p.partP = (float2*)take(sizeof(float2) * (size_t)p.C * Nx * R);
+  p.partMB = (float4*)take(sizeof(float4) * (size_t)p.C * R * R);
+  p.partP = (float4*)take(sizeof(float4) * (size_t)p.C * Nx * R);
+  p.partMA = (float4*)take(sizeof(float4) * (size_t)p.C * R * R);
   p.sf = (double*)take(sizeof(double) * SF_COUNT);
   p.gamma_d = (double2*)take(sizeof(double2) * R);
   p.status = (int*)take(sizeof(int) * (1 + TTS_MAX_CLUSTER));

@@ -27,15 +27,18 @@ TTS_FULL_FRAME = 2
 TTS_POLICY_UNIFORM, TTS_POLICY_VARDENS, TTS_POLICY_INFORMATIVE = 0, 1, 2
 TTS_UPDATE_GAUSS_SEIDEL, TTS_UPDATE_JACOBI = 0, 1
 TTS_LAUNCH_FUSED, TTS_LAUNCH_PHASES = 0, 1
+TTS_RIDGE_FF_ALL, TTS_RIDGE_FF_LAST = 0, 1
 
 EXPORTS = [
     "tts_config_init", "tts_create", "tts_create_ex", "tts_destroy", "tts_set_factors", "tts_get_factors",
-    "tts_get_stats", "tts_set_stats", "tts_get_gamma", "tts_get_config", "tts_push_frame", "tts_image", "tts_next_mask",
+    "tts_get_stats", "tts_set_stats", "tts_get_gamma", "tts_get_gamma_fp64", "tts_get_ridge_operands",
+    "tts_get_config", "tts_push_frame", "tts_image", "tts_next_mask",
     "tts_line_probs", "tts_sample_lines_from_probs", "tts_save", "tts_load", "tts_synchronize",
     "tts_launches_per_frame", "tts_ridge_solve", "tts_fft2d", "tts_push_frame_noalloc",
     "tts_stream_footprint", "tts_engine_create", "tts_engine_destroy", "tts_engine_admit", "tts_engine_release",
     "tts_engine_handle", "tts_engine_step", "tts_engine_image", "tts_engine_mask", "tts_engine_synchronize",
-    "tts_engine_info", "tts_engine_autotune", "tts_dft2d_gemm", "tts_set_coil_maps", "tts_last_error",
+    "tts_engine_info", "tts_engine_autotune", "tts_dft2d_gemm", "tts_set_coil_maps", "tts_fp32_fma_rate",
+    "tts_last_error",
 ]
 
 
@@ -53,7 +56,7 @@ class tts_config(ctypes.Structure):
         ("vd_alpha", ctypes.c_double), ("with_replacement", ctypes.c_int), ("update", ctypes.c_int),
         ("launch", ctypes.c_int), ("cluster_ctas", ctypes.c_int), ("init_seed", ctypes.c_uint64),
         ("stream_id", ctypes.c_uint32), ("cuda_stream", ctypes.c_void_p), ("row_dft", ctypes.c_int),
-        ("kspace", ctypes.c_int),
+        ("kspace", ctypes.c_int), ("ridge_precision", ctypes.c_int),
     ]
 
 
@@ -101,6 +104,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
                               ctypes.POINTER(ctypes.c_int64)]),
         "tts_set_stats": (I, [H, D, D, D, ctypes.c_int64]),
         "tts_get_gamma": (I, [H, P]),
+        "tts_get_gamma_fp64": (I, [H, P]),
+        "tts_get_ridge_operands": (I, [H, P, P, P, ctypes.POINTER(I)]),
         "tts_get_config": (I, [H, ctypes.POINTER(tts_config)]),
         "tts_push_frame": (I, [H, P, P, I]),
         "tts_image": (I, [H, ctypes.c_int64, P, I]),
@@ -128,6 +133,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "tts_engine_synchronize": (I, [H]),
         "tts_engine_info": (I, [H, ctypes.POINTER(tts_engine_stats)]),
         "tts_engine_autotune": (I, [ctypes.POINTER(tts_config), I, I, ctypes.POINTER(I), P]),
+        "tts_fp32_fma_rate": (I, [I, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "tts_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -230,6 +236,23 @@ def tts_get_gamma(h, R) -> np.ndarray:
     g = np.zeros(R, np.complex64)
     _check(load().tts_get_gamma(h, g.ctypes.data))
     return g
+
+
+def tts_get_gamma_fp64(h, R) -> np.ndarray:
+    g = np.zeros(2 * R, np.float64)
+    _check(load().tts_get_gamma_fp64(h, g.ctypes.data))
+    return g[0::2] + 1j * g[1::2]
+
+
+def tts_get_ridge_operands(h, Nx, Ny, R):
+    """(Ahat_S, Yt, rows) of the most recent frame's first ridge step (test hook)."""
+    A = np.zeros((Nx, R), np.complex64)
+    Y = np.zeros((Nx, Ny), np.complex64)
+    rows = np.zeros(Nx, np.int32)
+    n = ctypes.c_int(0)
+    _check(load().tts_get_ridge_operands(h, A.ctypes.data, Y.ctypes.data, rows.ctypes.data, ctypes.byref(n)))
+    s = n.value
+    return A[:s].copy(), Y[:s].copy(), rows[:s].copy()
 
 
 def tts_get_config(h) -> tts_config:
@@ -368,6 +391,13 @@ def tts_push_frame_noalloc(A, B, stats, gamma, y_rows, line_mask, lambda_forget,
     else:
         s = stream if isinstance(stream, int) else stream.cuda_stream
     _check(load().tts_push_frame_noalloc(ctypes.byref(args), s))
+
+
+def tts_fp32_fma_rate(iters=200000, reps=3) -> tuple[float, float]:
+    """(TFLOP/s, best ms) of the device's FP32 FMA throughput (calibration kernel)."""
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().tts_fp32_fma_rate(iters, reps, ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
 
 
 def tts_stream_footprint(cfg: tts_config) -> int:
@@ -563,6 +593,12 @@ class Tracker:
 
     def gamma(self):
         return tts_get_gamma(self.h, self.R)
+
+    def gamma_fp64(self):
+        return tts_get_gamma_fp64(self.h, self.R)
+
+    def ridge_operands(self):
+        return tts_get_ridge_operands(self.h, self.Nx, self.Ny, self.R)
 
     def set_coil_maps(self, maps):
         tts_set_coil_maps(self.h, np.ascontiguousarray(maps, np.complex64) if isinstance(maps, np.ndarray) else maps)

@@ -121,15 +121,17 @@ def _footprint(tts, Nx, Ny, R, C):
 def test_stream_footprint_is_host_arithmetic_and_grows_with_the_cluster():
     """tts_stream_footprint needs no device. It covers the resident state of a stream (A, B,
     their anchors and the three Nx x Ny planes: staged rows, transformed rows, image), and
-    the per-CTA partial sums make it grow by exactly C x (2 Nx R complex + R float + R^2
-    complex) between cluster sizes. A layout that does not fit clusters of the size asked is
+    the per-CTA partial sums make it grow by exactly C x (Nx R complex + Nx R + 2 R^2 float-float
+    complex + R float) between cluster sizes. A layout that does not fit clusters of the size asked is
     refused with TTS_EINVAL; 0 means the engine default (4 CTAs)."""
     from paper_1609_04104_gb300 import tts
     for Nx, Ny, R in [(64, 64, 8), (256, 256, 32), (128, 96, 16), (192, 120, 24)]:
         f = {C: _footprint(tts, Nx, Ny, R, C) for C in (2, 4, 8, 16)}
         assert f[4] == _footprint(tts, Nx, Ny, R, 0)
         assert f[2] >= 8 * (2 * (Nx + Ny) * R + 3 * Nx * Ny)
-        per_cta = 8 * 2 * Nx * R + 4 * R + 8 * R * R
+        # partials: Ahat (complex), P (float-float complex), ||a||^2 (float), B^H B and
+        # Ahat^H Ahat (float-float complex)
+        per_cta = 8 * Nx * R + 16 * Nx * R + 4 * R + 2 * 16 * R * R
         for a, b in [(2, 4), (4, 8), (8, 16)]:
             assert abs((f[b] - f[a]) - (b - a) * per_cta) <= 4 * 256, (Nx, Ny, R, a, b)
     with pytest.raises(tts.TtsError) as e:
