@@ -103,8 +103,13 @@ def parse():
                     help="image error against the ground-truth phantom for informative, variable-density "
                          "and uniform line draws at the same line budget")
     ap.add_argument("--study-frames", type=int, default=200)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the engine (64 uneven streams) and serving (256 preloaded streams) sub-objects "
+                         "of the default line")
     ap.add_argument("--fft-n", type=int, default=256)
     ap.add_argument("--fft-batch", type=int, default=512)
+    ap.add_argument("--tune", action="store_true",
+                    help="with --fft2d: pick the launch shape with tts_fft2d_autotune before timing")
     return ap.parse_args()
 
 
@@ -541,6 +546,12 @@ def run_fft2d(args):
     x = torch.randn((b, n, n), dtype=torch.complex64, device="cuda", generator=g)
     y = torch.empty_like(x)
     st = torch.cuda.current_stream()
+    tuned = None
+    if args.tune:
+        if n in (64, 96, 128, 144, 160, 192, 256, 288, 320, 384):
+            tuned = tts.tts_fft2d_autotune(n, b, reps=3)
+        else:
+            tuned = "no tunable launch shape for this size (row- and column-band launches)"
     for _ in range(max(3, args.warmup)):
         tts.tts_fft2d(x, y, stream=st)
     torch.cuda.synchronize()
@@ -561,7 +572,8 @@ def run_fft2d(args):
         pass
     achieved = algo / t / 1e9
     return {"metric": "batched unitary 2D DFT throughput", "value": b / t, "unit": "images/s",
-            "config": {"workload": f"fft2d_{n}x{n}_batch{b}", "bytes_per_call": algo, "l2": "working set > L2"},
+            "config": {"workload": f"fft2d_{n}x{n}_batch{b}", "bytes_per_call": algo, "l2": "working set > L2",
+                       "autotune": tuned},
             "ms_per_call": t * 1e3, "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                                                  "unit": "GB/s", "frac": achieved / peak,
                                                  "note": "algorithmic bytes 16 N^2 per image; two passes move 32 N^2"}}
@@ -834,6 +846,7 @@ def run_serve(args):
     max_active = 0
     frames_done = 0
     first_last = {}
+    clocks = ClockSampler(torch.cuda.current_device(), enabled=not args.no_clocks)
     t0 = time.perf_counter()
     while waiting or active:
         now = time.perf_counter() - t0
@@ -890,6 +903,7 @@ def run_serve(args):
                 eng.release(active[k][0])
                 del active[k]
     wall = time.perf_counter() - t0
+    clk = clocks.stop()
     info = eng.info()
     eng.close()
 
@@ -929,6 +943,7 @@ def run_serve(args):
                     "admission_waits": refused, "alone_equals_mix_bitwise": same, "checked_streams": len(first_last)},
         "engine": info,
         "gpu_launches": 3 * len(step_sizes),
+        "clocks": clk,
     }
 
 
@@ -1231,6 +1246,34 @@ def run_sampling_study(args):
             "policies": out}
 
 
+def extras(args):
+    """The many-stream forms next to the one-stream line: 64 uneven streams through the
+    engine against the same streams one at a time (frames/s, image agreement, an oracle spot
+    check of sampled streams), and the real-time serving loop with 256 streams preloaded
+    (p50 / p99 frame latency, aggregate frames/s, alone-vs-mix bit identity); each with its
+    own clock record."""
+    import copy
+    b = copy.copy(args)
+    b.batched, b.streams, b.stream_frames, b.cluster, b.autotune = True, 64, 100, 0, False
+    rb = run_batched(b)
+    srv = copy.copy(args)
+    srv.serve, srv.preload, srv.serve_streams, srv.serve_frames, srv.cluster = True, True, 256, 300, 0
+    rs = run_serve(srv)
+    keys_b = ["value", "unit", "ms_per_step", "latency_ms", "plain_path", "speedup_vs_plain", "nrmse_vs_plain_path",
+              "bit_identical_at_same_cluster_size", "e2e", "roofline", "clocks", "gpu_launches"]
+    batched = {"workload": rb["config"]["workload"], **{k: rb.get(k) for k in keys_b},
+               "config": {k: rb["config"][k] for k in ("streams", "T", "sizes", "ranks", "rates", "cluster_ctas_used",
+                                                        "graph", "l2")}}
+    if rb.get("cpu_baseline"):
+        batched["oracle_spot_check"] = {k: v for k, v in rb["cpu_baseline"].items() if k != "value"}
+    serve = {"workload": rs["config"]["workload"], "value": rs["value"], "unit": rs["unit"],
+             "latency_ms": rs["latency_ms"], "serving": rs["serving"], "clocks": rs["clocks"],
+             "config": {k: rs["config"][k] for k in ("streams", "frames_per_stream", "fps_range", "sizes", "ranks",
+                                                      "rate", "cluster_ctas")},
+             "gpu_launches": rs["gpu_launches"]}
+    return batched, serve
+
+
 def main():
     args = parse()
     if args.sampling_study:
@@ -1266,6 +1309,8 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         torch.distributed.init_process_group("nccl")
     out = run_tts(args, rank, world)
+    if world == 1 and not args.no_extras:
+        out["batched"], out["serve"] = extras(args)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

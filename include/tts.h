@@ -432,6 +432,40 @@ int tts_engine_info(tts_engine* e, tts_engine_stats* stats);
  * temporary engines and frames on the current device and frees them before returning. */
 int tts_engine_autotune(const tts_config* cfgs, int n, int steps, int* best_C, double* step_ms);
 
+/* Autotuner of tts_fft2d's launch shape for square N x N images of the band-task sizes
+ * (64, 96, 128, 144, 160, 192, 256, 288, 320, 384): times, on batch zero-filled images in
+ * buffers of its own, the persistent launch at the CTAs per SM that fit and up to two fewer,
+ * each with the row-ahead lag between an image's row and column tasks scaled by 0.5, 1, 1.5, 2
+ * and 3 (one untimed launch, then the best of `reps`), and records the fastest shape for later
+ * tts_fft2d calls of that N and direction on the current device (the library's default shape
+ * until then). Outputs (each may be NULL): the best time per call in ms, its CTAs per SM and
+ * lag scale. Synchronous; allocates and frees its buffers (2 x batch x N^2 complex64). */
+int tts_fft2d_autotune(int N, int batch, int inverse, int reps, double* best_ms, int* per_sm, double* lag);
+
+/* ---- Test hooks for the failure detection of the bounded device waits ----------------
+ * No counterpart in the paper. Kernels that wait on other threads' arrivals (the square
+ * band-task FFT's column tasks on an image's row tasks; the tensor-core DFT's MMA issuer and
+ * producers on each other's mbarrier arrivals) give every wait a limit, after which they
+ * record an error status and return; these hooks withhold one awaited arrival so that a test
+ * can run such a wait out without faulting or hanging the GPU.
+ *
+ * tts_test_withheld_wait: kind 0 runs tts_fft2d's square band-task kernel (batch images of
+ * N x N, N one of its sizes 64..384, forward) with the row tasks of image `index` publishing
+ * nothing; kind 1 runs tts_dft2d_gemm (BF16 hi + lo, N x N, N a multiple of 32 in [32, 256];
+ * tmp as there) with the bulk copy and producer arrival of K' chunk `index` (< 2N / 16) of the
+ * first pass withheld. Every wait of the launch lasts at most wait_cycles SM clocks. The waits
+ * for the withheld arrival run out, the kernel sets *dev_status (a device int the caller
+ * zeroes first) to 1, and the outputs are invalid; the next ordinary call is unaffected.
+ * Device buffers; asynchronous on cuda_stream. */
+int tts_test_withheld_wait(int kind, const tts_c64* in, tts_c64* out, tts_c64* tmp, int batch, int N, int index,
+                           long long wait_cycles, int* dev_status, void* cuda_stream);
+/* The next tts_push_frame of a handle whose row transform runs on the tensor cores (row_dft
+ * != TTS_ROWDFT_FFT) withholds K' chunk `chunk` (< 2 Ny / 16) of that transform, with every
+ * wait limited to wait_cycles SM clocks: the transform gives up, the frame is skipped (the
+ * factors, statistics and gamma keep their values) and tts_synchronize reports TTS_ETIMEOUT.
+ * Later frames run as usual. */
+int tts_test_withhold_row_transform(tts_handle* h, int chunk, long long wait_cycles);
+
 /* Calibration (no counterpart in the paper): the device's FP32 fused multiply-add rate,
  * the denominator of the frame kernel's ALU roofline. A kernel fills every SM (the largest
  * number of 256-thread CTAs that fit) and each thread runs eight independent chains of

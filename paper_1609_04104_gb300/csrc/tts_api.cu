@@ -75,7 +75,7 @@ std::vector<Piece> handle_pieces(tts_handle* h, int Nx, int Ny, int R, int C) {
       {(void**)&p.partMA, sizeof(float4) * C * R * R},
       {(void**)&p.sc, sizeof(double) * SC_COUNT},
       {(void**)&p.sf, sizeof(double) * SF_COUNT},       {(void**)&p.gamma, sizeof(float2) * R},
-      {(void**)&p.gamma_d, sizeof(double2) * R},        {(void**)&p.status, sizeof(int) * (2 + TTS_MAX_CLUSTER)},
+      {(void**)&p.gamma_d, sizeof(double2) * R},        {(void**)&p.status, sizeof(int) * (3 + TTS_MAX_CLUSTER)},
       {(void**)&p.Wx, sizeof(float2) * Nx},             {(void**)&p.Wy, sizeof(float2) * Ny},
       {(void**)&h->X, sizeof(float2) * Nx * Ny},        {(void**)&h->dmask_push, (size_t)Nx},
       {(void**)&h->dmask_next, (size_t)Nx},             {(void**)&h->dp, sizeof(double) * Nx},
@@ -487,10 +487,19 @@ int tts_push_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line_mas
     }
   };
   if (h->cfg.row_dft != TTS_ROWDFT_FFT) {
-    // the acquired rows' transform on the tensor cores, straight into Yt
+    // the acquired rows' transform on the tensor cores, straight into Yt; it reports a wait
+    // that ran out in the frame's own status word, which the frame kernel reads (and then
+    // skips the frame and raises the handle's sticky timeout word)
+    int* frame_tmo = p.status + 2 + TTS_MAX_CLUSTER;
+    const int withhold = h->test_withhold;
+    const long long limit = withhold >= 0 ? h->test_wait_cycles : 2000000000LL;
+    h->test_withhold = -1;
+    if (cudaMemsetAsync(frame_tmo, 0, sizeof(int), h->stream) != cudaSuccess) {
+      release_staging();
+      return fail(TTS_ECUDA, "status reset failed%s");
+    }
     const int rr = launch_row_dft(p.yrows, p.Yt, p.mask, h->cfg.Nx, h->cfg.Ny, p.full_frame,
-                                  h->cfg.row_dft == TTS_ROWDFT_BF16X3 ? 1 : 0, p.status + 1 + TTS_MAX_CLUSTER,
-                                  h->stream);
+                                  h->cfg.row_dft == TTS_ROWDFT_BF16X3 ? 1 : 0, frame_tmo, h->stream, withhold, limit);
     if (rr != TTS_OK) {
       release_staging();
       return fail(rr, "row transform launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -798,6 +807,57 @@ int tts_fft2d(const tts_c64* in, tts_c64* out, int batch, int Nx, int Ny, int in
   return rc == TTS_OK ? TTS_OK : fail(rc, "fft kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
 }
 
+
+int tts_fft2d_autotune(int N, int batch, int inverse, int reps, double* best_ms, int* per_sm, double* lag) {
+  if (!fft2d_square_ok(N, N)) return fail(TTS_EINVAL, "the autotuner covers the square band-task sizes%s");
+  if (batch < 1 || reps < 1) return fail(TTS_EINVAL, "batch and reps must be positive%s");
+  int rc = TTS_OK;
+  const float2* w = device_twiddles(N, &rc);
+  if (!w) return rc;
+  int* st = device_status(&rc);
+  if (!st) return fail(rc, "device status word%s");
+  float2* buf = nullptr;
+  const size_t n = (size_t)batch * N * N;
+  CK(cudaMalloc(&buf, 2 * n * sizeof(float2)));
+  cudaError_t e = cudaMemset(buf, 0, 2 * n * sizeof(float2));
+  if (e == cudaSuccess)
+    rc = tune_fft2d_square(buf, buf + n, batch, N, inverse, w, st, reps, best_ms, per_sm, lag);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune buffers");
+  return rc == TTS_OK ? TTS_OK : fail(rc, "autotune launch failed%s");
+}
+
+int tts_test_withheld_wait(int kind, const tts_c64* in, tts_c64* out, tts_c64* tmp, int batch, int N, int index,
+                           long long wait_cycles, int* dev_status, void* cuda_stream) {
+  if (!in || !out || !dev_status) return fail(TTS_EINVAL, "NULL argument%s");
+  if (batch < 1 || index < 0 || wait_cycles < 1) return fail(TTS_EINVAL, "bad batch, index or wait_cycles%s");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (kind == 0) {
+    if (!fft2d_square_ok(N, N) || index >= batch) return fail(TTS_EINVAL, "kind 0: square band size, index < batch%s");
+    int rc = TTS_OK;
+    const float2* w = device_twiddles(N, &rc);
+    if (!w) return rc;
+    rc = launch_fft2d_square((const float2*)in, (float2*)out, batch, N, 0, w, dev_status, st, index, wait_cycles);
+    return rc == TTS_OK ? TTS_OK : fail(rc, "square FFT launch failed%s");
+  }
+  if (kind == 1) {
+    if (!tmp || !dft_gemm_size_ok(N) || index >= 2 * N / 16) return fail(TTS_EINVAL, "kind 1: N, tmp, chunk index%s");
+    if (((uintptr_t)in | (uintptr_t)out | (uintptr_t)tmp) % 16 != 0) return fail(TTS_EINVAL, "16-byte alignment%s");
+    const int rc = launch_dft2d_gemm((const float2*)in, (float2*)out, (float2*)tmp, batch, N, N, 0, 1, dev_status, st,
+                                     index, wait_cycles);
+    return rc == TTS_OK ? TTS_OK : fail(rc, "tensor-core DFT launch failed%s");
+  }
+  return fail(TTS_EINVAL, "kind must be 0 or 1%s");
+}
+
+int tts_test_withhold_row_transform(tts_handle* h, int chunk, long long wait_cycles) {
+  if (!h) return fail(TTS_EINVAL, "NULL handle%s");
+  if (h->cfg.row_dft == TTS_ROWDFT_FFT) return fail(TTS_EINVAL, "the handle has no tensor-core row transform%s");
+  if (chunk < 0 || chunk >= 2 * h->cfg.Ny / 16 || wait_cycles < 1) return fail(TTS_EINVAL, "bad chunk or wait_cycles%s");
+  h->test_withhold = chunk;
+  h->test_wait_cycles = wait_cycles;
+  return TTS_OK;
+}
 
 int tts_dft2d_gemm(const tts_c64* in, tts_c64* out, tts_c64* tmp, int batch, int Nx, int Ny, int inverse,
                    int precision, int* dev_status, void* cuda_stream) {

@@ -21,11 +21,13 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase with the given parity: gives up after ~1 s of SM clock.
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+// SM clocks a bounded device wait gives an awaited arrival before it gives up (~1 s)
+#define TTS_WAIT_LIMIT 2000000000LL
+// Bounded wait for the phase with the given parity: gives up after `limit` SM clocks.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, long long limit = TTS_WAIT_LIMIT) {
   const long long t0 = clock64();
   while (!mbar_try(a, parity))
-    if (clock64() - t0 > 2000000000LL) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 // bytes (a multiple of 16, both addresses 16-byte aligned) from global to this CTA's shared

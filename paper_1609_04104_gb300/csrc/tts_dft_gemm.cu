@@ -95,6 +95,8 @@ struct GemmArgs {
   int nh;                 // accumulators (1, or 2 when 2N > 256)
   int split;              // 1: hi*hi + hi*lo + lo*hi; 0: hi*hi
   int* err;               // set to 1 when a wait ran out
+  long long limit;        // SM clocks a bounded wait lasts (TTS_WAIT_LIMIT)
+  int withhold;           // test hook: K' chunk whose copy and arrival are withheld (-1: none)
   // row mode (the acquired rows of one k-space frame): when mask is set, the rows are the
   // lines i with mask[i] != 0 (M = their number, one row per "image", so the output is
   // row-major); with full_frame, row m is x row S[m], else x row m
@@ -177,11 +179,15 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm_kernel(GemmArgs g) {
     unsigned char* alo = st + a_bytes();
     unsigned char* bhi = st + 2 * a_bytes();
     unsigned char* blo = bhi + b_bytes(N);
+    int last = -1;   // the last use of the stage whose copy was issued
     for (int kc = s, use = 0; kc < nK; kc += kStages, ++use) {
-      if (use > 0 && (*abort_v || !mbar_wait(empty0 + 8 * s, (use - 1) & 1))) {
+      if (use > 0 && (*abort_v || !mbar_wait(empty0 + 8 * s, (use - 1) & 1, g.limit))) {
         abort_flag = 1;
         break;
       }
+      // test hook: this chunk's arrivals never come, so the wait for it runs out
+      if (kc == g.withhold) break;
+      last = use;
       if (lane == 0) {
         mbar_expect_tx(full0 + 8 * s, g.split ? 2 * bchunk : bchunk);
         bulk_g2s(smem_u32(bhi), (const char*)g.bhi + (size_t)kc * bchunk, bchunk, full0 + 8 * s);
@@ -222,11 +228,14 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm_kernel(GemmArgs g) {
       __syncwarp();
       if (lane == 0) mbar_arrive(full0 + 8 * s);
     }
+    // the stage's last copy has landed before the CTA moves on (already so unless a wait ran
+    // out: that phase then completes with the copy, the warp's own arrival being in)
+    if (lane == 0 && last >= 0 && !mbar_wait(full0 + 8 * s, last & 1, g.limit)) abort_flag = 1;
   } else if (warp == kIssuer) {
     if (lane == 0) {
       for (int kc = 0; kc < nK; ++kc) {
         const int s = kc % kStages, use = kc / kStages;
-        if (*abort_v || !mbar_wait(full0 + 8 * s, use & 1)) {
+        if (*abort_v || !mbar_wait(full0 + 8 * s, use & 1, g.limit)) {
           abort_flag = 1;
           break;
         }
@@ -253,7 +262,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm_kernel(GemmArgs g) {
     }
     __syncwarp();
   }
-  const bool fin = mbar_wait(done, 0);
+  const bool fin = mbar_wait(done, 0, g.limit);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncthreads();
   if (abort_flag || !fin) {
@@ -378,7 +387,7 @@ int launch_args(GemmArgs& a, int inverse, int grid, cudaStream_t st) {
 }
 
 int launch_pass(const float2* x, float2* out, int batch, int rows, int N, int inverse, int split, int* err,
-                cudaStream_t st) {
+                cudaStream_t st, int withhold = -1, long long limit = TTS_WAIT_LIMIT) {
   const uint4 *hi = nullptr, *lo = nullptr;
   int rc = embedding(N, inverse, &hi, &lo);
   if (rc != TTS_OK) return rc;
@@ -396,6 +405,8 @@ int launch_pass(const float2* x, float2* out, int batch, int rows, int N, int in
   a.mask = nullptr;
   a.mask_n = 0;
   a.full_frame = 0;
+  a.limit = limit;
+  a.withhold = withhold;
   // TMEM holds 512 columns per SM: ask for enough shared memory that the CTAs resident on
   // one SM never need more (two CTAs of 256 columns, or one of 512), so an allocation never
   // waits on a CTA that cannot finish
@@ -414,7 +425,7 @@ int launch_pass(const float2* x, float2* out, int batch, int rows, int N, int in
 bool dft_gemm_size_ok(int N) { return N >= 32 && N <= 256 && N % 32 == 0; }
 
 int launch_row_dft(const float2* y, float2* yt, const uint8_t* mask, int Nx, int Ny, int full_frame, int split,
-                   int* err, cudaStream_t st) {
+                   int* err, cudaStream_t st, int withhold, long long limit) {
   GemmArgs a;
   a.x = y;
   a.out = yt;
@@ -426,14 +437,16 @@ int launch_row_dft(const float2* y, float2* yt, const uint8_t* mask, int Nx, int
   a.mask = mask;
   a.mask_n = Nx;
   a.full_frame = full_frame;
+  a.limit = limit;
+  a.withhold = withhold;
   return launch_args(a, 1, (Nx + kRows - 1) / kRows, st);
 }
 
 int launch_dft2d_gemm(const float2* in, float2* out, float2* tmp, int batch, int Nx, int Ny, int inverse,
-                      int split, int* err, cudaStream_t st) {
+                      int split, int* err, cudaStream_t st, int withhold, long long limit) {
   // rows of each image (length Ny) -> tmp holds the transposes (Ny x Nx); then the rows of
   // the transposes (length Nx) -> out holds F_Nx X F_Ny (Nx x Ny)
-  int rc = launch_pass(in, tmp, batch, Nx, Ny, inverse, split, err, st);
+  int rc = launch_pass(in, tmp, batch, Nx, Ny, inverse, split, err, st, withhold, limit);
   if (rc == TTS_OK) rc = launch_pass(tmp, out, batch, Ny, Nx, inverse, split, err, st);
   return rc;
 }

@@ -74,7 +74,7 @@ constexpr int square_minb() {
 template <int N, bool INV>
 __global__ void __launch_bounds__(Shape<N>::NT, square_minb<N>())
     fft2d_square_kernel(const float2* in, float2* out, int batch, int L, const float2* __restrict__ Wg, float scale,
-                        int* ctrl, int* err) {
+                        int* ctrl, int* err, int withhold, long long limit) {
   constexpr int BAND = Shape<N>::BAND, NT = Shape<N>::NT, NB = N / BAND;
   static_assert(BAND * Shape<N>::T == NT && N % BAND == 0, "one line of the band per thread");
   extern __shared__ __align__(16) unsigned char smem[];
@@ -96,7 +96,9 @@ __global__ void __launch_bounds__(Shape<N>::NT, square_minb<N>())
     const int q = s_task[it & 1];
     if (tid == 0) {
       if (pub >= 0) {
-        red_release_add(done + pub, 1);   // cumulative over the CTA's stores (the barrier before)
+        // cumulative over the CTA's stores (the barrier before); the test hook withholds
+        // the publication of one image, so that its column tasks' waits run out
+        if (pub != withhold) red_release_add(done + pub, 1);
         pub = -1;
       }
       if (q < total) nq = atomicAdd(next, 1);
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(Shape<N>::NT, square_minb<N>())
       if (tid == 0) {   // acquire the NB row tasks of the image
         const long long t0 = clock64();
         while (ld_acquire(done + img) < NB) {
-          if (clock64() - t0 > 2000000000LL) {
+          if (clock64() - t0 > limit) {
             atomicOr(err, 1);
             break;
           }
@@ -154,9 +156,44 @@ cudaMemPool_t ctrl_pool() {
   return pools[dev];
 }
 
+// Launch shape of the square kernel per (device, N, direction): CTAs per SM of the
+// persistent grid (0: as many as fit) and the multiplier of the row-ahead lag L. The defaults
+// (all that fit, multiplier 1) stand until tts_fft2d_autotune records a measured pick.
+struct SquareShape {
+  int per_sm;
+  float lag;
+};
+std::mutex g_shape_mu;
+SquareShape g_shape[TTS_MAX_DEVICES][2][10];
+
+int size_slot(int N) {
+  switch (N) {
+    case 64: return 0;
+    case 96: return 1;
+    case 128: return 2;
+    case 144: return 3;
+    case 160: return 4;
+    case 192: return 5;
+    case 256: return 6;
+    case 288: return 7;
+    case 320: return 8;
+    case 384: return 9;
+    default: return -1;
+  }
+}
+
+SquareShape square_shape(int N, bool inv) {
+  int dev = 0;
+  const int k = size_slot(N);
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= TTS_MAX_DEVICES || k < 0) return {0, 1.f};
+  std::lock_guard<std::mutex> lk(g_shape_mu);
+  const SquareShape sh = g_shape[dev][inv ? 1 : 0][k];
+  return sh.lag > 0.f ? sh : SquareShape{0, 1.f};
+}
+
+// CTAs of the kernel that fit on one SM (*fit) and the SM count, set up once per device
 template <int N, bool INV>
-int launch_t(const float2* in, float2* out, int batch, const float2* W, int* err, cudaStream_t st) {
-  constexpr int NB = N / Shape<N>::BAND;
+int grid_info(int* fit, int* sms_out) {
   constexpr int smem = fftband::smem_bytes<N>();
   static PerDevice grids;
   int grid = 0;
@@ -170,31 +207,87 @@ int launch_t(const float2* in, float2* out, int batch, const float2* W, int* err
                                                                      Shape<N>::NT, smem) != cudaSuccess ||
                        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1)
                      return TTS_ECUDA;
-                   *v = per_sm * sms;
+                   *v = per_sm * 1000 + sms;
                    return TTS_OK;
                  },
                  &grid) != TTS_OK)
     return TTS_ECUDA;
+  *fit = grid / 1000;
+  *sms_out = grid % 1000;
+  return TTS_OK;
+}
+
+template <int N, bool INV>
+int launch_t(const float2* in, float2* out, int batch, const float2* W, int* err, cudaStream_t st, int withhold,
+             long long limit, SquareShape shape) {
+  constexpr int NB = N / Shape<N>::BAND;
+  constexpr int smem = fftband::smem_bytes<N>();
+  int fit = 0, sms = 0;
+  if (grid_info<N, INV>(&fit, &sms) != TTS_OK) return TTS_ECUDA;
+  const int per_sm = shape.per_sm > 0 ? std::min(shape.per_sm, fit) : fit;
   const int tasks = 2 * NB * batch;
-  const int g = std::min(grid, tasks);
-  // lag between an image's row and column tasks: the 2 NB L tasks in between are about three
-  // times the tasks in flight (measured at 256^2: half of it, 62 % of HBM; this, 66 %; twice
-  // it, 63 %)
-  const int L = std::max(1, (3 * g) / (2 * NB) + 1);
+  const int g = std::min(per_sm * sms, tasks);
+  // lag between an image's row and column tasks: by default the 2 NB L tasks in between are
+  // about three times the tasks in flight (measured at 256^2: half of it, 62 % of HBM; this,
+  // 66 %; twice it, 63 %); the autotuner may scale it
+  const int L = std::max(1, (int)(shape.lag * (float)((3 * g) / (2 * NB))) + 1);
   int* ctrl = nullptr;
   const size_t cb = sizeof(int) * (1 + (size_t)batch);
   cudaMemPool_t pool = ctrl_pool();
   if (!pool || cudaMallocFromPoolAsync((void**)&ctrl, cb, pool, st) != cudaSuccess) return TTS_ECUDA;
   if (cudaMemsetAsync(ctrl, 0, cb, st) != cudaSuccess) return TTS_ECUDA;
-  fft2d_square_kernel<N, INV><<<g, Shape<N>::NT, smem, st>>>(in, out, batch, L, W, 1.0f / (float)N, ctrl, err);
+  fft2d_square_kernel<N, INV><<<g, Shape<N>::NT, smem, st>>>(in, out, batch, L, W, 1.0f / (float)N, ctrl, err,
+                                                               withhold, limit);
   const cudaError_t e = cudaGetLastError();
   if (cudaFreeAsync(ctrl, st) != cudaSuccess || e != cudaSuccess) return TTS_ECUDA;
   return TTS_OK;
 }
 
 template <int N>
-int launch_n(const float2* in, float2* out, int batch, int inverse, const float2* W, int* err, cudaStream_t st) {
-  return inverse ? launch_t<N, true>(in, out, batch, W, err, st) : launch_t<N, false>(in, out, batch, W, err, st);
+int launch_n(const float2* in, float2* out, int batch, int inverse, const float2* W, int* err, cudaStream_t st,
+             int withhold, long long limit, const SquareShape* forced) {
+  const SquareShape sh = forced ? *forced : square_shape(N, inverse != 0);
+  return inverse ? launch_t<N, true>(in, out, batch, W, err, st, withhold, limit, sh)
+                 : launch_t<N, false>(in, out, batch, W, err, st, withhold, limit, sh);
+}
+
+template <int N>
+int fit_n(int inverse, int* fit) {
+  int sms = 0;
+  return inverse ? grid_info<N, true>(fit, &sms) : grid_info<N, false>(fit, &sms);
+}
+
+int square_fit(int N, int inverse, int* fit) {
+  switch (N) {
+    case 64: return fit_n<64>(inverse, fit);
+    case 96: return fit_n<96>(inverse, fit);
+    case 128: return fit_n<128>(inverse, fit);
+    case 144: return fit_n<144>(inverse, fit);
+    case 160: return fit_n<160>(inverse, fit);
+    case 192: return fit_n<192>(inverse, fit);
+    case 256: return fit_n<256>(inverse, fit);
+    case 288: return fit_n<288>(inverse, fit);
+    case 320: return fit_n<320>(inverse, fit);
+    case 384: return fit_n<384>(inverse, fit);
+    default: return TTS_EINVAL;
+  }
+}
+
+int launch_any(const float2* in, float2* out, int batch, int N, int inverse, const float2* W, int* err,
+               cudaStream_t st, int withhold, long long limit, const SquareShape* forced) {
+  switch (N) {
+    case 64: return launch_n<64>(in, out, batch, inverse, W, err, st, withhold, limit, forced);
+    case 96: return launch_n<96>(in, out, batch, inverse, W, err, st, withhold, limit, forced);
+    case 128: return launch_n<128>(in, out, batch, inverse, W, err, st, withhold, limit, forced);
+    case 144: return launch_n<144>(in, out, batch, inverse, W, err, st, withhold, limit, forced);
+    case 160: return launch_n<160>(in, out, batch, inverse, W, err, st, withhold, limit, forced);
+    case 192: return launch_n<192>(in, out, batch, inverse, W, err, st, withhold, limit, forced);
+    case 256: return launch_n<256>(in, out, batch, inverse, W, err, st, withhold, limit, forced);
+    case 288: return launch_n<288>(in, out, batch, inverse, W, err, st, withhold, limit, forced);
+    case 320: return launch_n<320>(in, out, batch, inverse, W, err, st, withhold, limit, forced);
+    case 384: return launch_n<384>(in, out, batch, inverse, W, err, st, withhold, limit, forced);
+    default: return TTS_EINVAL;
+  }
 }
 
 }  // namespace
@@ -208,19 +301,56 @@ bool fft2d_square_ok(int Nx, int Ny) {
 }
 
 int launch_fft2d_square(const float2* in, float2* out, int batch, int N, int inverse, const float2* W, int* err,
-                        cudaStream_t st) {
+                        cudaStream_t st, int withhold, long long limit) {
   if (batch <= 0) return TTS_OK;
-  switch (N) {
-    case 64: return launch_n<64>(in, out, batch, inverse, W, err, st);
-    case 96: return launch_n<96>(in, out, batch, inverse, W, err, st);
-    case 128: return launch_n<128>(in, out, batch, inverse, W, err, st);
-    case 144: return launch_n<144>(in, out, batch, inverse, W, err, st);
-    case 160: return launch_n<160>(in, out, batch, inverse, W, err, st);
-    case 192: return launch_n<192>(in, out, batch, inverse, W, err, st);
-    case 256: return launch_n<256>(in, out, batch, inverse, W, err, st);
-    case 288: return launch_n<288>(in, out, batch, inverse, W, err, st);
-    case 320: return launch_n<320>(in, out, batch, inverse, W, err, st);
-    case 384: return launch_n<384>(in, out, batch, inverse, W, err, st);
-    default: return TTS_EINVAL;
+  return launch_any(in, out, batch, N, inverse, W, err, st, withhold, limit, nullptr);
+}
+
+int tune_fft2d_square(const float2* in, float2* out, int batch, int N, int inverse, const float2* W, int* err,
+                      int reps, double* best_ms, int* best_per_sm, double* best_lag) {
+  const int k = size_slot(N);
+  int dev = 0;
+  if (k < 0 || batch < 1 || reps < 1 || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= TTS_MAX_DEVICES)
+    return TTS_EINVAL;
+  int fit = 0;
+  if (square_fit(N, inverse, &fit) != TTS_OK || fit < 1) return TTS_ECUDA;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TTS_ECUDA;
+  const float lags[] = {0.5f, 1.f, 1.5f, 2.f, 3.f};
+  float best = 0.f;
+  SquareShape pick{0, 1.f};
+  int rc = TTS_OK;
+  // candidates: the CTAs per SM that fit and up to two fewer (more registers and cache per
+  // CTA), each with five lags; one untimed launch each, then the best of `reps`
+  for (int per_sm = fit; per_sm >= std::max(1, fit - 2) && rc == TTS_OK; --per_sm)
+    for (float lag : lags) {
+      const SquareShape sh{per_sm, lag};
+      rc = launch_any(in, out, batch, N, inverse, W, err, 0, -1, 2000000000LL, &sh);
+      float t_best = 0.f;
+      for (int r = 0; r < reps && rc == TTS_OK; ++r) {
+        cudaEventRecord(e0, 0);
+        rc = launch_any(in, out, batch, N, inverse, W, err, 0, -1, 2000000000LL, &sh);
+        cudaEventRecord(e1, 0);
+        float t = 0.f;
+        if (rc == TTS_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+          rc = TTS_ECUDA;
+        if (rc == TTS_OK && (t_best == 0.f || t < t_best)) t_best = t;
+      }
+      if (rc != TTS_OK) break;
+      if (best == 0.f || t_best < best) {
+        best = t_best;
+        pick = sh;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != TTS_OK) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    g_shape[dev][inverse ? 1 : 0][k] = pick;
   }
+  if (best_ms) *best_ms = best;
+  if (best_per_sm) *best_per_sm = pick.per_sm;
+  if (best_lag) *best_lag = pick.lag;
+  return TTS_OK;
 }

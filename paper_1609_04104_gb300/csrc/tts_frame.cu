@@ -196,34 +196,39 @@ __device__ __forceinline__ void tri_pair(int idx, int R, int& q, int& r) {
 // kappa(G) u_32, so two sweeps reach the float-float accuracy of the system; the sweeps
 // stop once every correction is below sqrt(tol2) relative.
 // ---------------------------------------------------------------------------------
+// rows of the ridge matrix each warp of the Gauss-Jordan inverse keeps in registers
+#ifndef TTS_GJ_ROWS
+#define TTS_GJ_ROWS 8
+#endif
+
 __device__ __forceinline__ void bar_named(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 // Gauss-Jordan inverse of G (R x R, row stride R; padded with the identity to RP x RP) into
-// Gi (row stride RP + 8) by warps 0 .. RP/8 - 1: warp w keeps rows 8w .. 8w+7 in registers,
-// lane l the columns l + 32q. Each pivot step publishes the scaled pivot row through `prow`
+// Gi (row stride RP + 8) by warps 0 .. RP/RW - 1: warp w keeps rows RW w .. RW w + RW - 1 in
+// registers, lane l the columns l + 32q. Each pivot step publishes the scaled pivot row through `prow`
 // (two slots, 2 RP float2) and the warps meet at named barrier 1; the pivot column comes
 // from the lane that holds it by shuffles. The pivot loop is not unrolled (the kernel's
 // phases run once per MM iteration, so compact code matters more than loop overhead):
 // registers of the pivot row and column are picked by selects. Other warps return at once.
-template <int RP>
+template <int RP, int RW>
 __device__ void gj_inverse_warps(const float2* G, int R, float2* Gi, float2* prow) {
-  constexpr int NW = RP / 8, CPL = RP / 32, LD = RP + 8;
+  constexpr int NW = RP / RW, CPL = RP / 32, LD = RP + 8;
   const unsigned FULL = 0xffffffffu;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp >= NW) return;
-  float2 M[8][CPL];
+  float2 M[RW][CPL];
 #pragma unroll
-  for (int r = 0; r < 8; ++r)
+  for (int r = 0; r < RW; ++r)
 #pragma unroll
     for (int q = 0; q < CPL; ++q) {
-      const int i = warp * 8 + r, j = lane + 32 * q;
+      const int i = warp * RW + r, j = lane + 32 * q;
       M[r][q] = (i < R && j < R) ? G[i * R + j] : make_float2(i == j ? 1.f : 0.f, 0.f);
     }
 #pragma unroll 1
   for (int k = 0; k < RP; ++k) {
-    const int ow = k >> 3, kr = k & 7, kl = k & 31, kq = k >> 5;
+    const int ow = k / RW, kr = k % RW, kl = k & 31, kq = k >> 5;
     float2* pr = prow + (k & 1) * RP;
     if (warp == ow) {
       float2 rowk[CPL];
@@ -231,7 +236,7 @@ __device__ void gj_inverse_warps(const float2* G, int R, float2* Gi, float2* pro
       for (int q = 0; q < CPL; ++q) {
         rowk[q] = M[0][q];
 #pragma unroll
-        for (int r = 1; r < 8; ++r) rowk[q] = r == kr ? M[r][q] : rowk[q];
+        for (int r = 1; r < RW; ++r) rowk[q] = r == kr ? M[r][q] : rowk[q];
       }
       float2 dk = rowk[0];
 #pragma unroll
@@ -246,7 +251,7 @@ __device__ void gj_inverse_warps(const float2* G, int R, float2* Gi, float2* pro
         const float2 v = (lane + 32 * q == k) ? piv : cmul(rowk[q], piv);
         pr[lane + 32 * q] = v;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) M[r][q] = r == kr ? v : M[r][q];
+        for (int r = 0; r < RW; ++r) M[r][q] = r == kr ? v : M[r][q];
       }
     }
     bar_named(1, NW * 32);
@@ -256,7 +261,7 @@ __device__ void gj_inverse_warps(const float2* G, int R, float2* Gi, float2* pro
     const float2 piv = pr[k];
     const bool own = warp == ow;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
+    for (int r = 0; r < RW; ++r) {
       float2 src = M[r][0];
 #pragma unroll
       for (int q = 1; q < CPL; ++q) src = q == kq ? M[r][q] : src;
@@ -275,9 +280,9 @@ __device__ void gj_inverse_warps(const float2* G, int R, float2* Gi, float2* pro
     }
   }
 #pragma unroll
-  for (int r = 0; r < 8; ++r)
+  for (int r = 0; r < RW; ++r)
 #pragma unroll
-    for (int q = 0; q < CPL; ++q) Gi[(warp * 8 + r) * LD + lane + 32 * q] = M[r][q];
+    for (int q = 0; q < CPL; ++q) Gi[(warp * RW + r) * LD + lane + 32 * q] = M[r][q];
 }
 
 // sum over the 8 lanes of a row group (lanes 8g .. 8g+7) of a float2
@@ -378,11 +383,11 @@ __device__ void ridge_refine(SM& sm, int R, const float2* Gi, const float2* Glo,
 // barrier.
 __device__ void ridge_solve(SM& sm, int R, const float2* Glo, const float2* hlo, int iters, float tol2) {
   if (R <= 32) {
-    gj_inverse_warps<32>(sm.Gf, R, sm.GJa, sm.Pk);
+    gj_inverse_warps<32, TTS_GJ_ROWS>(sm.Gf, R, sm.GJa, sm.Pk);
     __syncthreads();
     ridge_refine<32>(sm, R, sm.GJa, Glo, hlo, iters, tol2);
   } else {
-    gj_inverse_warps<64>(sm.Gf, R, sm.GJa, sm.Pk);
+    gj_inverse_warps<64, TTS_GJ_ROWS>(sm.Gf, R, sm.GJa, sm.Pk);
     __syncthreads();
     ridge_refine<64>(sm, R, sm.GJa, Glo, hlo, iters, tol2);
   }
@@ -588,7 +593,9 @@ __device__ void step_ingest(const FrameParams& p, SM& sm, int cta) {
     }
     __syncthreads();
   }
-  if (bad) atomicOr(&sm.misc[1], 1);
+  // a tensor-core row transform whose bounded wait ran out left Yt invalid: skip the frame
+  if (p.yt_ready && ((volatile int*)p.status)[2 + TTS_MAX_CLUSTER]) bad |= 2;
+  if (bad) atomicOr(&sm.misc[1], bad);
   // anchors A[t-1], B[t-1]
   for (int e = tid; e < p.rA * R; e += nth) sm.A0[e] = sm.A[e];
   for (int e = tid; e < p.rB * R; e += nth) sm.B0[e] = sm.B[e];
@@ -725,9 +732,10 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
   }
   __syncthreads();
   const bool ffk = p.ridge_ff_all || k == p.K - 1;   // readout sums of this system in float-float
-  // stop once the corrections fall below the accuracy of the system: ~1e-13 relative for the
-  // float-float sums, ~1e-6 for FP32 readout sums
-  ridge_solve(sm, R, Glo, hlo, p.refine, ffk ? 1e-26f : 1e-12f);
+  // float-float readout sums: refine until the corrections fall below ~1e-13 relative; FP32
+  // readout sums (an MM iteration before the last with TTS_RIDGE_FF_LAST): one sweep takes the
+  // FP32 inverse's kappa u error to the accuracy of that system
+  ridge_solve(sm, R, Glo, hlo, ffk ? p.refine : 1, ffk ? 1e-26f : 1e-12f);
   // B^H B (hi) in shared memory for the factor step, over the solve's low parts
   float2* MBt = sm.GJb;
   for (int e = tid; e < RR; e += nth) MBt[e] = p.MB[e];
@@ -900,7 +908,7 @@ __device__ void reduce_A_rows(const FrameParams& p, SM& sm, int cta, int dst, bo
 template <int OWN>
 __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) {
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int Nx = p.Nx, Ny = p.Ny, R = p.R, C = p.C, MC = p.MC;
+  const int Ny = p.Ny, R = p.R, C = p.C, MC = p.MC;
   const int s = sm.misc[0];
   const int src = p.jacobi ? (k & 1) : ((k + 1) & 1);
   const float2* Ah = p.AhS[src];
@@ -1083,7 +1091,10 @@ __device__ __forceinline__ void frame_run(const FrameParams& p, unsigned char* s
       int bad = 0;
       for (int c = 0; c < p.C; ++c) bad |= ((volatile int*)p.status)[1 + c];
       if (bad) {
-        if (step == 1 && cta == 0 && tid == 0) atomicOr(p.status, 1);
+        if (step == 1 && cta == 0 && tid == 0) {
+          if (bad & 1) atomicOr(p.status, 1);                      // non-finite input sample
+          if (bad & 2) atomicOr(p.status + 1 + TTS_MAX_CLUSTER, 1);   // row transform ran out of time
+        }
         return;
       }
     }

@@ -42,6 +42,10 @@ struct tts_handle {
   // (mask_map on the host, mask_map_dev its device address), so no copy follows the draw
   uint8_t* mask_map = nullptr;
   uint8_t* mask_map_dev = nullptr;
+  // test hook (tts_test_withhold_row_transform): the next row transform withholds this K'
+  // chunk's arrival and waits at most test_wait_cycles; -1: none
+  int test_withhold = -1;
+  long long test_wait_cycles = 0;
 };
 
 // Validates a configuration (message through tts_last_error on failure).

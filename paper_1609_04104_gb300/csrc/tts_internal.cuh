@@ -359,7 +359,7 @@ __host__ __device__ inline FrameLayout frame_layout(int Nx, int Ny, int R, int r
   L.Gf = take(f2 * R * R);
   L.GJa = take(f2 * Rq * (Rq + 8));
   L.GJb = take(f2 * R * R);        // low parts of the ridge matrix; B^H B for the factor step
-  L.gjx = take(f2 * 136);
+  L.gjx = take(f2 * 136);          // pivot rows of the inverse (2 slots x 64), sweep flags
   L.vec = take(f2 * (6 * R + 16));
   L.yb = take(f2 * MC * rB);       // Yt block of this CTA's B rows, kept when |S| <= MC
   const int rmax = rA > rB ? rA : rB;
@@ -479,8 +479,15 @@ int launch_ridge(const double2* G, const double2* h, int R, double2* gamma, cuda
 // batched 2D DFT for square N in {64, 128, 256} as one persistent launch over row and
 // column band tasks (tts_fft_square.cu)
 bool fft2d_square_ok(int Nx, int Ny);
+// Times the square kernel's launch shapes (CTAs per SM, row-ahead lag) on in/out (batch
+// images of N x N) and records the fastest for later launches of (device, N, direction);
+// synchronous on the legacy default stream.
+int tune_fft2d_square(const float2* in, float2* out, int batch, int N, int inverse, const float2* W, int* err,
+                      int reps, double* best_ms, int* best_per_sm, double* best_lag);
+// withhold >= 0 (test hook): the image whose row tasks publish nothing, so that the waits of
+// its column tasks run out after `limit` SM clocks
 int launch_fft2d_square(const float2* in, float2* out, int batch, int N, int inverse, const float2* W, int* err,
-                        cudaStream_t st);
+                        cudaStream_t st, int withhold = -1, long long limit = 2000000000LL);
 // batched 2D DFT for other Nx x Ny whose line lengths both have a band shape: a row-band and a
 // column-band launch per group of images that fits L2 (tts_fft_lines.cu)
 bool fft2d_lines_ok(int Nx, int Ny);
@@ -491,7 +498,9 @@ bool dft_gemm_size_ok(int N);
 // Inverse unitary DFT of the acquired rows (mask lines) of a frame, Yt = y_S conj(F_Ny),
 // row-major |S| x Ny, on the tensor cores.
 int launch_row_dft(const float2* y, float2* yt, const uint8_t* mask, int Nx, int Ny, int full_frame, int split,
-                   int* err, cudaStream_t st);
+                   int* err, cudaStream_t st, int withhold = -1, long long limit = 2000000000LL);
+// withhold >= 0 (test hook): the first pass's K' chunk whose copy and producer arrival are
+// withheld, so that the waits for it run out after `limit` SM clocks
 int launch_dft2d_gemm(const float2* in, float2* out, float2* tmp, int batch, int Nx, int Ny, int inverse,
-                      int split, int* err, cudaStream_t st);
+                      int split, int* err, cudaStream_t st, int withhold = -1, long long limit = 2000000000LL);
 int launch_init_factors(float2* A, int N, int R, uint64_t seed, uint32_t which, cudaStream_t st);

@@ -558,6 +558,13 @@ int launch_image(const float2* A, const float2* B, const float2* gamma, float2* 
   int sms = 0;
   if (per_device(sm_count,
                  [](int dev, int* v) {
+                   // the largest shared-memory carveout, as the frame kernel runs with: SMs
+                   // then keep one L1 / shared split across a frame's launches
+                   if (cudaFuncSetAttribute(image_kernel<32>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                            cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
+                       cudaFuncSetAttribute(image_kernel<8>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                            cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+                     return TTS_ECUDA;
                    return cudaDeviceGetAttribute(v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess ? TTS_OK
                                                                                                       : TTS_ECUDA;
                  },
@@ -616,6 +623,8 @@ int launch_image_batch(const ImageJob* jobs, const int* n, int grid, cudaStream_
   return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
 }
 
+size_t sampler_smem_max();
+
 int launch_sampler(const float2* A, int Nx, int Ny, int R, const double* p_in, double* p_out, int policy,
                    double vd_alpha, int k_lines, int central, uint64_t seed, uint64_t ctr, int with_replacement,
                    const float2* Wx, uint8_t* mask_out, uint8_t* mask_out2, cudaStream_t st, int no_fft) {
@@ -623,8 +632,21 @@ int launch_sampler(const float2* A, int Nx, int Ny, int R, const double* p_in, d
                              with_replacement, Wx, mask_out, mask_out2);
   j.no_fft = no_fft;
   const size_t smem = sampler_smem(Nx, j.fft_cols);
-  cudaError_t e = cudaFuncSetAttribute(sampler_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return TTS_ECUDA;
+  static PerDevice attrs;
+  int done = 0;
+  if (per_device(attrs,
+                 [](int, int* v) {
+                   // room for any job, and the largest carveout (see launch_image)
+                   if (cudaFuncSetAttribute(sampler_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)sampler_smem_max()) != cudaSuccess ||
+                       cudaFuncSetAttribute(sampler_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                            cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+                     return TTS_ECUDA;
+                   *v = 1;
+                   return TTS_OK;
+                 },
+                 &done) != TTS_OK)
+    return TTS_ECUDA;
   sampler_kernel<<<1, SAMPLER_THREADS, smem, st>>>(j);
   return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
 }

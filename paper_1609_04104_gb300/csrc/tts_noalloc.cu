@@ -35,7 +35,7 @@ size_t scratch_bytes(int Nx, int Ny, int R, int C) {
   b += up(sizeof(float4) * (size_t)C * R * R) + up(sizeof(float4) * (size_t)C * Nx * R);  // partials of B
   b += up(sizeof(float4) * (size_t)C * R * R);                             // partials of MA
   b += up(sizeof(double) * SF_COUNT) + up(sizeof(double2) * R);           // frame scalars, gamma (FP64)
-  b += up(sizeof(int) * (1 + TTS_MAX_CLUSTER));                           // status words
+  b += up(sizeof(int) * (3 + TTS_MAX_CLUSTER));                           // status words
   return b;
 }
 
@@ -173,10 +173,10 @@ extern "C" int tts_push_frame_noalloc(const tts_frame_args* a, void* cuda_stream
   p.partMA = (float4*)take(sizeof(float4) * (size_t)p.C * R * R);
   p.sf = (double*)take(sizeof(double) * SF_COUNT);
   p.gamma_d = (double2*)take(sizeof(double2) * R);
-  p.status = (int*)take(sizeof(int) * (1 + TTS_MAX_CLUSTER));
+  p.status = (int*)take(sizeof(int) * (3 + TTS_MAX_CLUSTER));
 
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  const int nstatus = 1 + TTS_MAX_CLUSTER;
+  const int nstatus = 3 + TTS_MAX_CLUSTER;
   noalloc_setup_kernel<<<(Nx + Ny + nstatus + 255) / 256, 256, 0, st>>>(Wx, Nx, Wy, Ny, p.status, nstatus);
   if (cudaGetLastError() != cudaSuccess)
     return na_fail(TTS_ECUDA, "tts_push_frame_noalloc: set-up of the device scratch failed");

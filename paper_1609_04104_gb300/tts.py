@@ -38,7 +38,7 @@ EXPORTS = [
     "tts_stream_footprint", "tts_engine_create", "tts_engine_destroy", "tts_engine_admit", "tts_engine_release",
     "tts_engine_handle", "tts_engine_step", "tts_engine_image", "tts_engine_mask", "tts_engine_synchronize",
     "tts_engine_info", "tts_engine_autotune", "tts_dft2d_gemm", "tts_set_coil_maps", "tts_fp32_fma_rate",
-    "tts_last_error",
+    "tts_test_withheld_wait", "tts_test_withhold_row_transform", "tts_fft2d_autotune", "tts_last_error",
 ]
 
 
@@ -134,6 +134,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "tts_engine_info": (I, [H, ctypes.POINTER(tts_engine_stats)]),
         "tts_engine_autotune": (I, [ctypes.POINTER(tts_config), I, I, ctypes.POINTER(I), P]),
         "tts_fp32_fma_rate": (I, [I, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "tts_test_withheld_wait": (I, [I, P, P, P, I, I, I, ctypes.c_longlong, P, P]),
+        "tts_test_withhold_row_transform": (I, [H, I, ctypes.c_longlong]),
+        "tts_fft2d_autotune": (I, [I, I, I, I, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(D)]),
         "tts_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -398,6 +401,27 @@ def tts_fp32_fma_rate(iters=200000, reps=3) -> tuple[float, float]:
     tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
     _check(load().tts_fp32_fma_rate(iters, reps, ctypes.byref(tf), ctypes.byref(ms)))
     return tf.value, ms.value
+
+
+def tts_fft2d_autotune(N, batch, inverse=False, reps=3) -> dict:
+    """Times tts_fft2d's launch shapes for square N x N and keeps the fastest (tts.h)."""
+    ms, per_sm, lag = ctypes.c_double(0.0), ctypes.c_int(0), ctypes.c_double(0.0)
+    _check(load().tts_fft2d_autotune(N, batch, int(inverse), reps, ctypes.byref(ms), ctypes.byref(per_sm),
+                                     ctypes.byref(lag)))
+    return {"ms": ms.value, "ctas_per_sm": per_sm.value, "lag_scale": lag.value}
+
+
+def tts_test_withheld_wait(kind, x, out, tmp, index, wait_cycles, status, stream=None) -> None:
+    """Test hook: a square FFT (kind 0) or tensor-core DFT (kind 1) of torch CUDA tensors
+    (batch, N, N) complex64 with one awaited arrival withheld (tts.h)."""
+    batch, N = x.shape[0], x.shape[1]
+    s = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(load().tts_test_withheld_wait(kind, x.data_ptr(), out.data_ptr(), None if tmp is None else tmp.data_ptr(),
+                                         batch, N, index, wait_cycles, status.data_ptr(), s))
+
+
+def tts_test_withhold_row_transform(h, chunk, wait_cycles) -> None:
+    _check(load().tts_test_withhold_row_transform(h, chunk, wait_cycles))
 
 
 def tts_stream_footprint(cfg: tts_config) -> int:
