@@ -196,10 +196,9 @@ __device__ __forceinline__ void tri_pair(int idx, int R, int& q, int& r) {
 // kappa(G) u_32, so two sweeps reach the float-float accuracy of the system; the sweeps
 // stop once every correction is below sqrt(tol2) relative.
 // ---------------------------------------------------------------------------------
-// rows of the ridge matrix each warp of the Gauss-Jordan inverse keeps in registers
-#ifndef TTS_GJ_ROWS
-#define TTS_GJ_ROWS 8
-#endif
+// rows of the ridge matrix each warp of the Gauss-Jordan inverse keeps in registers (four:
+// eight warps share each pivot step for R <= 32; measured 6.9 us against 7.4 us with eight rows)
+#define TTS_GJ_ROWS 4
 
 __device__ __forceinline__ void bar_named(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
@@ -902,6 +901,66 @@ __device__ void reduce_A_rows(const FrameParams& p, SM& sm, int cta, int dst, bo
   }
 }
 
+// The single-chunk form of reduce_A_rows (|S| <= MC), run at the start of the phase that
+// needs the result, with no cluster barrier of its own: every CTA sums the per-CTA partials
+// of all |S| rows of Ahat_S into shared memory AR for itself and writes its slice of the rows
+// to AhS[dst]; it sums ||a_r||^2 into nAs (shared, when given) and, on CTA 0, into nA[dst];
+// with ma it accumulates its slice of the upper triangle of Ahat_S^H Ahat_S over all |S| rows
+// in float-float (eight threads a pair, combined by shuffles) and writes those entries of
+// MA / MAlo, which are then final. Ends with a block barrier.
+__device__ void reduce_A_full(const FrameParams& p, SM& sm, int cta, int dst, float2* AR, float* nAs, bool ma) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int R = p.R, C = p.C, Nx = p.Nx;
+  const int s = sm.misc[0];
+  const Slice ms = slice_of(s, C, cta);
+  for (int e = tid; e < s * R; e += nth) {
+    const float2 v = sum_partials(p.partA + e, (size_t)Nx * R, C);
+    AR[e] = v;
+    if (e >= ms.lo * R && e < ms.hi * R) p.AhS[dst][e] = v;
+  }
+  for (int r = tid; r < R; r += nth) {
+    float acc = 0.f;
+    for (int c = 0; c < C; c += 4) {
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = c + u < C ? p.partNA[(c + u) * R + r] : 0.f;
+      acc += (v[0] + v[1]) + (v[2] + v[3]);
+    }
+    if (nAs) nAs[r] = acc;
+    if (cta == 0) p.nA[dst][r] = acc;
+  }
+  __syncthreads();
+  if (!ma) return;
+  const int RT = R * (R + 1) / 2;
+  const Slice ps = slice_of(RT, C, cta);
+  const int g = tid >> 3, u = tid & 7;
+  for (int base = ps.lo; base < ps.hi; base += nth / 8) {   // uniform trip count
+    const int idx = base + g;
+    const bool valid = idx < ps.hi;
+    int q = 0, r = 0;
+    if (valid) tri_pair(idx, R, q, r);
+    CFF acc = cff_zero();
+    if (valid)
+      for (int m = u; m < s; m += 8) cff_macc(acc, AR[m * R + q], AR[m * R + r]);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      const float a = __shfl_xor_sync(0xffffffffu, acc.rh, o), b = __shfl_xor_sync(0xffffffffu, acc.rl, o);
+      const float c = __shfl_xor_sync(0xffffffffu, acc.ih, o), d = __shfl_xor_sync(0xffffffffu, acc.il, o);
+      ff_add_ff(acc.rh, acc.rl, a, b);
+      ff_add_ff(acc.ih, acc.il, c, d);
+    }
+    if (valid && u == 0) {
+      const float4 v = cff_pack(acc);
+      p.MA[q * R + r] = make_float2(v.x, v.y);
+      p.MAlo[q * R + r] = make_float2(v.z, v.w);
+      if (q != r) {
+        p.MA[r * R + q] = make_float2(v.x, -v.y);
+        p.MAlo[r * R + q] = make_float2(v.z, -v.w);
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------
 // step B: majorized B step (S2) on this CTA's rows, then partials of B^H B and P
 // ---------------------------------------------------------------------------------
@@ -926,9 +985,15 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) 
     ocol[o] = e - orow[o] * R;
   }
   float* nAs = (float*)sm.tmpv;   // ||a_r||^2 in shared memory
+  // |S| <= MC: Ahat'_S (and ||a'||^2, and the next Gram's Ahat'^H Ahat') reduced here, every
+  // CTA for itself, instead of in a phase of its own
+  const bool merged = s <= MC;
+  float2* AR = sm.chunk + MC * R;
+  if (merged) reduce_A_full(p, sm, cta, (k + 1) & 1, AR, p.jacobi ? nullptr : nAs, k + 1 < p.K);
+  const bool own_ah = merged && !p.jacobi;   // the reduced rows are this step's Ahat
   for (int r = tid; r < R; r += nth) {
     sm.gam[r] = p.gamma[r];
-    nAs[r] = nA[r];
+    if (!own_ah) nAs[r] = nA[r];
   }
   // MA = Ahat^H Ahat (thread-owned entries) and U[j][r] = sum_m Yt[m][j] conj(Ahat[m][r])
   float2 ma[OWN], u[OWN];
@@ -937,7 +1002,8 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) 
   const int NO = nb * R;
   for (int m0 = 0; m0 < s; m0 += MC) {
     const int mc = min(MC, s - m0);
-    for (int e = tid; e < mc * R; e += nth) AH[e] = Ah[m0 * R + e];
+    if (!own_ah)
+      for (int e = tid; e < mc * R; e += nth) AH[e] = Ah[m0 * R + e];
     if (s > MC || !sm.yb_ready) load_yb(p, YB, m0, mc, bs.lo, nb);
     __syncthreads();
     if (s <= MC) sm.yb_ready = true;
@@ -950,11 +1016,12 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) 
       uj[o] = vu ? orow[o] : 0;
       ur[o] = vu ? ocol[o] : 0;
     }
+    const float2* AHm = own_ah ? AR : AH;
     for (int mm = 0; mm < mc; ++mm) {
 #pragma unroll
       for (int o = 0; o < OWN; ++o) {
-        cfmac(ma[o], AH[mm * R + mr[o]], AH[mm * R + mq[o]]);
-        cfmac(u[o], AH[mm * R + ur[o]], YB[mm * nb + uj[o]]);
+        cfmac(ma[o], AHm[mm * R + mr[o]], AHm[mm * R + mq[o]]);
+        cfmac(u[o], AHm[mm * R + ur[o]], YB[mm * nb + uj[o]]);
       }
     }
     __syncthreads();
@@ -1080,9 +1147,16 @@ __device__ __forceinline__ void frame_run(const FrameParams& p, unsigned char* s
   }
   __syncthreads();
   cg::cluster_group cluster = cg::this_cluster();
+  // |S| <= MC: the reduction of Ahat'_S after each A step runs at the start of the B step
+  // (reduce_A_full), so its own step and the barrier before it are skipped (uniform: every
+  // CTA has the same |S|)
+  const bool merged = sm.misc[0] <= p.MC;
   for (int step = step_begin; step < step_end; ++step) {
+    if (merged && step >= 3 && (step - 3) % 4 == 1) continue;
     if (step > step_begin) {
-      __threadfence();
+      // the cluster barrier releases every thread's earlier writes (shared and global) to
+      // the cluster and acquires the others': the partial sums in global memory need no
+      // separate fence (separate launches are ordered by the stream)
       if (fused) cluster.sync();
       else __syncthreads();
     }
@@ -1104,15 +1178,17 @@ __device__ __forceinline__ void frame_run(const FrameParams& p, unsigned char* s
       continue;
     }
     if (step == 1) {
-      // Ahat_S of A[t-1] by rows (and its Gram partial); P of B[t-1] over this CTA's rows
-      reduce_A_rows(p, sm, cta, 0, true);
+      // Ahat_S of A[t-1] and its Gram (partials by rows, or final in the single-chunk form);
+      // P of B[t-1] over this CTA's rows
+      if (merged) reduce_A_full(p, sm, cta, 0, sm.chunk + p.MC * R, nullptr, true);
+      else reduce_A_rows(p, sm, cta, 0, true);
       __syncthreads();
       partials_B<OWN>(p, sm, cta, false, true, p.ridge_ff_all || p.K == 1);
       __syncthreads();
       continue;
     }
     if (step == 2) {
-      reduce_sums(p, sm, cta, true);
+      reduce_sums(p, sm, cta, !merged);
       __syncthreads();
       continue;
     }
@@ -1120,7 +1196,7 @@ __device__ __forceinline__ void frame_run(const FrameParams& p, unsigned char* s
     if (sub == 0) step_solve_A<OWN>(p, sm, cta, k);
     else if (sub == 1) reduce_A_rows(p, sm, cta, (k + 1) & 1, k + 1 < p.K);
     else if (sub == 2) step_B<OWN>(p, sm, cta, k, k == p.K - 1);
-    else reduce_sums(p, sm, cta, true);
+    else reduce_sums(p, sm, cta, !merged);
     __syncthreads();
   }
 }
