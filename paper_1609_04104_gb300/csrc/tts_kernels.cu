@@ -356,14 +356,25 @@ __device__ __forceinline__ void sampler_run(const SamplerJob& job, unsigned char
       Q[k] = v > 0.0 ? (unsigned long long)floor(v * two52) : 0ull;
     }
     __syncthreads();
-    // inclusive prefix sum (Hillis-Steele over Nx <= 512 entries; integer, exact)
-    unsigned long long* T = (unsigned long long*)buf;  // scan scratch (>= Nx u64)
-    for (int off = 1; off < ncand; off <<= 1) {
-      for (int k = tid; k < ncand; k += blockDim.x) T[k] = Q[k] + (k >= off ? Q[k - off] : 0ull);
-      __syncthreads();
-      for (int k = tid; k < ncand; k += blockDim.x) Q[k] = T[k];
-      __syncthreads();
+    // inclusive prefix sum by one warp (integer, exact): blocks of 32 entries in order, a
+    // shuffle scan within each block and the running total carried across blocks, so no
+    // CTA barrier is needed between the steps
+    if (warp == 0) {
+      unsigned long long carry = 0ull;
+      for (int b0 = 0; b0 < ncand; b0 += 32) {
+        const int k = b0 + lane;
+        unsigned long long v = k < ncand ? Q[k] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
+          if (lane >= o) v += t;
+        }
+        v += carry;
+        if (k < ncand) Q[k] = v;
+        carry = __shfl_sync(0xffffffffu, v, 31);
+      }
     }
+    __syncthreads();
     const unsigned long long Qtot = Q[ncand - 1];
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     const uint32_t c2 = (uint32_t)ctr, c3 = (uint32_t)(ctr >> 32);
