@@ -161,9 +161,21 @@ __device__ __forceinline__ float4 cff_pack(const CFF& c) {
   fast_two_sum(c.ih, c.il, ih, il);
   return make_float4(rh, ih, rl, il);
 }
-// float-float sum of n float4 partials (hi.x, hi.y, lo.x, lo.y) `stride` apart
+// float-float sum of n float4 partials (hi.x, hi.y, lo.x, lo.y) `stride` apart, in order; for
+// n <= 8 every load is issued before the first addition
 __device__ __forceinline__ float4 ff_sum_partials(const float4* src, size_t stride, int n) {
   float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+  if (n <= 8) {
+    float4 v[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v[c] = c < n ? src[c * stride] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      ff_add_ff(rh, rl, v[c].x, v[c].z);
+      ff_add_ff(ih, il, v[c].y, v[c].w);
+    }
+    return make_float4(rh, ih, rl, il);
+  }
   for (int c = 0; c < n; c += 4) {
     float4 v[4];
 #pragma unroll
@@ -211,8 +223,10 @@ __device__ __forceinline__ void bar_named(int id, int nthreads) {
 // from the lane that holds it by shuffles. The pivot loop is not unrolled (the kernel's
 // phases run once per MM iteration, so compact code matters more than loop overhead):
 // registers of the pivot row and column are picked by selects. Other warps return at once.
+// Not inlined: its registers are then allocated apart from the rest of the frame code, whose
+// changes otherwise moved its time per inverse between 6.6 and 8.3 us.
 template <int RP, int RW>
-__device__ void gj_inverse_warps(const float2* G, int R, float2* Gi, float2* prow) {
+__device__ __noinline__ void gj_inverse_warps(const float2* G, int R, float2* Gi, float2* prow) {
   constexpr int NW = RP / RW, CPL = RP / 32, LD = RP + 8;
   const unsigned FULL = 0xffffffffu;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -645,7 +659,7 @@ __device__ __forceinline__ void step_coefficients(const FrameParams& p, SM& sm, 
   }
 }
 
-template <int OWN>
+template <int OWN, bool LOADS_FIRST>
 __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int Nx = p.Nx, R = p.R, C = p.C, MC = p.MC;
@@ -668,13 +682,46 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
   // The ridge system (S1) in float-float: G = (Ahat_S^H Ahat_S) .* (B^H B) + mu I, the Gram of
   // the masked DFTs of the rank-one images (separable form), from the reduced float-float
   // sums; h = sum_m conj(Ahat_S[m][r]) P[m][r] = (Phi^H y)_r with P = hi + lo.
-  float2* Glo = sm.GJb;   // low parts of G (GJb holds B^H B again after the solve)
+  float2* Glo = sm.GJb;   // low parts of G
   float2* hlo = sm.tmpv;
+  // B^H B (hi) for the factor step after the solve: kept from the loads below in the twiddle
+  // region, which the solve leaves alone (it is filled after gM is formed), when that region
+  // is large enough; else read again into GJb after the solve
+  const bool mb_tw = MC * na >= RR;
+  float2* MBt = mb_tw ? TW : sm.GJb;
+  // the loads of the system first, so that their L2 latencies overlap: this thread's first LF
+  // entries of the reduced Gram factors and of the first chunk of Ahat_S, P and P's low part
+  // (two each at most, one in the kernels with four or more outputs a thread, to bound the
+  // registers they hold; none in the persistent multi-stream kernel, whose other state leaves
+  // no registers for them; any further entries follow in loops, in the same arithmetic)
+  constexpr int LF = !LOADS_FIRST ? 0 : (OWN >= 4 ? 1 : OWN);
+  constexpr int LFA = LF > 0 ? LF : 1;
+  const int mc0 = min(MC, s);
+  float2 gah[LFA], gal[LFA], gbh[LFA], gbl[LFA], sa[LFA], sp[LFA], sl[LFA];
+#pragma unroll
+  for (int o = 0; o < LF; ++o) {
+    const int e = tid + o * nth;
+    if (e < RR) {
+      gah[o] = p.MA[e];
+      gal[o] = p.MAlo[e];
+      gbh[o] = p.MB[e];
+      gbl[o] = p.MBlo[e];
+    }
+  }
+#pragma unroll
+  for (int o = 0; o < LF; ++o) {
+    const int e = tid + o * nth;
+    if (e < mc0 * R) {
+      sa[o] = AhS[e];
+      sp[o] = p.P[e];
+      sl[o] = p.Plo[e];
+    }
+  }
   {
     const float mu_hi = (float)p.mu, mu_lo = (float)(p.mu - (double)mu_hi);
-    for (int e = tid; e < RR; e += nth) {
-      const float2 ah = p.MA[e], al = p.MAlo[e], bh = p.MB[e], bl = p.MBlo[e];
-      // (ah + al)(bh + bl): ah bh exactly, ah bl + al bh rounded
+    // (ah + al)(bh + bl) + mu [q == r] in float-float: ah bh exactly, ah bl + al bh rounded
+    auto entry = [&](int e, float2 ah, float2 al, float2 bh, float2 bl) {
+      if (mb_tw) MBt[e] = bh;
       float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
       ff_acc2(rh, rl, ah.x, bh.x, -ah.y, bh.y);
       ff_acc2(ih, il, ah.x, bh.y, ah.y, bh.x);
@@ -695,7 +742,13 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
       two_sum(ih, il, ih, il);
       sm.Gf[e] = make_float2(rh, ih);
       Glo[e] = make_float2(rl, il);
+    };
+#pragma unroll
+    for (int o = 0; o < LF; ++o) {
+      const int e = tid + o * nth;
+      if (e < RR) entry(e, gah[o], gal[o], gbh[o], gbl[o]);
     }
+    for (int e = tid + LF * nth; e < RR; e += nth) entry(e, p.MA[e], p.MAlo[e], p.MB[e], p.MBlo[e]);
   }
   {
     // T threads per output r (T a power of two dividing 32), m strided over them
@@ -707,10 +760,27 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
     float2* QL = QC;   // low parts of P, staged
     for (int m0 = 0; m0 < s; m0 += MC) {
       const int mc = min(MC, s - m0);
-      for (int e = tid; e < mc * R; e += nth) {
-        AH[e] = AhS[m0 * R + e];
-        PC[e] = p.P[m0 * R + e];
-        QL[e] = p.Plo[m0 * R + e];
+      if (m0 == 0) {
+#pragma unroll
+        for (int o = 0; o < LF; ++o) {
+          const int e = tid + o * nth;
+          if (e < mc * R) {
+            AH[e] = sa[o];
+            PC[e] = sp[o];
+            QL[e] = sl[o];
+          }
+        }
+        for (int e = tid + LF * nth; e < mc * R; e += nth) {
+          AH[e] = AhS[e];
+          PC[e] = p.P[e];
+          QL[e] = p.Plo[e];
+        }
+      } else {
+        for (int e = tid; e < mc * R; e += nth) {
+          AH[e] = AhS[m0 * R + e];
+          PC[e] = p.P[m0 * R + e];
+          QL[e] = p.Plo[m0 * R + e];
+        }
       }
       __syncthreads();
       if (valid)
@@ -735,10 +805,10 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
   // readout sums (an MM iteration before the last with TTS_RIDGE_FF_LAST): one sweep takes the
   // FP32 inverse's kappa u error to the accuracy of that system
   ridge_solve(sm, R, Glo, hlo, ffk ? p.refine : 1, ffk ? 1e-26f : 1e-12f);
-  // B^H B (hi) in shared memory for the factor step, over the solve's low parts
-  float2* MBt = sm.GJb;
-  for (int e = tid; e < RR; e += nth) MBt[e] = p.MB[e];
-  __syncthreads();
+  if (!mb_tw) {
+    for (int e = tid; e < RR; e += nth) MBt[e] = p.MB[e];
+    __syncthreads();
+  }
   // alpha_A = sum |gamma_r|^2 ||b_r||^2 + rho (||b_r||^2 = (B^H B)[r][r])
   step_coefficients(p, sm, (const float*)MBt, 2 * (R + 1), p.sf[SF_RHO], p.sf[SF_ABAR_A]);
   if (cta == 0)
@@ -913,10 +983,35 @@ __device__ void reduce_A_full(const FrameParams& p, SM& sm, int cta, int dst, fl
   const int R = p.R, C = p.C, Nx = p.Nx;
   const int s = sm.misc[0];
   const Slice ms = slice_of(s, C, cta);
-  for (int e = tid; e < s * R; e += nth) {
-    const float2 v = sum_partials(p.partA + e, (size_t)Nx * R, C);
-    AR[e] = v;
-    if (e >= ms.lo * R && e < ms.hi * R) p.AhS[dst][e] = v;
+  if (C <= 8) {
+    // two entries a thread at a time, all their loads issued before the first addition (the
+    // additions in the order of sum_partials)
+    for (int e0 = tid; e0 < s * R; e0 += 2 * nth) {
+      float2 v[2][8];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int e = e0 + u * nth;
+          v[u][c] = (e < s * R && c < C) ? p.partA[(size_t)c * Nx * R + e] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = e0 + u * nth;
+        if (e >= s * R) continue;
+        float2 acc = make_float2(0.f, 0.f);
+        acc = cadd(acc, cadd(cadd(v[u][0], v[u][1]), cadd(v[u][2], v[u][3])));
+        if (C > 4) acc = cadd(acc, cadd(cadd(v[u][4], v[u][5]), cadd(v[u][6], v[u][7])));
+        AR[e] = acc;
+        if (e >= ms.lo * R && e < ms.hi * R) p.AhS[dst][e] = acc;
+      }
+    }
+  } else {
+    for (int e = tid; e < s * R; e += nth) {
+      const float2 v = sum_partials(p.partA + e, (size_t)Nx * R, C);
+      AR[e] = v;
+      if (e >= ms.lo * R && e < ms.hi * R) p.AhS[dst][e] = v;
+    }
   }
   for (int r = tid; r < R; r += nth) {
     float acc = 0.f;
@@ -1109,7 +1204,7 @@ __device__ void reduce_sums(const FrameParams& p, SM& sm, int cta, bool ma) {
 }
 
 // Steps [step_begin, step_end) of one frame, run by CTA `cta` of the cluster that owns it.
-template <int OWN>
+template <int OWN, bool LOADS_FIRST>
 __device__ __forceinline__ void frame_run(const FrameParams& p, unsigned char* smem_raw, int cta, int step_begin,
                                           int step_end, int fused) {
   SM sm = carve(p, smem_raw);
@@ -1193,7 +1288,7 @@ __device__ __forceinline__ void frame_run(const FrameParams& p, unsigned char* s
       continue;
     }
     const int k = (step - 3) / 4, sub = (step - 3) % 4;
-    if (sub == 0) step_solve_A<OWN>(p, sm, cta, k);
+    if (sub == 0) step_solve_A<OWN, LOADS_FIRST>(p, sm, cta, k);
     else if (sub == 1) reduce_A_rows(p, sm, cta, (k + 1) & 1, k + 1 < p.K);
     else if (sub == 2) step_B<OWN>(p, sm, cta, k, k == p.K - 1);
     else reduce_sums(p, sm, cta, !merged);
@@ -1205,7 +1300,9 @@ template <int OWN>
 __global__ void __launch_bounds__(TTS_THREADS, 1) frame_kernel(FrameParams p, int step_begin, int step_end,
                                                                int fused) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  frame_run<OWN>(p, smem_raw, blockIdx.x, step_begin, step_end, fused);
+  pdl_release();
+  pdl_wait();
+  frame_run<OWN, true>(p, smem_raw, blockIdx.x, step_begin, step_end, fused);
 }
 
 // Frames of many independent trackers (streams of any Nx, Ny, R) in one persistent
@@ -1233,7 +1330,7 @@ __global__ void __launch_bounds__(TTS_THREADS, 1) frame_batch_kernel(const Frame
     int* dst = (int*)&sp;
     for (int e = threadIdx.x; e < (int)(sizeof(FrameParams) / sizeof(int)); e += blockDim.x) dst[e] = src[e];
     __syncthreads();
-    frame_run<OWN>(sp, smem_raw, rank, 0, frame_num_steps(sp.K), 1);
+    frame_run<OWN, false>(sp, smem_raw, rank, 0, frame_num_steps(sp.K), 1);
     __syncthreads();
   }
 }
@@ -1340,19 +1437,7 @@ static int launch_frame_t(const FrameParams& p, int launch_mode, cudaStream_t st
   const int smem = p.lay.bytes;
   const int nsteps = frame_num_steps(p.K);
   if (launch_mode == TTS_LAUNCH_FUSED) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(p.C, 1, 1);
-    cfg.blockDim = dim3(TTS_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = p.C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, frame_kernel<OWN>, p, 0, nsteps, 1);
+    e = launch_pdl(frame_kernel<OWN>, dim3(p.C), dim3(TTS_THREADS), (size_t)smem, st, p.C, p, 0, nsteps, 1);
     if (e != cudaSuccess) return TTS_ECUDA;
   } else {
     for (int s = 0; s < nsteps; ++s) {

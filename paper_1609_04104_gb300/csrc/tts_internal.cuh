@@ -46,6 +46,46 @@ inline int per_device(PerDevice& c, F&& compute, int* out) {
 }
 
 // ------------------------------------------------------------------------------------
+// Programmatic dependent launch between the per-frame kernels of one stream (line draw,
+// frame, image). Each is launched with programmatic stream serialization, so its CTAs may
+// become resident while the kernel before it in the stream still runs; it calls pdl_wait()
+// before its first global access, which returns once every earlier kernel of the stream has
+// completed and its writes are visible (each of these kernels waits before it finishes, so
+// the chain is transitive). pdl_release() at the top of a kernel lets the next one launch
+// as soon as all of this kernel's CTAs have started. Launched without the attribute, both
+// are no-ops.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch `kernel` on `st` with programmatic stream serialization (and a cluster of
+// `cluster` CTAs along x when cluster > 0).
+template <typename... Params, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              int cluster, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  int n = 0;
+  attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[n].val.programmaticStreamSerializationAllowed = 1;
+  ++n;
+  if (cluster > 0) {
+    attr[n].id = cudaLaunchAttributeClusterDimension;
+    attr[n].val.clusterDim.x = cluster;
+    attr[n].val.clusterDim.y = 1;
+    attr[n].val.clusterDim.z = 1;
+    ++n;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = n;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// ------------------------------------------------------------------------------------
 // complex float / double helpers
 // ------------------------------------------------------------------------------------
 // Products are written with explicit fused multiply-adds and the library is compiled

@@ -66,6 +66,8 @@ __global__ void __launch_bounds__(256) image_kernel(const float2* __restrict__ A
                                                     const float2* __restrict__ gamma, float2* __restrict__ X,
                                                     int Nx, int Ny, int R) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_release();
+  pdl_wait();
   image_tile<TR>(A, B, gamma, X, Nx, Ny, R, blockIdx.y * TR, blockIdx.x * 32, smem_raw);
 }
 
@@ -450,6 +452,8 @@ __device__ __forceinline__ void sampler_run(const SamplerJob& job, unsigned char
 
 __global__ void __launch_bounds__(SAMPLER_THREADS) sampler_kernel(SamplerJob job) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_release();
+  pdl_wait();
   sampler_run(job, smem_raw);
 }
 
@@ -584,12 +588,14 @@ int launch_image(const float2* A, const float2* B, const float2* gamma, float2* 
   const int tiles32 = ((Ny + 31) / 32) * ((Nx + 31) / 32);
   if (tiles32 >= sms) {
     dim3 grid((Ny + 31) / 32, (Nx + 31) / 32);
-    image_kernel<32><<<grid, 256, smem, st>>>(A, B, gamma, X, Nx, Ny, R);
+    if (launch_pdl(image_kernel<32>, grid, dim3(256), smem, st, 0, A, B, gamma, X, Nx, Ny, R) != cudaSuccess)
+      return TTS_ECUDA;
   } else {
     dim3 grid((Ny + 31) / 32, (Nx + 7) / 8);
-    image_kernel<8><<<grid, 256, smem, st>>>(A, B, gamma, X, Nx, Ny, R);
+    if (launch_pdl(image_kernel<8>, grid, dim3(256), smem, st, 0, A, B, gamma, X, Nx, Ny, R) != cudaSuccess)
+      return TTS_ECUDA;
   }
-  return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
+  return TTS_OK;
 }
 
 SamplerJob sampler_job(const float2* A, int Nx, int Ny, int R, const double* p_in, double* p_out, int policy,
@@ -658,8 +664,8 @@ int launch_sampler(const float2* A, int Nx, int Ny, int R, const double* p_in, d
                  },
                  &done) != TTS_OK)
     return TTS_ECUDA;
-  sampler_kernel<<<1, SAMPLER_THREADS, smem, st>>>(j);
-  return cudaGetLastError() == cudaSuccess ? TTS_OK : TTS_ECUDA;
+  return launch_pdl(sampler_kernel, dim3(1), dim3(SAMPLER_THREADS), smem, st, 0, j) == cudaSuccess ? TTS_OK
+                                                                                         : TTS_ECUDA;
 }
 
 // Largest shared memory any sampler job needs (Nx <= TTS_MAX_N, at most 8192 staged
