@@ -310,10 +310,14 @@ __device__ __forceinline__ float2 sum8(float2 v) {
 
 // Refinement against G_hi (sm.Gf, row stride R) + Glo and h_hi (sm.h) + hlo with the inverse
 // Gi (row stride RP + 8): 8 threads per row (all R <= 64 rows in one pass of 512 threads).
-// The result is gamma = sm.gam + sm.glo. Ends with a block barrier.
+// The result is gamma = sm.gam + sm.glo. Returns true once a sweep's largest correction is
+// within sqrt(tol2) of the largest |gamma_r|. With slow2 > 0 (Gi the inverse of a nearby
+// system, not of this one) it gives up, returning false, when a correction has not shrunk
+// by sqrt(slow2) against the one before or when `iters` sweeps did not converge. Ends with a
+// block barrier; the return value is the same in every thread.
 template <int RP>
-__device__ void ridge_refine(SM& sm, int R, const float2* Gi, const float2* Glo, const float2* hlo, int iters,
-                             float tol2) {
+__device__ bool ridge_refine(SM& sm, int R, const float2* Gi, const float2* Glo, const float2* hlo, int iters,
+                             float tol2, float slow2) {
   constexpr int LD = RP + 8;
   const int tid = threadIdx.x, i = tid >> 3, u = tid & 7;
   const bool row = i < R;
@@ -333,6 +337,7 @@ __device__ void ridge_refine(SM& sm, int R, const float2* Gi, const float2* Glo,
     }
   }
   __syncthreads();
+  float prev = 0.f;
   for (int it = 0; it < iters; ++it) {
     unsigned* fl = flags + 2 * (it % 3);
     // r = h - G gamma, every product exact (two_prod), sums in float-float
@@ -387,22 +392,33 @@ __device__ void ridge_refine(SM& sm, int R, const float2* Gi, const float2* Glo,
     }
     __syncthreads();
     // float bits of non-negative floats order like unsigned integers
-    if (__uint_as_float(fl[0]) <= tol2 * __uint_as_float(fl[1])) break;
+    const float d2 = __uint_as_float(fl[0]);
+    if (d2 <= tol2 * __uint_as_float(fl[1])) return true;
+    if (slow2 > 0.f && it > 0 && d2 > slow2 * prev) return false;
+    prev = d2;
   }
+  return slow2 <= 0.f;
 }
 
 // The whole solve; G_hi in sm.Gf, h_hi in sm.h. Uses sm.GJa (64 x 72 float2 at most) for the
-// inverse and sm.Pk (136 float2) for the pivot rows and the sweep flags. Ends with a block
+// inverse and sm.Pk (136 float2) for the pivot rows and the sweep flags. With reuse > 0,
+// sm.GJa still holds the inverse of the previous MM iteration's system, which the factor
+// steps changed only a little: refinement with it as the preconditioner (up to `reuse`
+// sweeps, each required to shrink the correction at least tenfold) replaces the
+// Gauss-Jordan inverse, which is computed only when that does not converge. Ends with a block
 // barrier.
-__device__ void ridge_solve(SM& sm, int R, const float2* Glo, const float2* hlo, int iters, float tol2) {
+__device__ void ridge_solve(SM& sm, int R, const float2* Glo, const float2* hlo, int iters, float tol2,
+                            int reuse = 0) {
   if (R <= 32) {
+    if (reuse > 0 && ridge_refine<32>(sm, R, sm.GJa, Glo, hlo, reuse, tol2, 1e-2f)) return;
     gj_inverse_warps<32, TTS_GJ_ROWS>(sm.Gf, R, sm.GJa, sm.Pk);
     __syncthreads();
-    ridge_refine<32>(sm, R, sm.GJa, Glo, hlo, iters, tol2);
+    ridge_refine<32>(sm, R, sm.GJa, Glo, hlo, iters, tol2, 0.f);
   } else {
+    if (reuse > 0 && ridge_refine<64>(sm, R, sm.GJa, Glo, hlo, reuse, tol2, 1e-2f)) return;
     gj_inverse_warps<64, TTS_GJ_ROWS>(sm.Gf, R, sm.GJa, sm.Pk);
     __syncthreads();
-    ridge_refine<64>(sm, R, sm.GJa, Glo, hlo, iters, tol2);
+    ridge_refine<64>(sm, R, sm.GJa, Glo, hlo, iters, tol2, 0.f);
   }
 }
 
@@ -635,6 +651,15 @@ __device__ void step_ingest(const FrameParams& p, SM& sm, int cta) {
 // step A: ridge solve for gamma (S1), majorized A step (S2) on this CTA's rows, then the
 // partial sums of Ahat'_S and ||a'_r||^2 over those rows. OWN = outputs per thread.
 // ---------------------------------------------------------------------------------
+// Whether the ridge inverse stays in sm.GJa from one MM iteration to the next (the fused
+// launch, with the gamma-weighted products gM / gMA then in sm.GJb and B^H B in the twiddle
+// region of every CTA): the same answer in every CTA of the cluster.
+__device__ __forceinline__ bool keep_inverse(const FrameParams& p, int fused) {
+  const int per = (p.Nx + p.C - 1) / p.C;
+  const int least = max(0, min(per, p.Nx - (p.C - 1) * per));   // rows of A in the smallest slice
+  return fused && p.MC * least >= p.R * p.R;
+}
+
 // warp 0: alpha = sum_r |gamma_r|^2 w_r + rho and the MM step coefficients
 // c0 = lf abar / den, c1 = alpha / den, c2 = 1 / den (den = lf abar + alpha) into sm.fs,
 // alpha into sm.ds[0]
@@ -660,7 +685,7 @@ __device__ __forceinline__ void step_coefficients(const FrameParams& p, SM& sm, 
 }
 
 template <int OWN, bool LOADS_FIRST>
-__device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
+__device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k, int fused) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int Nx = p.Nx, R = p.R, C = p.C, MC = p.MC;
   const int s = sm.misc[0];
@@ -803,8 +828,13 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
   const bool ffk = p.ridge_ff_all || k == p.K - 1;   // readout sums of this system in float-float
   // float-float readout sums: refine until the corrections fall below ~1e-13 relative; FP32
   // readout sums (an MM iteration before the last with TTS_RIDGE_FF_LAST): one sweep takes the
-  // FP32 inverse's kappa u error to the accuracy of that system
-  ridge_solve(sm, R, Glo, hlo, ffk ? p.refine : 1, ffk ? 1e-26f : 1e-12f);
+  // FP32 inverse's kappa u error to the accuracy of that system. After the first MM iteration
+  // the previous iteration's inverse serves as the preconditioner (on the cine workloads
+  // I - Ginv_prev G has spectral radius ~4e-3 from the first to the second iteration and
+  // ~2e-4 from the second to the third), so the corrections shrink about a hundredfold per
+  // sweep: at most 4 sweeps to 1e-6 relative, 12 to 1e-13
+  const bool keep = keep_inverse(p, fused);
+  ridge_solve(sm, R, Glo, hlo, ffk ? p.refine : 1, ffk ? 1e-26f : 1e-12f, keep && k > 0 ? (ffk ? 12 : 4) : 0);
   if (!mb_tw) {
     for (int e = tid; e < RR; e += nth) MBt[e] = p.MB[e];
     __syncthreads();
@@ -818,7 +848,7 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k) {
                                   (double)sm.gam[r].y + (double)sm.glo[r].y);
     }
   // gM[q][r] = gamma_q (B^H B)[r][q]
-  float2* gM = sm.GJa;
+  float2* gM = keep ? sm.GJb : sm.GJa;
   for (int e = tid; e < RR; e += nth) {
     const int q = e / R, r = e - q * R;
     gM[e] = cmul(sm.gam[q], MBt[r * R + q]);
@@ -1060,7 +1090,7 @@ __device__ void reduce_A_full(const FrameParams& p, SM& sm, int cta, int dst, fl
 // step B: majorized B step (S2) on this CTA's rows, then partials of B^H B and P
 // ---------------------------------------------------------------------------------
 template <int OWN>
-__device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) {
+__device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last, int fused) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int Ny = p.Ny, R = p.R, C = p.C, MC = p.MC;
   const int s = sm.misc[0];
@@ -1122,7 +1152,7 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last) 
     __syncthreads();
   }
   // gMA[q][r] = gamma_q MA[r][q]
-  float2* gMA = sm.GJa;
+  float2* gMA = keep_inverse(p, fused) ? sm.GJb : sm.GJa;
 #pragma unroll
   for (int o = 0; o < OWN; ++o) {
     const int e = tid + o * nth;
@@ -1288,9 +1318,9 @@ __device__ __forceinline__ void frame_run(const FrameParams& p, unsigned char* s
       continue;
     }
     const int k = (step - 3) / 4, sub = (step - 3) % 4;
-    if (sub == 0) step_solve_A<OWN, LOADS_FIRST>(p, sm, cta, k);
+    if (sub == 0) step_solve_A<OWN, LOADS_FIRST>(p, sm, cta, k, fused);
     else if (sub == 1) reduce_A_rows(p, sm, cta, (k + 1) & 1, k + 1 < p.K);
-    else if (sub == 2) step_B<OWN>(p, sm, cta, k, k == p.K - 1);
+    else if (sub == 2) step_B<OWN>(p, sm, cta, k, k == p.K - 1, fused);
     else reduce_sums(p, sm, cta, !merged);
     __syncthreads();
   }
