@@ -871,16 +871,49 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k, int f
       }
     fill_twiddles(p, sm, TW, m0, mc, as.lo, na);
     __syncthreads();
-    for (int e = tid; e < mc * R; e += nth) {
-      const int mm = e / R, r = e - mm * R;
-      float2 a0 = PC[e], a1 = make_float2(0.f, 0.f);
+    // with R dividing the block, every output of a thread (of Q and of Theta conj(B)) has column
+    // tid % R: gM[q][r] and Q[m][r] are loaded once for all of them and the outputs' sums run as
+    // independent chains (the same arithmetic per output as the general loops)
+    const bool shared_col = OWN <= 4 && nth % R == 0 && mc * R <= OWN * nth;
+    if (shared_col) {
+      const int cc = tid % R, q0 = tid / R, step = nth / R;
+      float2 a0[OWN], a1[OWN];
+      int mr[OWN];
+#pragma unroll
+      for (int o = 0; o < OWN; ++o) {
+        mr[o] = q0 + o * step < mc ? q0 + o * step : 0;
+        a0[o] = PC[mr[o] * R + cc];
+        a1[o] = make_float2(0.f, 0.f);
+      }
       int q = 0;
       for (; q + 1 < R; q += 2) {
-        cfms(a0, AH[mm * R + q], gM[q * R + r]);
-        cfms(a1, AH[mm * R + q + 1], gM[(q + 1) * R + r]);
+        const float2 g0 = gM[q * R + cc], g1 = gM[(q + 1) * R + cc];
+#pragma unroll
+        for (int o = 0; o < OWN; ++o) {
+          cfms(a0[o], AH[mr[o] * R + q], g0);
+          cfms(a1[o], AH[mr[o] * R + q + 1], g1);
+        }
       }
-      if (q < R) cfms(a0, AH[mm * R + q], gM[q * R + r]);
-      QC[e] = cadd(a0, a1);
+      if (q < R) {
+        const float2 g0 = gM[q * R + cc];
+#pragma unroll
+        for (int o = 0; o < OWN; ++o) cfms(a0[o], AH[mr[o] * R + q], g0);
+      }
+#pragma unroll
+      for (int o = 0; o < OWN; ++o)
+        if (q0 + o * step < mc) QC[(q0 + o * step) * R + cc] = cadd(a0[o], a1[o]);
+    } else {
+      for (int e = tid; e < mc * R; e += nth) {
+        const int mm = e / R, r = e - mm * R;
+        float2 a0 = PC[e], a1 = make_float2(0.f, 0.f);
+        int q = 0;
+        for (; q + 1 < R; q += 2) {
+          cfms(a0, AH[mm * R + q], gM[q * R + r]);
+          cfms(a1, AH[mm * R + q + 1], gM[(q + 1) * R + r]);
+        }
+        if (q < R) cfms(a0, AH[mm * R + q], gM[q * R + r]);
+        QC[e] = cadd(a0, a1);
+      }
     }
     __syncthreads();
     int ir[OWN], ic[OWN];
@@ -891,16 +924,33 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k, int f
       ic[o] = v ? ocol[o] : 0;
     }
     int mm = 0;
-    for (; mm + 1 < mc; mm += 2) {
+    if (OWN <= 4 && nth % R == 0) {
+      const int cc = tid % R;
+      for (; mm + 1 < mc; mm += 2) {
+        const float2 qa = QC[mm * R + cc], qb = QC[(mm + 1) * R + cc];
 #pragma unroll
-      for (int o = 0; o < OWN; ++o) {
-        cfmac(t0[o], TW[mm * na + ir[o]], QC[mm * R + ic[o]]);
-        cfmac(t1[o], TW[(mm + 1) * na + ir[o]], QC[(mm + 1) * R + ic[o]]);
+        for (int o = 0; o < OWN; ++o) {
+          cfmac(t0[o], TW[mm * na + ir[o]], qa);
+          cfmac(t1[o], TW[(mm + 1) * na + ir[o]], qb);
+        }
       }
-    }
-    if (mm < mc) {
+      if (mm < mc) {
+        const float2 qa = QC[mm * R + cc];
 #pragma unroll
-      for (int o = 0; o < OWN; ++o) cfmac(t0[o], TW[mm * na + ir[o]], QC[mm * R + ic[o]]);
+        for (int o = 0; o < OWN; ++o) cfmac(t0[o], TW[mm * na + ir[o]], qa);
+      }
+    } else {
+      for (; mm + 1 < mc; mm += 2) {
+#pragma unroll
+        for (int o = 0; o < OWN; ++o) {
+          cfmac(t0[o], TW[mm * na + ir[o]], QC[mm * R + ic[o]]);
+          cfmac(t1[o], TW[(mm + 1) * na + ir[o]], QC[(mm + 1) * R + ic[o]]);
+        }
+      }
+      if (mm < mc) {
+#pragma unroll
+        for (int o = 0; o < OWN; ++o) cfmac(t0[o], TW[mm * na + ir[o]], QC[mm * R + ic[o]]);
+      }
     }
     __syncthreads();
   }
@@ -1142,11 +1192,25 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last, 
       ur[o] = vu ? ocol[o] : 0;
     }
     const float2* AHm = own_ah ? AR : AH;
-    for (int mm = 0; mm < mc; ++mm) {
+    if (OWN <= 4 && nth % R == 0) {
+      // every output of this thread has column tid % R (R divides the block): that column's
+      // entry of Ahat is loaded once per m for all of them (same arithmetic as below)
+      const int cc = tid % R;
+      for (int mm = 0; mm < mc; ++mm) {
+        const float2 ac = AHm[mm * R + cc];
 #pragma unroll
-      for (int o = 0; o < OWN; ++o) {
-        cfmac(ma[o], AHm[mm * R + mr[o]], AHm[mm * R + mq[o]]);
-        cfmac(u[o], AHm[mm * R + ur[o]], YB[mm * nb + uj[o]]);
+        for (int o = 0; o < OWN; ++o) {
+          cfmac(ma[o], AHm[mm * R + mr[o]], ac);
+          cfmac(u[o], ac, YB[mm * nb + uj[o]]);
+        }
+      }
+    } else {
+      for (int mm = 0; mm < mc; ++mm) {
+#pragma unroll
+        for (int o = 0; o < OWN; ++o) {
+          cfmac(ma[o], AHm[mm * R + mr[o]], AHm[mm * R + mq[o]]);
+          cfmac(u[o], AHm[mm * R + ur[o]], YB[mm * nb + uj[o]]);
+        }
       }
     }
     __syncthreads();
@@ -1164,23 +1228,58 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last, 
   const float c0 = sm.fs[0], c1 = sm.fs[1], c2 = sm.fs[2], frho = sm.fs[3];
   // B step: T_B = U - B diag(gamma) MA^T, grad = rho B - T_B diag(conj gamma)
   float2 nbv[OWN];
+  // the majorized step of output o from its T_B entry tb
+  auto bstep = [&](int o, float2 tb) {
+    const int e = tid + o * nth, r = ocol[o];
+    const float2 b = sm.B[e], b0 = sm.B0[e];
+    const float2 grad = csub(cscale(b, frho), cmul(tb, cconj(sm.gam[r])));
+    nbv[o].x = fmaf(-c2, grad.x, fmaf(c1, b.x, c0 * b0.x));
+    nbv[o].y = fmaf(-c2, grad.y, fmaf(c1, b.y, c0 * b0.y));
+  };
+  if (OWN <= 4 && nth % R == 0) {
+    // column tid % R for every output: gMA[q][r] loaded once per q for all of them, the
+    // sums of all outputs as independent chains (same arithmetic as below)
+    const int cc = tid % R;
+    float2 t0[OWN], t1[OWN];
+    int jr[OWN];
 #pragma unroll
-  for (int o = 0; o < OWN; ++o) {
-    const int e = tid + o * nth;
-    if (e < NO) {
-      const int jl = orow[o], r = ocol[o];
-      float2 tb0 = u[o], tb1 = make_float2(0.f, 0.f);
-      int q = 0;
-      for (; q + 1 < R; q += 2) {
-        cfms(tb0, sm.B[jl * R + q], gMA[q * R + r]);
-        cfms(tb1, sm.B[jl * R + q + 1], gMA[(q + 1) * R + r]);
+    for (int o = 0; o < OWN; ++o) {
+      t0[o] = u[o];
+      t1[o] = make_float2(0.f, 0.f);
+      jr[o] = tid + o * nth < NO ? orow[o] : 0;
+    }
+    int q = 0;
+    for (; q + 1 < R; q += 2) {
+      const float2 g0 = gMA[q * R + cc], g1 = gMA[(q + 1) * R + cc];
+#pragma unroll
+      for (int o = 0; o < OWN; ++o) {
+        cfms(t0[o], sm.B[jr[o] * R + q], g0);
+        cfms(t1[o], sm.B[jr[o] * R + q + 1], g1);
       }
-      if (q < R) cfms(tb0, sm.B[jl * R + q], gMA[q * R + r]);
-      const float2 tb = cadd(tb0, tb1);
-      const float2 b = sm.B[e], b0 = sm.B0[e];
-      const float2 grad = csub(cscale(b, frho), cmul(tb, cconj(sm.gam[r])));
-      nbv[o].x = fmaf(-c2, grad.x, fmaf(c1, b.x, c0 * b0.x));
-      nbv[o].y = fmaf(-c2, grad.y, fmaf(c1, b.y, c0 * b0.y));
+    }
+    if (q < R) {
+      const float2 g0 = gMA[q * R + cc];
+#pragma unroll
+      for (int o = 0; o < OWN; ++o) cfms(t0[o], sm.B[jr[o] * R + q], g0);
+    }
+#pragma unroll
+    for (int o = 0; o < OWN; ++o)
+      if (tid + o * nth < NO) bstep(o, cadd(t0[o], t1[o]));
+  } else {
+#pragma unroll
+    for (int o = 0; o < OWN; ++o) {
+      const int e = tid + o * nth;
+      if (e < NO) {
+        const int jl = orow[o], r = ocol[o];
+        float2 tb0 = u[o], tb1 = make_float2(0.f, 0.f);
+        int q = 0;
+        for (; q + 1 < R; q += 2) {
+          cfms(tb0, sm.B[jl * R + q], gMA[q * R + r]);
+          cfms(tb1, sm.B[jl * R + q + 1], gMA[(q + 1) * R + r]);
+        }
+        if (q < R) cfms(tb0, sm.B[jl * R + q], gMA[q * R + r]);
+        bstep(o, cadd(tb0, tb1));
+      }
     }
   }
   __syncthreads();
