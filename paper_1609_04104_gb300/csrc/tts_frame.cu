@@ -120,8 +120,10 @@ __device__ __forceinline__ void ff_add_ff(float& hi, float& lo, float h2, float 
 }
 
 // Float-float accumulation of sums of products of FP32 numbers (the ridge system's sums):
-// every product exact (two_prod), every addition error-free (two_sum), the low part
-// renormalised after each pair of products, so the sum carries about 48 significant bits.
+// every product exact (two_prod), every addition to the high part error-free (two_sum), the
+// product and addition errors summed in the low part (the compensated dot product of Ogita,
+// Rump and Oishi, 2005: the result is as accurate as if computed with twice the working
+// precision); the pair is renormalised where it is read (cff_pack, ff_add_ff).
 // hi + lo += a1 b1 + a2 b2
 __device__ __forceinline__ void ff_acc2(float& hi, float& lo, float a1, float b1, float a2, float b2) {
   float p, pe, s, e;
@@ -131,7 +133,6 @@ __device__ __forceinline__ void ff_acc2(float& hi, float& lo, float a1, float b1
   two_prod(a2, b2, p, pe);
   two_sum(s, p, hi, e);
   lo = lo + (e + pe);
-  fast_two_sum(hi, lo, hi, lo);
 }
 // complex float-float accumulator (re: rh + rl, im: ih + il)
 struct CFF {
@@ -454,16 +455,39 @@ __device__ void partials_A(const FrameParams& p, SM& sm, int cta, float2* TW, bo
     const int mc = min(MC, s - m0);
     if (!(tw_ready && s <= MC)) fill_twiddles(p, sm, TW, m0, mc, as.lo, na);
     __syncthreads();
-    for (int e = tid; e < mc * R; e += nth) {
-      const int mm = e / R, r = e - mm * R;
-      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+    if (nth % R == 0 && mc * R <= 2 * nth) {
+      // the thread's (at most two) outputs share the column r = tid % R: A[n][r] is loaded
+      // once for both, the two sums run as independent chains (arithmetic as below)
+      const int cc = tid % R, q0 = tid / R, q1 = q0 + nth / R;
+      const int ma = q0 < mc ? q0 : 0, mb = q1 < mc ? q1 : 0;
+      float2 x0 = make_float2(0.f, 0.f), x1 = x0, y0 = x0, y1 = x0;
       int nl = 0;
       for (; nl + 1 < na; nl += 2) {
-        cfma(a0, TW[mm * na + nl], sm.A[nl * R + r]);
-        cfma(a1, TW[mm * na + nl + 1], sm.A[(nl + 1) * R + r]);
+        const float2 av = sm.A[nl * R + cc], aw = sm.A[(nl + 1) * R + cc];
+        cfma(x0, TW[ma * na + nl], av);
+        cfma(x1, TW[ma * na + nl + 1], aw);
+        cfma(y0, TW[mb * na + nl], av);
+        cfma(y1, TW[mb * na + nl + 1], aw);
       }
-      if (nl < na) cfma(a0, TW[mm * na + nl], sm.A[nl * R + r]);
-      part[(m0 + mm) * R + r] = cscale(cadd(a0, a1), p.isx);
+      if (nl < na) {
+        const float2 av = sm.A[nl * R + cc];
+        cfma(x0, TW[ma * na + nl], av);
+        cfma(y0, TW[mb * na + nl], av);
+      }
+      if (q0 < mc) part[(m0 + q0) * R + cc] = cscale(cadd(x0, x1), p.isx);
+      if (q1 < mc) part[(m0 + q1) * R + cc] = cscale(cadd(y0, y1), p.isx);
+    } else {
+      for (int e = tid; e < mc * R; e += nth) {
+        const int mm = e / R, r = e - mm * R;
+        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+        int nl = 0;
+        for (; nl + 1 < na; nl += 2) {
+          cfma(a0, TW[mm * na + nl], sm.A[nl * R + r]);
+          cfma(a1, TW[mm * na + nl + 1], sm.A[(nl + 1) * R + r]);
+        }
+        if (nl < na) cfma(a0, TW[mm * na + nl], sm.A[nl * R + r]);
+        part[(m0 + mm) * R + r] = cscale(cadd(a0, a1), p.isx);
+      }
     }
     __syncthreads();
   }
@@ -512,7 +536,11 @@ __device__ void partials_B(const FrameParams& p, SM& sm, int cta, bool do_mb, bo
     float4* pmb = p.partMB + (size_t)cta * RR;
     if (ff) {
       const int RT = R * (R + 1) / 2;
-      for (int idx = tid; idx < RT; idx += nth) {
+      // whole blocks of nth pairs one thread a pair; the pairs of a last partial block (16 at
+      // R = 32) one warp a pair, its rows over the lanes and the lanes' sums combined in
+      // float-float by shuffles, so that a few threads do not run a whole pair alone
+      const int full = RT - RT % nth;
+      for (int idx = tid; idx < full; idx += nth) {
         int q, r;
         tri_pair(idx, R, q, r);
         CFF acc = cff_zero();
@@ -520,6 +548,25 @@ __device__ void partials_B(const FrameParams& p, SM& sm, int cta, bool do_mb, bo
         const float4 v = cff_pack(acc);
         pmb[q * R + r] = v;
         if (q != r) pmb[r * R + q] = make_float4(v.x, -v.y, v.z, -v.w);
+      }
+      const int warp = tid >> 5, lane = tid & 31;
+      for (int idx = full + warp; idx < RT; idx += nth >> 5) {
+        int q, r;
+        tri_pair(idx, R, q, r);
+        CFF acc = cff_zero();
+        for (int jl = lane; jl < nb; jl += 32) cff_macc(acc, sm.B[jl * R + q], sm.B[jl * R + r]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float a = __shfl_xor_sync(0xffffffffu, acc.rh, o), b = __shfl_xor_sync(0xffffffffu, acc.rl, o);
+          const float c = __shfl_xor_sync(0xffffffffu, acc.ih, o), d = __shfl_xor_sync(0xffffffffu, acc.il, o);
+          ff_add_ff(acc.rh, acc.rl, a, b);
+          ff_add_ff(acc.ih, acc.il, c, d);
+        }
+        if (lane == 0) {
+          const float4 v = cff_pack(acc);
+          pmb[q * R + r] = v;
+          if (q != r) pmb[r * R + q] = make_float4(v.x, -v.y, v.z, -v.w);
+        }
       }
     } else {
 #pragma unroll
@@ -1384,8 +1431,10 @@ __device__ __forceinline__ void frame_run(const FrameParams& p, unsigned char* s
       if (fused) cluster.sync();
       else __syncthreads();
     }
-    if (step > 0) {
-      // the frame is rejected when any CTA saw a non-finite input sample
+    if (step > 0 && (step == 1 || step == step_begin)) {
+      // the frame is rejected when any CTA saw a non-finite input sample (the flags are set by
+      // the ingest step only, so one look after it suffices in a fused launch; a launch that
+      // starts later in the frame looks again)
       int bad = 0;
       for (int c = 0; c < p.C; ++c) bad |= ((volatile int*)p.status)[1 + c];
       if (bad) {
