@@ -317,7 +317,7 @@ def run_tts(args, rank, world):
 
     # end to end through the C ABI with host buffers: per frame the drawn lines come back to
     # the host (the scanner needs them before it acquires the frame), the host frame goes in
-    # (the library gathers the acquired rows into mapped pinned memory the kernels read),
+    # (page-locked; the kernels read the acquired rows from it in place, TTS_HOST_PINNED),
     # and the image comes back to the host asynchronously on a copy stream (its copy overlaps
     # the next line draw and frame; every image is on the host when the step ends)
     e2e = None
@@ -338,12 +338,12 @@ def run_tts(args, rank, world):
             with torch.cuda.stream(stream):
                 for t in range(T):
                     if t < w.warmup_frames:
-                        trk.push_frame(Yp[t], full, full_frame=True)
+                        trk.push_frame(Yp[t], full, full_frame=True, pinned=True)
                         hb += w.Nx * w.Ny * 8 + w.Nx
                     else:
                         trk.next_mask(w.rate, seed, out=mh)
                         db += w.Nx
-                        trk.push_frame(Yp[t], None, full_frame=True)   # the lines just drawn
+                        trk.push_frame(Yp[t], None, full_frame=True, pinned=True)   # the lines just drawn
                         hb += int(mh.sum()) * w.Ny * 8
                     tts.tts_image(trk.h, t, dimg[t])
                     img_ready[t].record(stream)
@@ -357,8 +357,8 @@ def run_tts(args, rank, world):
                 h2d, d2h = hb, db
         e2e = {"value": T * world / float(np.mean(e2e_s)), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h,
-               "note": "host lines back every frame (synchronous); host frames in (the acquired rows "
-                       "gathered by the library into mapped pinned memory the kernels read); images out "
+               "note": "host lines back every frame (synchronous); host frames in (page-locked, the "
+                       "acquired rows read by the kernels in place, TTS_HOST_PINNED); images out "
                        "on a copy stream"}
 
     # roofline of the dominant kernel (the frame kernel, timed on the sampled informative

@@ -61,6 +61,16 @@ enum {
 /* tts_push_frame only: y_rows points to a whole Nx x Ny k-space frame; only the rows
  * the mask selects are read (a scanner buffer that holds the full Cartesian grid). */
 #define TTS_FULL_FRAME 2
+/* tts_push_frame only, host y_rows: the frame is in page-locked host memory (cudaHostAlloc,
+ * cudaHostRegister or a pinned torch tensor) that the caller leaves unchanged until the
+ * frame has been processed (the next synchronising call, or an event recorded on the
+ * handle's stream after the call). The kernels then read the acquired rows from it in place
+ * instead of the host gathering them into staging memory first, which takes that copy off
+ * the path between the line draw and the frame update; a NaN or Inf is then found on the
+ * device and reported by the next synchronising call (TTS_ENONFINITE), as with
+ * TTS_DEVICE_PTRS. Memory that is not page-locked gives TTS_EINVAL. Ignored with the
+ * tensor-core row transform and by the multi-coil tracker, which gather as without it. */
+#define TTS_HOST_PINNED 4
 
 /* Sampling policy of tts_next_mask (S0 of Alg. 5). */
 enum {

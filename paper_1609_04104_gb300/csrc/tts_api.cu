@@ -275,6 +275,20 @@ int handle_stage_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line
     int s = 0;
     for (int i = 0; i < Nx; ++i) s += m[i] != 0;
     if (s == 0) return fail(TTS_EINVAL, "the line mask selects no line%s");
+    if (pinned_gather && (flags & TTS_HOST_PINNED) && h->cfg.row_dft == TTS_ROWDFT_FFT) {
+      // page-locked caller memory: the kernels read the acquired rows in place
+      cudaPointerAttributes a;
+      if (cudaPointerGetAttributes(&a, y_rows) != cudaSuccess || a.type != cudaMemoryTypeHost ||
+          a.devicePointer == nullptr) {
+        cudaGetLastError();
+        return fail(TTS_EINVAL, "TTS_HOST_PINNED: y_rows is not page-locked host memory%s");
+      }
+      if (line_mask) CK(cudaMemcpyAsync(h->dmask_push, m, Nx, cudaMemcpyHostToDevice, h->stream));
+      p.mask = line_mask ? h->dmask_push : h->dmask_next;
+      p.yrows = (const float2*)a.devicePointer;
+      *pout = p;
+      return TTS_OK;
+    }
     if (pinned_gather) {
       float2* staged = nullptr;
       const int rg = gather_host_rows(h, (const float*)y_rows, m, (flags & TTS_FULL_FRAME) != 0, &staged);

@@ -24,6 +24,7 @@ TTS_DFT_BF16X3, TTS_DFT_BF16 = 0, 1
 TTS_ROWDFT_FFT, TTS_ROWDFT_BF16X3, TTS_ROWDFT_BF16 = 0, 1, 2
 TTS_DEVICE_PTRS = 1
 TTS_FULL_FRAME = 2
+TTS_HOST_PINNED = 4
 TTS_POLICY_UNIFORM, TTS_POLICY_VARDENS, TTS_POLICY_INFORMATIVE = 0, 1, 2
 TTS_UPDATE_GAUSS_SEIDEL, TTS_UPDATE_JACOBI = 0, 1
 TTS_LAUNCH_FUSED, TTS_LAUNCH_PHASES = 0, 1
@@ -273,11 +274,12 @@ def tts_set_coil_maps(h, maps) -> None:
     _check(load().tts_set_coil_maps(h, pm, maps.shape[0], fm))
 
 
-def tts_push_frame(h, y_rows, line_mask=None, full_frame=False) -> None:
+def tts_push_frame(h, y_rows, line_mask=None, full_frame=False, pinned=False) -> None:
     py, fy = _ptr(y_rows, np.complex64)
     pm, fm = _ptr(line_mask, np.uint8)
     flags = _flags(fy, fm if line_mask is not None else None)
-    _check(load().tts_push_frame(h, py, pm, flags | (TTS_FULL_FRAME if full_frame else 0)))
+    flags |= (TTS_FULL_FRAME if full_frame else 0) | (TTS_HOST_PINNED if pinned and not fy else 0)
+    _check(load().tts_push_frame(h, py, pm, flags))
 
 
 def tts_image(h, t, out) -> None:
@@ -627,12 +629,14 @@ class Tracker:
     def set_coil_maps(self, maps):
         tts_set_coil_maps(self.h, np.ascontiguousarray(maps, np.complex64) if isinstance(maps, np.ndarray) else maps)
 
-    def push_frame(self, y_rows, line_mask=None, full_frame=False):
-        if isinstance(y_rows, np.ndarray):
+    def push_frame(self, y_rows, line_mask=None, full_frame=False, pinned=False):
+        """pinned: y_rows is a numpy view of page-locked memory that stays unchanged until the
+        frame has been processed; the kernels read it in place (TTS_HOST_PINNED)."""
+        if isinstance(y_rows, np.ndarray) and not pinned:
             y_rows = np.ascontiguousarray(y_rows, np.complex64)
         if isinstance(line_mask, np.ndarray):
             line_mask = np.ascontiguousarray(line_mask, np.uint8)
-        tts_push_frame(self.h, y_rows, line_mask, full_frame)
+        tts_push_frame(self.h, y_rows, line_mask, full_frame, pinned)
 
     def image(self, t=None, out=None):
         if t is None:
