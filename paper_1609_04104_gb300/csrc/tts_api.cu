@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <chrono>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -250,6 +251,16 @@ static int gather_host_rows(tts_handle* h, const float* y, const uint8_t* m, boo
   if (bad) return fail(TTS_ENONFINITE, "frame holds NaN or Inf; not applied%s");
   *out = h->hstage[b];
   return TTS_OK;
+}
+
+// Poll a word in mapped host memory until it reads v (acquire), for at most ~10 s; false if
+// it never did.
+static bool wait_word(unsigned int* w, unsigned int v) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (unsigned int i = 0;; ++i) {
+    if (__atomic_load_n(w, __ATOMIC_ACQUIRE) == v) return true;
+    if ((i & 4095u) == 4095u && std::chrono::steady_clock::now() - t0 > std::chrono::seconds(10)) return false;
+  }
 }
 
 int handle_stage_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line_mask, int flags, FrameParams* pout,
@@ -555,10 +566,14 @@ int tts_next_mask(tts_handle* h, double rate, uint64_t seed, uint8_t* line_mask_
   if (host && !h->mask_map) {
     uint8_t* m = nullptr;
     void* d = nullptr;
-    if (cudaHostAlloc((void**)&m, Nx, cudaHostAllocMapped) == cudaSuccess) {
+    const size_t at = ((size_t)Nx + 63) & ~(size_t)63;   // the completion word after the mask
+    if (cudaHostAlloc((void**)&m, at + 64, cudaHostAllocMapped) == cudaSuccess) {
       if (cudaHostGetDevicePointer(&d, m, 0) == cudaSuccess) {
         h->mask_map = m;
         h->mask_map_dev = (uint8_t*)d;
+        h->draw_done = (unsigned int*)(m + at);
+        h->draw_done_dev = (unsigned int*)((uint8_t*)d + at);
+        *h->draw_done = h->draw_seq;
       } else {
         cudaFreeHost(m);
       }
@@ -566,16 +581,23 @@ int tts_next_mask(tts_handle* h, double rate, uint64_t seed, uint8_t* line_mask_
     cudaGetLastError();   // without mapped memory the mask is copied back instead
   }
   uint8_t* out2 = host ? h->mask_map_dev : line_mask_out;
+  const unsigned int seq = h->draw_seq + 1;
   int rc = launch_sampler(h->fp.A, Nx, h->cfg.Ny, h->cfg.R, nullptr, h->dp, h->cfg.policy, h->cfg.vd_alpha, k_lines,
                           h->cfg.central_lines, seed, handle_draw_counter(h), h->cfg.with_replacement, h->fp.Wx,
-                          h->dmask_next, out2, h->stream, h->cfg.kspace);
+                          h->dmask_next, out2, h->stream, h->cfg.kspace, host ? h->draw_done_dev : nullptr, seq);
   if (rc != TTS_OK) return fail(rc, "sampler kernel launch failed%s");
   h->have_next = true;
   if (flags & TTS_DEVICE_PTRS) {
     h->next_on_host = false;
   } else {
     if (!h->mask_map) CK(cudaMemcpyAsync(h->next_host.data(), h->dmask_next, Nx, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    // the mask is on the host once the sampler has set its completion word: poll that word
+    // (the scanner waits on these lines) instead of synchronising the stream; a stream
+    // synchronisation after a bounded wait reports any error of the work before it
+    if (!(h->mask_map && wait_word(h->draw_done, seq))) CK(cudaStreamSynchronize(h->stream));
+    if (h->mask_map && __atomic_load_n(h->draw_done, __ATOMIC_ACQUIRE) != seq)
+      return fail(TTS_ECUDA, "the line draw did not complete%s");
+    h->draw_seq = seq;
     if (h->mask_map) memcpy(h->next_host.data(), h->mask_map, Nx);
     memcpy(line_mask_out, h->next_host.data(), Nx);
     h->next_on_host = true;

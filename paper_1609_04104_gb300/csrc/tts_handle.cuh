@@ -42,6 +42,11 @@ struct tts_handle {
   // (mask_map on the host, mask_map_dev its device address), so no copy follows the draw
   uint8_t* mask_map = nullptr;
   uint8_t* mask_map_dev = nullptr;
+  // completion word of the last draw in the same mapped allocation (after the mask, 64-byte
+  // aligned): the sampler sets it to draw_seq once the mask is written, the host polls it
+  unsigned int* draw_done = nullptr;
+  unsigned int* draw_done_dev = nullptr;
+  unsigned int draw_seq = 0;
   // test hook (tts_test_withhold_row_transform): the next row transform withholds this K'
   // chunk's arrival and waits at most test_wait_cycles; -1: none
   int test_withhold = -1;

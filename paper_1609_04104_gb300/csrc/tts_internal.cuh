@@ -480,6 +480,8 @@ struct SamplerJob {
   uint8_t* mask_out2;   // optional second copy, or NULL
   int fft_cols;         // columns of A transformed together
   int no_fft;           // scores on the rows of A itself (k-space factor)
+  unsigned int* done;   // optional word set to done_value once the masks are written (mapped memory)
+  unsigned int done_value;
 };
 
 // One image X = A diag(gamma) B^T as a job of a batched launch: tiles [tile0, tile0 + tiles).
@@ -511,7 +513,8 @@ int launch_image(const float2* A, const float2* B, const float2* gamma, float2* 
                  cudaStream_t st);
 int launch_sampler(const float2* A, int Nx, int Ny, int R, const double* p_in, double* p_out, int policy,
                    double vd_alpha, int k_lines, int central, uint64_t seed, uint64_t ctr, int with_replacement,
-                   const float2* Wx, uint8_t* mask_out, uint8_t* mask_out2, cudaStream_t st, int no_fft = 0);
+                   const float2* Wx, uint8_t* mask_out, uint8_t* mask_out2, cudaStream_t st, int no_fft = 0,
+                   unsigned int* done = nullptr, unsigned int done_value = 0);
 void tts_internal_set_error(const char* msg);   // message returned by tts_last_error
 int launch_fft2d(const float2* in, float2* out, int batch, int Nx, int Ny, int inverse, const float2* Wx,
                  const float2* Wy, float2* scratch, cudaStream_t st);

@@ -455,6 +455,13 @@ __global__ void __launch_bounds__(SAMPLER_THREADS) sampler_kernel(SamplerJob job
   pdl_release();
   pdl_wait();
   sampler_run(job, smem_raw);
+  if (job.done) {
+    // the masks are in memory the host polls: every thread's writes are made visible system
+    // wide before the completion word is set
+    __threadfence_system();
+    __syncthreads();
+    if (threadIdx.x == 0) *(volatile unsigned int*)job.done = job.done_value;
+  }
 }
 
 // One CTA per job; the number of jobs is read from device memory (*n), so a captured
@@ -620,6 +627,8 @@ SamplerJob sampler_job(const float2* A, int Nx, int Ny, int R, const double* p_i
   j.mask_out2 = mask_out2;
   j.fft_cols = max(1, min(min(R, 64), 8192 / max(Nx, 1)));
   j.no_fft = 0;
+  j.done = nullptr;
+  j.done_value = 0;
   return j;
 }
 
@@ -644,10 +653,13 @@ size_t sampler_smem_max();
 
 int launch_sampler(const float2* A, int Nx, int Ny, int R, const double* p_in, double* p_out, int policy,
                    double vd_alpha, int k_lines, int central, uint64_t seed, uint64_t ctr, int with_replacement,
-                   const float2* Wx, uint8_t* mask_out, uint8_t* mask_out2, cudaStream_t st, int no_fft) {
+                   const float2* Wx, uint8_t* mask_out, uint8_t* mask_out2, cudaStream_t st, int no_fft,
+                   unsigned int* done_word, unsigned int done_value) {
   SamplerJob j = sampler_job(A, Nx, Ny, R, p_in, p_out, policy, vd_alpha, k_lines, central, seed, ctr,
                              with_replacement, Wx, mask_out, mask_out2);
   j.no_fft = no_fft;
+  j.done = done_word;
+  j.done_value = done_value;
   const size_t smem = sampler_smem(Nx, j.fft_cols);
   static PerDevice attrs;
   int done = 0;
