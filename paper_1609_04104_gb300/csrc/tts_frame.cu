@@ -444,6 +444,7 @@ __device__ __forceinline__ void fill_twiddles(const FrameParams& p, SM& sm, floa
 // Ahat_S[m][r] = sum over this CTA's rows n of F[S_m, n] A[n][r] / sqrt(Nx), and ||a_r||^2;
 // TW is chunk scratch of MC x (rows of A). With tw_ready the twiddles of a single chunk
 // are already in TW.
+template <bool SC>
 __device__ void partials_A(const FrameParams& p, SM& sm, int cta, float2* TW, bool tw_ready) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int Nx = p.Nx, R = p.R, MC = p.MC;
@@ -455,7 +456,7 @@ __device__ void partials_A(const FrameParams& p, SM& sm, int cta, float2* TW, bo
     const int mc = min(MC, s - m0);
     if (!(tw_ready && s <= MC)) fill_twiddles(p, sm, TW, m0, mc, as.lo, na);
     __syncthreads();
-    if (nth % R == 0 && mc * R <= 2 * nth) {
+    if (SC || (nth % R == 0 && mc * R <= 2 * nth)) {
       // the thread's (at most two) outputs share the column r = tid % R: A[n][r] is loaded
       // once for both, the two sums run as independent chains (arithmetic as below)
       const int cc = tid % R, q0 = tid / R, q1 = q0 + nth / R;
@@ -622,7 +623,7 @@ __device__ void partials_B(const FrameParams& p, SM& sm, int cta, bool do_mb, bo
 // step 0: ingest the frame: inverse row transforms of this CTA's slice of S (Yt), the
 // anchors A[t-1], B[t-1], and partial sums of Ahat_S, ||a||^2 and B^H B over this CTA's rows
 // ---------------------------------------------------------------------------------
-template <int OWN>
+template <int OWN, bool SC>
 __device__ void step_ingest(const FrameParams& p, SM& sm, int cta) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int Nx = p.Nx, Ny = p.Ny, R = p.R, C = p.C;
@@ -678,7 +679,7 @@ __device__ void step_ingest(const FrameParams& p, SM& sm, int cta) {
   const Slice as = slice_of(Nx, C, cta), bs = slice_of(Ny, C, cta);
   for (int e = as.lo * R + tid; e < as.hi * R; e += nth) p.A0[e] = p.A[e];
   for (int e = bs.lo * R + tid; e < bs.hi * R; e += nth) p.B0[e] = p.B[e];
-  partials_A(p, sm, cta, sm.chunk, false);
+  partials_A<SC>(p, sm, cta, sm.chunk, false);
   partials_B<OWN>(p, sm, cta, true, false, p.ridge_ff_all || p.K == 1);
   __syncthreads();
   if (tid == 0) p.status[1 + cta] = sm.misc[1];
@@ -731,7 +732,7 @@ __device__ __forceinline__ void step_coefficients(const FrameParams& p, SM& sm, 
   }
 }
 
-template <int OWN, bool LOADS_FIRST>
+template <int OWN, bool LOADS_FIRST, bool SC>
 __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k, int fused) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int Nx = p.Nx, R = p.R, C = p.C, MC = p.MC;
@@ -921,7 +922,7 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k, int f
     // with R dividing the block, every output of a thread (of Q and of Theta conj(B)) has column
     // tid % R: gM[q][r] and Q[m][r] are loaded once for all of them and the outputs' sums run as
     // independent chains (the same arithmetic per output as the general loops)
-    const bool shared_col = OWN <= 4 && nth % R == 0 && mc * R <= OWN * nth;
+    const bool shared_col = SC || (OWN <= 4 && nth % R == 0 && mc * R <= OWN * nth);
     if (shared_col) {
       const int cc = tid % R, q0 = tid / R, step = nth / R;
       float2 a0[OWN], a1[OWN];
@@ -971,7 +972,7 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k, int f
       ic[o] = v ? ocol[o] : 0;
     }
     int mm = 0;
-    if (OWN <= 4 && nth % R == 0) {
+    if (SC || (OWN <= 4 && nth % R == 0)) {
       const int cc = tid % R;
       for (; mm + 1 < mc; mm += 2) {
         const float2 qa = QC[mm * R + cc], qb = QC[(mm + 1) * R + cc];
@@ -1019,7 +1020,7 @@ __device__ void step_solve_A(const FrameParams& p, SM& sm, int cta, int k, int f
   }
   __syncthreads();
   // partial sums over this CTA's rows: Ahat'_S[m][r] and ||a'_r||^2
-  partials_A(p, sm, cta, TW, one_chunk);
+  partials_A<SC>(p, sm, cta, TW, one_chunk);
 }
 
 // sum of C per-CTA partials stride apart, loads issued four at a time
@@ -1186,7 +1187,7 @@ __device__ void reduce_A_full(const FrameParams& p, SM& sm, int cta, int dst, fl
 // ---------------------------------------------------------------------------------
 // step B: majorized B step (S2) on this CTA's rows, then partials of B^H B and P
 // ---------------------------------------------------------------------------------
-template <int OWN>
+template <int OWN, bool SC>
 __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last, int fused) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int Ny = p.Ny, R = p.R, C = p.C, MC = p.MC;
@@ -1239,7 +1240,7 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last, 
       ur[o] = vu ? ocol[o] : 0;
     }
     const float2* AHm = own_ah ? AR : AH;
-    if (OWN <= 4 && nth % R == 0) {
+    if (SC || (OWN <= 4 && nth % R == 0)) {
       // every output of this thread has column tid % R (R divides the block): that column's
       // entry of Ahat is loaded once per m for all of them (same arithmetic as below)
       const int cc = tid % R;
@@ -1283,7 +1284,7 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last, 
     nbv[o].x = fmaf(-c2, grad.x, fmaf(c1, b.x, c0 * b0.x));
     nbv[o].y = fmaf(-c2, grad.y, fmaf(c1, b.y, c0 * b0.y));
   };
-  if (OWN <= 4 && nth % R == 0) {
+  if (SC || (OWN <= 4 && nth % R == 0)) {
     // column tid % R for every output: gMA[q][r] loaded once per q for all of them, the
     // sums of all outputs as independent chains (same arithmetic as below)
     const int cc = tid % R;
@@ -1380,7 +1381,7 @@ __device__ void reduce_sums(const FrameParams& p, SM& sm, int cta, bool ma) {
 }
 
 // Steps [step_begin, step_end) of one frame, run by CTA `cta` of the cluster that owns it.
-template <int OWN, bool LOADS_FIRST>
+template <int OWN, bool LOADS_FIRST, bool SC>
 __device__ __forceinline__ void frame_run(const FrameParams& p, unsigned char* smem_raw, int cta, int step_begin,
                                           int step_end, int fused) {
   SM sm = carve(p, smem_raw);
@@ -1446,7 +1447,7 @@ __device__ __forceinline__ void frame_run(const FrameParams& p, unsigned char* s
       }
     }
     if (step == 0) {
-      step_ingest<OWN>(p, sm, cta);
+      step_ingest<OWN, SC>(p, sm, cta);
       __syncthreads();
       continue;
     }
@@ -1466,21 +1467,21 @@ __device__ __forceinline__ void frame_run(const FrameParams& p, unsigned char* s
       continue;
     }
     const int k = (step - 3) / 4, sub = (step - 3) % 4;
-    if (sub == 0) step_solve_A<OWN, LOADS_FIRST>(p, sm, cta, k, fused);
+    if (sub == 0) step_solve_A<OWN, LOADS_FIRST, SC>(p, sm, cta, k, fused);
     else if (sub == 1) reduce_A_rows(p, sm, cta, (k + 1) & 1, k + 1 < p.K);
-    else if (sub == 2) step_B<OWN>(p, sm, cta, k, k == p.K - 1, fused);
+    else if (sub == 2) step_B<OWN, SC>(p, sm, cta, k, k == p.K - 1, fused);
     else reduce_sums(p, sm, cta, !merged);
     __syncthreads();
   }
 }
 
-template <int OWN>
+template <int OWN, bool SC>
 __global__ void __launch_bounds__(TTS_THREADS, 1) frame_kernel(FrameParams p, int step_begin, int step_end,
                                                                int fused) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_release();
   pdl_wait();
-  frame_run<OWN, true>(p, smem_raw, blockIdx.x, step_begin, step_end, fused);
+  frame_run<OWN, true, SC>(p, smem_raw, blockIdx.x, step_begin, step_end, fused);
 }
 
 // Frames of many independent trackers (streams of any Nx, Ny, R) in one persistent
@@ -1508,7 +1509,7 @@ __global__ void __launch_bounds__(TTS_THREADS, 1) frame_batch_kernel(const Frame
     int* dst = (int*)&sp;
     for (int e = threadIdx.x; e < (int)(sizeof(FrameParams) / sizeof(int)); e += blockDim.x) dst[e] = src[e];
     __syncthreads();
-    frame_run<OWN, false>(sp, smem_raw, rank, 0, frame_num_steps(sp.K), 1);
+    frame_run<OWN, false, false>(sp, smem_raw, rank, 0, frame_num_steps(sp.K), 1);
     __syncthreads();
   }
 }
@@ -1595,16 +1596,16 @@ int frame_configure(FrameParams& p, int requested_C, int smem_limit) {
   return TTS_EINVAL;
 }
 
-template <int OWN>
+template <int OWN, bool SC>
 static int launch_frame_t(const FrameParams& p, int launch_mode, cudaStream_t st) {
   static PerDevice attrs;
   int done = 0;
   if (per_device(attrs,
                  [](int, int* v) {
-                   if (cudaFuncSetAttribute(frame_kernel<OWN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                   if (cudaFuncSetAttribute(frame_kernel<OWN, SC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             227 * 1024) != cudaSuccess ||
-                       cudaFuncSetAttribute(frame_kernel<OWN>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-                           cudaSuccess)
+                       cudaFuncSetAttribute(frame_kernel<OWN, SC>, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                            1) != cudaSuccess)
                      return TTS_ECUDA;
                    *v = 1;
                    return TTS_OK;
@@ -1615,11 +1616,11 @@ static int launch_frame_t(const FrameParams& p, int launch_mode, cudaStream_t st
   const int smem = p.lay.bytes;
   const int nsteps = frame_num_steps(p.K);
   if (launch_mode == TTS_LAUNCH_FUSED) {
-    e = launch_pdl(frame_kernel<OWN>, dim3(p.C), dim3(TTS_THREADS), (size_t)smem, st, p.C, p, 0, nsteps, 1);
+    e = launch_pdl(frame_kernel<OWN, SC>, dim3(p.C), dim3(TTS_THREADS), (size_t)smem, st, p.C, p, 0, nsteps, 1);
     if (e != cudaSuccess) return TTS_ECUDA;
   } else {
     for (int s = 0; s < nsteps; ++s) {
-      frame_kernel<OWN><<<p.C, TTS_THREADS, smem, st>>>(p, s, s + 1, 0);
+      frame_kernel<OWN, SC><<<p.C, TTS_THREADS, smem, st>>>(p, s, s + 1, 0);
       if (cudaGetLastError() != cudaSuccess) return TTS_ECUDA;
     }
   }
@@ -1636,11 +1637,15 @@ int frame_own(const FrameParams& p) {
 }
 
 int launch_frame(const FrameParams& p, int launch_mode, cudaStream_t st) {
+  // R dividing the block and R <= 32: every output a thread owns in the factor-sized loops
+  // has the same column, so the kernel is compiled with only the shared-column form of them
+  // (the others keep both forms and choose at run time)
+  const bool sc = TTS_THREADS % p.R == 0 && p.R <= 32;
   switch (frame_own(p)) {
-    case 1: return launch_frame_t<1>(p, launch_mode, st);
-    case 2: return launch_frame_t<2>(p, launch_mode, st);
-    case 4: return launch_frame_t<4>(p, launch_mode, st);
-    default: return launch_frame_t<8>(p, launch_mode, st);
+    case 1: return sc ? launch_frame_t<1, true>(p, launch_mode, st) : launch_frame_t<1, false>(p, launch_mode, st);
+    case 2: return sc ? launch_frame_t<2, true>(p, launch_mode, st) : launch_frame_t<2, false>(p, launch_mode, st);
+    case 4: return sc ? launch_frame_t<4, true>(p, launch_mode, st) : launch_frame_t<4, false>(p, launch_mode, st);
+    default: return launch_frame_t<8, false>(p, launch_mode, st);
   }
 }
 
