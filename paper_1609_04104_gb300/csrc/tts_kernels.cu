@@ -195,20 +195,122 @@ __device__ __forceinline__ void sampler_scores_band(const float2* __restrict__ A
   }
 }
 
-// scores for one band-shape length: up to blockDim / T columns per pass (T threads each)
+// The same scores with the T = 16 threads of a column in 16 different warps, one column per
+// lane (T warps, up to 32 columns a pass): every load of A is a coalesced piece of a row, the
+// transpose goes through the column's region of shared memory (stride N + 1, so that the 32
+// columns of a warp fall on different banks) with a CTA barrier, and the column norm is summed
+// through shared memory (red, T x 32 floats) in the order of the shuffle butterfly of
+// sampler_scores_band, so the weights are bit-identical to it.
+template <int N>
+__device__ __forceinline__ void sampler_scores_lanes(const float2* __restrict__ A, int R, int no_fft,
+                                                     const float2* W, float2* buf, float* rowacc, int cols,
+                                                     float* red) {
+  using fftband::Shape;
+  constexpr int T = Shape<N>::T, RL = Shape<N>::R, J = (RL + T - 1) / T, CS = N + 1;
+  static_assert(T == 16, "one warp per thread of a column");
+  constexpr int WS = N + 16;
+  float* Wt = (float*)(buf + cols * CS);
+  const int tid = threadIdx.x, t = tid >> 5, c = tid & 31;
+  for (int r0 = 0; r0 < R; r0 += cols) {
+    const int nc = min(cols, R - r0);
+    const bool act = c < nc;
+    float2 v[RL];
+    float2 u[J][T];
+    float s = 0.f;
+    if (act) {
+#pragma unroll
+      for (int n2 = 0; n2 < RL; ++n2) v[n2] = A[(size_t)(t + T * n2) * R + r0 + c];
+    }
+    if (no_fft) {
+      if (act) {
+#pragma unroll
+        for (int n2 = 0; n2 < RL; ++n2) s += cabs2(v[n2]);
+      }
+    } else {
+      float2* sc = buf + c * CS;
+      if (act) {
+        fftband::dft_small<RL, false>(v, W, N);
+#pragma unroll
+        for (int k2 = 1; k2 < RL; ++k2) v[k2] = cmul(v[k2], fftsmall::twn<false>(W, t * k2));
+#pragma unroll
+        for (int k2 = 0; k2 < RL; ++k2) sc[k2 * T + (t ^ (k2 % T))] = v[k2];
+      }
+      __syncthreads();
+      if (act) {
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const int k2 = t + T * j;
+          if (J * T == RL || k2 < RL) {
+#pragma unroll
+            for (int n1 = 0; n1 < T; ++n1) u[j][n1] = sc[k2 * T + (n1 ^ (k2 % T))];
+            fftband::dft_small<T, false>(u[j], W, N);
+#pragma unroll
+            for (int k1 = 0; k1 < T; ++k1) s += cabs2(u[j][k1]);
+          }
+        }
+      }
+    }
+    // column norm: the butterfly x1[i] = s[i] + s[i ^ 8], x2[i] = x1[i] + x1[i ^ 4], ... of
+    // the 16 per-thread sums, whose value is the same for every i
+    red[t * 32 + c] = s;
+    __syncthreads();
+    float x[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = red[i * 32 + c];
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1)
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (i < o) x[i] = x[i] + x[i + o];   // x[i] for i < o holds the value of both i and i + o
+    const float tot = x[0];
+    const float inv = tot > 0.f ? 1.f / tot : 0.f;
+    if (act) {
+      float* wrow = Wt + c * WS;
+      if (no_fft) {
+#pragma unroll
+        for (int n2 = 0; n2 < RL; ++n2) wrow[t + T * n2] = inv > 0.f ? cabs2(v[n2]) * inv : 1.f / (float)N;
+      } else {
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const int k2 = t + T * j;
+          if (J * T == RL || k2 < RL) {
+#pragma unroll
+            for (int k1 = 0; k1 < T; ++k1) wrow[k2 + RL * k1] = inv > 0.f ? cabs2(u[j][k1]) * inv : 1.f / (float)N;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    for (int k = tid; k < N; k += blockDim.x) {
+      float acc = rowacc[k];
+      for (int cc = 0; cc < nc; ++cc) acc += Wt[cc * WS + k];
+      rowacc[k] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// scores for one band-shape length: up to blockDim / T columns per pass (T threads each); for
+// the 16-thread shapes with 16 warps, one column per lane instead (coalesced loads of A)
 template <int N>
 __device__ __forceinline__ void sampler_scores_for(const float2* A, int R, int no_fft, const float2* W, float2* buf,
-                                                   float* rowacc, int fft_cols) {
+                                                   float* rowacc, int fft_cols, float* red) {
+  if constexpr (fftband::Shape<N>::T == 16) {
+    if (blockDim.x == 512) {
+      sampler_scores_lanes<N>(A, R, no_fft, W, buf, rowacc, min(min(32, R), fft_cols), red);
+      return;
+    }
+  }
   const int cols = min(min((int)blockDim.x / fftband::Shape<N>::T, R), fft_cols);
   sampler_scores_band<N>(A, R, no_fft, W, buf, rowacc, cols);
 }
 
 // the band-shape lengths: scores through sampler_scores_band; false for any other Nx
 __device__ __forceinline__ bool sampler_scores_fast(int Nx, const float2* A, int R, int no_fft, const float2* W,
-                                                    float2* buf, float* rowacc, int fft_cols) {
+                                                    float2* buf, float* rowacc, int fft_cols, float* red) {
   switch (Nx) {
 #define SCORES(N) \
-  case N: sampler_scores_for<N>(A, R, no_fft, W, buf, rowacc, fft_cols); return true;
+  case N: sampler_scores_for<N>(A, R, no_fft, W, buf, rowacc, fft_cols, red); return true;
     SCORES(64) SCORES(96) SCORES(120) SCORES(128) SCORES(144) SCORES(160) SCORES(192) SCORES(200) SCORES(216)
     SCORES(240) SCORES(256) SCORES(288) SCORES(320) SCORES(384)
 #undef SCORES
@@ -252,7 +354,8 @@ __device__ __forceinline__ void sampler_run(const SamplerJob& job, unsigned char
     __syncthreads();
     const FftPlan plan = fft_plan(Nx);
     const int ld = fsz(Nx) | 1;   // padded column stride (odd) in shared memory
-    const bool fast = sampler_scores_fast(Nx, A, R, job.no_fft, W, buf, rowacc, fft_cols);
+    // p (probabilities, written after the scores) serves as the scores' reduction scratch
+    const bool fast = sampler_scores_fast(Nx, A, R, job.no_fft, W, buf, rowacc, fft_cols, (float*)p);
     for (int r0 = 0; r0 < (fast ? 0 : R); r0 += fft_cols) {
       const int nc = min(fft_cols, R - r0);
       // coalesced along the rows of A, transposed into columns
