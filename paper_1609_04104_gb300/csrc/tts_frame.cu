@@ -299,10 +299,11 @@ __device__ __noinline__ void gj_inverse_warps(const float2* G, int R, float2* Gi
     for (int q = 0; q < CPL; ++q) Gi[(warp * RW + r) * LD + lane + 32 * q] = M[r][q];
 }
 
-// sum over the 8 lanes of a row group (lanes 8g .. 8g+7) of a float2
-__device__ __forceinline__ float2 sum8(float2 v) {
+// sum over the TPR lanes of a row group (lanes TPR g .. TPR g + TPR - 1) of a float2
+template <int TPR>
+__device__ __forceinline__ float2 sum_group(float2 v) {
 #pragma unroll
-  for (int o = 4; o > 0; o >>= 1) {
+  for (int o = TPR / 2; o > 0; o >>= 1) {
     v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
     v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
   }
@@ -319,8 +320,8 @@ __device__ __forceinline__ float2 sum8(float2 v) {
 template <int RP>
 __device__ bool ridge_refine(SM& sm, int R, const float2* Gi, const float2* Glo, const float2* hlo, int iters,
                              float tol2, float slow2) {
-  constexpr int LD = RP + 8;
-  const int tid = threadIdx.x, i = tid >> 3, u = tid & 7;
+  constexpr int LD = RP + 8, TPR = 8;   // 16 a row for R <= 32 measured slower
+  const int tid = threadIdx.x, i = tid / TPR, u = tid % TPR;
   const bool row = i < R;
   // three (max |delta|^2, max |gamma|^2) pairs used in turn: sweep `it` reads pair it % 3
   // after its last barrier and clears pair (it + 1) % 3, last read two sweeps earlier
@@ -330,8 +331,8 @@ __device__ bool ridge_refine(SM& sm, int R, const float2* Gi, const float2* Glo,
   {
     float2 acc = make_float2(0.f, 0.f);
     if (row)
-      for (int j = u; j < R; j += 8) cfma(acc, Gi[i * LD + j], sm.h[j]);
-    acc = sum8(acc);
+      for (int j = u; j < R; j += TPR) cfma(acc, Gi[i * LD + j], sm.h[j]);
+    acc = sum_group<TPR>(acc);
     if (row && u == 0) {
       sm.gam[i] = acc;
       sm.glo[i] = make_float2(0.f, 0.f);
@@ -344,7 +345,7 @@ __device__ bool ridge_refine(SM& sm, int R, const float2* Gi, const float2* Glo,
     // r = h - G gamma, every product exact (two_prod), sums in float-float
     float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
     if (row)
-      for (int j = u; j < R; j += 8) {
+      for (int j = u; j < R; j += TPR) {
         const float2 g = sm.Gf[i * R + j];
         const float2 x = sm.gam[j], xl = sm.glo[j];
         float pp, e;
@@ -362,7 +363,7 @@ __device__ bool ridge_refine(SM& sm, int R, const float2* Gi, const float2* Glo,
         ff_add_f(ih, il, cc.y);
       }
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1) {
+    for (int o = TPR / 2; o > 0; o >>= 1) {
       const float a = __shfl_xor_sync(0xffffffffu, rh, o), b = __shfl_xor_sync(0xffffffffu, rl, o);
       const float c = __shfl_xor_sync(0xffffffffu, ih, o), d = __shfl_xor_sync(0xffffffffu, il, o);
       ff_add_ff(rh, rl, a, b);
@@ -380,8 +381,8 @@ __device__ bool ridge_refine(SM& sm, int R, const float2* Gi, const float2* Glo,
     // gamma += Ginv r
     float2 acc = make_float2(0.f, 0.f);
     if (row)
-      for (int j = u; j < R; j += 8) cfma(acc, Gi[i * LD + j], sm.rr[j]);
-    acc = sum8(acc);
+      for (int j = u; j < R; j += TPR) cfma(acc, Gi[i * LD + j], sm.rr[j]);
+    acc = sum_group<TPR>(acc);
     if (row && u == 0) {
       float2 g = sm.gam[i], gl = sm.glo[i];
       atomicMax(fl, __float_as_uint(cabs2(acc)));
@@ -1156,17 +1157,19 @@ __device__ void reduce_A_full(const FrameParams& p, SM& sm, int cta, int dst, fl
   if (!ma) return;
   const int RT = R * (R + 1) / 2;
   const Slice ps = slice_of(RT, C, cta);
-  const int g = tid >> 3, u = tid & 7;
-  for (int base = ps.lo; base < ps.hi; base += nth / 8) {   // uniform trip count
+  // eight threads a pair when the slice fits one pass of the block that way, else four (one
+  // pass for up to nth / 4 pairs: 66 at R = 32 with 8 CTAs)
+  const int tpp = ps.hi - ps.lo <= nth / 8 ? 8 : 4;
+  const int g = tid / tpp, u = tid % tpp;
+  for (int base = ps.lo; base < ps.hi; base += nth / tpp) {   // uniform trip count
     const int idx = base + g;
     const bool valid = idx < ps.hi;
     int q = 0, r = 0;
     if (valid) tri_pair(idx, R, q, r);
     CFF acc = cff_zero();
     if (valid)
-      for (int m = u; m < s; m += 8) cff_macc(acc, AR[m * R + q], AR[m * R + r]);
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1) {
+      for (int m = u; m < s; m += tpp) cff_macc(acc, AR[m * R + q], AR[m * R + r]);
+    for (int o = tpp >> 1; o > 0; o >>= 1) {
       const float a = __shfl_xor_sync(0xffffffffu, acc.rh, o), b = __shfl_xor_sync(0xffffffffu, acc.rl, o);
       const float c = __shfl_xor_sync(0xffffffffu, acc.ih, o), d = __shfl_xor_sync(0xffffffffu, acc.il, o);
       ff_add_ff(acc.rh, acc.rl, a, b);
@@ -1214,8 +1217,10 @@ __device__ void step_B(const FrameParams& p, SM& sm, int cta, int k, bool last, 
   float2* AR = sm.chunk + MC * R;
   if (merged) reduce_A_full(p, sm, cta, (k + 1) & 1, AR, p.jacobi ? nullptr : nAs, k + 1 < p.K);
   const bool own_ah = merged && !p.jacobi;   // the reduced rows are this step's Ahat
+  // gamma: in a fused launch every CTA still holds the one it solved for (the same in all
+  // CTAs); a launch per step reads CTA 0's copy
   for (int r = tid; r < R; r += nth) {
-    sm.gam[r] = p.gamma[r];
+    if (!fused) sm.gam[r] = p.gamma[r];
     if (!own_ah) nAs[r] = nA[r];
   }
   // MA = Ahat^H Ahat (thread-owned entries) and U[j][r] = sum_m Yt[m][j] conj(Ahat[m][r])
