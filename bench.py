@@ -329,6 +329,13 @@ def run_tts(args, rank, world):
         full = np.ones(w.Nx, np.uint8)
         copy_stream = torch.cuda.Stream()
         img_ready = [torch.cuda.Event() for _ in range(T)]
+        # the C ABI called directly (as a scanner's control loop would), with the buffer
+        # addresses taken once: between a line draw and the frame's launch only the two calls
+        lib, h = tts.load(), trk.h
+        mh_p = mh.ctypes.data
+        yp_p = [Yp[t].ctypes.data for t in range(T)]
+        dimg_p = [dimg[t].data_ptr() for t in range(T)]
+        push_flags = tts.TTS_FULL_FRAME | tts.TTS_HOST_PINNED
         e2e_s, h2d, d2h = [], 0, 0
         for it in range(args.warmup + args.steps):
             reset()
@@ -341,11 +348,11 @@ def run_tts(args, rank, world):
                         trk.push_frame(Yp[t], full, full_frame=True, pinned=True)
                         hb += w.Nx * w.Ny * 8 + w.Nx
                     else:
-                        trk.next_mask(w.rate, seed, out=mh)
+                        tts._check(lib.tts_next_mask(h, w.rate, seed, mh_p, 0))
+                        tts._check(lib.tts_push_frame(h, yp_p[t], None, push_flags))   # the lines just drawn
                         db += w.Nx
-                        trk.push_frame(Yp[t], None, full_frame=True, pinned=True)   # the lines just drawn
                         hb += int(mh.sum()) * w.Ny * 8
-                    tts.tts_image(trk.h, t, dimg[t])
+                    tts._check(lib.tts_image(h, t, dimg_p[t], tts.TTS_DEVICE_PTRS))
                     img_ready[t].record(stream)
                     copy_stream.wait_event(img_ready[t])
                     with torch.cuda.stream(copy_stream):
@@ -357,7 +364,8 @@ def run_tts(args, rank, world):
                 h2d, d2h = hb, db
         e2e = {"value": T * world / float(np.mean(e2e_s)), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h,
-               "note": "host lines back every frame (synchronous); host frames in (page-locked, the "
+               "note": "C ABI calls from Python (ctypes) with host buffers: the lines back to the host "
+                       "every frame (the call waits for the draw); host frames in (page-locked, the "
                        "acquired rows read by the kernels in place, TTS_HOST_PINNED); images out "
                        "on a copy stream"}
 
