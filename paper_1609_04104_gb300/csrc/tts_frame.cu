@@ -26,6 +26,7 @@
 
 #include <algorithm>
 
+#include "tts_fft_band.cuh"
 #include "tts_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -620,6 +621,61 @@ __device__ void partials_B(const FrameParams& p, SM& sm, int cta, bool do_mb, bo
   }
 }
 
+// Rows [lo, hi) of S transformed by the register four-step FFT of the batched 2D DFT (line
+// length N with a band shape): Yt[m] = y_m conj(F_N) / sqrt(N), T threads a row, as many rows a
+// pass as there are thread groups and room in sm.chunk; bad |= 1 on a non-finite sample.
+template <int N>
+__device__ void rows_band(const FrameParams& p, SM& sm, int lo, int hi, int& bad) {
+  using fftband::Shape;
+  constexpr int T = Shape<N>::T, RL = Shape<N>::R, J = (RL + T - 1) / T;
+  const int g = threadIdx.x / T, t = threadIdx.x % T;
+  const int per = min((int)blockDim.x / T, p.lay.chunk_f2 / N);
+  const unsigned gmask = ((1u << T) - 1u) << ((threadIdx.x & 31) & ~(T - 1));
+  for (int m0 = lo; m0 < hi; m0 += per) {
+    const int m = m0 + g;
+    if (g < per && m < hi) {   // uniform over the row's T threads
+      const float2* src = p.yrows + (p.full_frame ? (size_t)sm.rows[m] * N : (size_t)m * N);
+      float2 v[RL];
+#pragma unroll
+      for (int n2 = 0; n2 < RL; ++n2) v[n2] = src[t + T * n2];
+#pragma unroll
+      for (int n2 = 0; n2 < RL; ++n2)
+        if (!isfinite(v[n2].x) || !isfinite(v[n2].y)) bad = 1;
+      float2* sc = sm.chunk + g * N;
+      fftband::dft_small<RL, true>(v, sm.Wy, N);
+#pragma unroll
+      for (int k2 = 1; k2 < RL; ++k2) v[k2] = cmul(v[k2], fftsmall::twn<true>(sm.Wy, t * k2));
+#pragma unroll
+      for (int k2 = 0; k2 < RL; ++k2) sc[k2 * T + (t ^ (k2 % T))] = v[k2];
+      __syncwarp(gmask);
+      float2* d = p.Yt + (size_t)m * N;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int k2 = t + T * j;
+        if (J * T == RL || k2 < RL) {
+          float2 u[T];
+#pragma unroll
+          for (int n1 = 0; n1 < T; ++n1) u[n1] = sc[k2 * T + (n1 ^ (k2 % T))];
+          fftband::dft_small<T, true>(u, sm.Wy, N);
+#pragma unroll
+          for (int k1 = 0; k1 < T; ++k1) d[k2 + RL * k1] = cscale(u[k1], p.isy);
+        }
+      }
+    }
+    __syncthreads();   // the scratch rows are free for the next pass
+  }
+}
+
+// the band-shape line lengths of the common cine sizes: rows by rows_band; false otherwise
+__device__ __forceinline__ bool rows_band_any(const FrameParams& p, SM& sm, int lo, int hi, int& bad) {
+  switch (p.Ny) {
+    case 128: rows_band<128>(p, sm, lo, hi, bad); return true;
+    case 192: rows_band<192>(p, sm, lo, hi, bad); return true;
+    case 256: rows_band<256>(p, sm, lo, hi, bad); return true;
+    default: return false;
+  }
+}
+
 // ---------------------------------------------------------------------------------
 // step 0: ingest the frame: inverse row transforms of this CTA's slice of S (Yt), the
 // anchors A[t-1], B[t-1], and partial sums of Ahat_S, ||a||^2 and B^H B over this CTA's rows
@@ -638,7 +694,8 @@ __device__ void step_ingest(const FrameParams& p, SM& sm, int cta) {
       const float2 v = p.Yt[e];
       if (!isfinite(v.x) || !isfinite(v.y)) bad = 1;
     }
-  for (int m0 = ms.lo; m0 < ms.hi && !p.yt_ready; m0 += fft_rows) {
+  const bool band = !p.yt_ready && !p.kspace && rows_band_any(p, sm, ms.lo, ms.hi, bad);
+  for (int m0 = ms.lo; m0 < ms.hi && !p.yt_ready && !band; m0 += fft_rows) {
     const int nr = min(fft_rows, ms.hi - m0);
     float2* buf = sm.chunk;
     float2* tmp = sm.chunk + fft_rows * bsy;
@@ -674,12 +731,12 @@ __device__ void step_ingest(const FrameParams& p, SM& sm, int cta) {
   // a tensor-core row transform whose bounded wait ran out left Yt invalid: skip the frame
   if (p.yt_ready && ((volatile int*)p.status)[2 + TTS_MAX_CLUSTER]) bad |= 2;
   if (bad) atomicOr(&sm.misc[1], bad);
-  // anchors A[t-1], B[t-1]
+  // anchors A[t-1], B[t-1] (the rows this CTA holds in shared memory)
   for (int e = tid; e < p.rA * R; e += nth) sm.A0[e] = sm.A[e];
   for (int e = tid; e < p.rB * R; e += nth) sm.B0[e] = sm.B[e];
   const Slice as = slice_of(Nx, C, cta), bs = slice_of(Ny, C, cta);
-  for (int e = as.lo * R + tid; e < as.hi * R; e += nth) p.A0[e] = p.A[e];
-  for (int e = bs.lo * R + tid; e < bs.hi * R; e += nth) p.B0[e] = p.B[e];
+  for (int e = tid; e < (as.hi - as.lo) * R; e += nth) p.A0[as.lo * R + e] = sm.A[e];
+  for (int e = tid; e < (bs.hi - bs.lo) * R; e += nth) p.B0[bs.lo * R + e] = sm.B[e];
   partials_A<SC>(p, sm, cta, sm.chunk, false);
   partials_B<OWN>(p, sm, cta, true, false, p.ridge_ff_all || p.K == 1);
   __syncthreads();
