@@ -235,7 +235,8 @@ int tts_set_coil_maps(tts_handle* h, const tts_c64* maps, int C, int flags);
  * (host, or device with TTS_DEVICE_PTRS) and keeps the mask for tts_push_frame(NULL).
  * rate must lie in (0, 1]. A host line_mask_out is filled before the call returns: the call
  * waits for the draw itself (a completion word the kernel sets in mapped host memory), not for
- * the whole stream; errors of earlier work surface at the next synchronising call. */
+ * the whole stream; errors of earlier work surface at the next synchronising call. A host
+ * line_mask_out while the handle's stream is being captured is refused (TTS_ESTATE). */
 int tts_next_mask(tts_handle* h, double rate, uint64_t seed, uint8_t* line_mask_out, int flags);
 
 /* The line probabilities p (Nx doubles) that tts_next_mask would draw from now: the

@@ -563,6 +563,14 @@ int tts_next_mask(tts_handle* h, double rate, uint64_t seed, uint8_t* line_mask_
   const int Nx = h->cfg.Nx;
   const int k_lines = handle_k_lines(h, rate);
   const bool host = !(flags & TTS_DEVICE_PTRS);
+  if (host) {
+    // a host mask is a wait for the draw, which a stream being captured never runs
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+      cudaGetLastError();
+      return fail(TTS_ESTATE, "a host line mask cannot be drawn while the stream is captured%s");
+    }
+  }
   if (host && !h->mask_map) {
     uint8_t* m = nullptr;
     void* d = nullptr;
