@@ -25,6 +25,10 @@ TTS_ROWDFT_FFT, TTS_ROWDFT_BF16X3, TTS_ROWDFT_BF16 = 0, 1, 2
 TTS_DEVICE_PTRS = 1
 TTS_FULL_FRAME = 2
 TTS_HOST_PINNED = 4
+TTS_MAX_COILS = 64
+TTS_NOALLOC_MAX_N = 256
+TTS_NOALLOC_MAX_R = 32
+TTS_NOALLOC_SCRATCH_BYTES = 4 << 20
 TTS_POLICY_UNIFORM, TTS_POLICY_VARDENS, TTS_POLICY_INFORMATIVE = 0, 1, 2
 TTS_UPDATE_GAUSS_SEIDEL, TTS_UPDATE_JACOBI = 0, 1
 TTS_LAUNCH_FUSED, TTS_LAUNCH_PHASES = 0, 1

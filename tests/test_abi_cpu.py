@@ -33,6 +33,24 @@ def test_library_exports_every_declared_entry_point(lib):
     assert sorted(tts.EXPORTS) == names
 
 
+def test_binding_constants_match_the_header():
+    """Every TTS_* constant of include/tts.h (#define or enum) has the same value in the
+    Python binding, so flags and limits passed through it mean what the library reads."""
+    from paper_1609_04104_gb300 import tts
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "tts.h")).read(), flags=re.S)
+    consts = {}
+    for name, expr in re.findall(r"#define\s+(TTS_[A-Z0-9_]+)\s+([^\n]+)", src):
+        expr = expr.strip()
+        m = re.fullmatch(r"\(?\s*(\d+)u?\s*(?:<<\s*(\d+))?\s*\)?", expr)
+        if m:
+            consts[name] = int(m.group(1)) << int(m.group(2) or 0)
+    for name, val in re.findall(r"\b(TTS_[A-Z0-9_]+)\s*=\s*(-?\d+)", src):
+        consts[name] = int(val)
+    assert len(consts) >= 30
+    for name, val in consts.items():
+        assert getattr(tts, name) == val, name
+
+
 def test_config_validation_runs_before_any_cuda_call():
     from paper_1609_04104_gb300 import tts
     for bad in (dict(Nx=7), dict(Nx=0), dict(Ny=600), dict(R=0), dict(R=65), dict(lambda_forget=0.0),
