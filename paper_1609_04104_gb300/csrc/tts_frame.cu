@@ -259,7 +259,9 @@ __device__ __noinline__ void gj_inverse_warps(const float2* G, int R, float2* Gi
       float2 d;
       d.x = __shfl_sync(FULL, dk.x, kl);
       d.y = __shfl_sync(FULL, dk.y, kl);
-      const float inv = __frcp_rn(cabs2(d));
+      // approximate reciprocal: the inverse is only the refinement's preconditioner, and
+      // this is on the dependent chain of the 32 pivot steps (pivots >= mu, never subnormal)
+      const float inv = __fdividef(1.0f, cabs2(d));
       const float2 piv = make_float2(d.x * inv, -d.y * inv);   // 1 / d
 #pragma unroll
       for (int q = 0; q < CPL; ++q) {
