@@ -202,8 +202,9 @@ int tts_get_config(tts_handle* h, tts_config* cfg);
  * With TTS_FULL_FRAME, y_rows is a full Nx x Ny frame of which only the acquired rows
  * are read. Host rows are gathered (and checked) into pinned memory of the handle, which the
  * kernels read in place (mapped) or which is copied in one transfer, so y_rows may be
- * pageable and is free again when the call returns. Asynchronous with TTS_DEVICE_PTRS (the buffers must stay valid until the
- * stream passes this work). */
+ * pageable and is free again when the call returns; with TTS_HOST_PINNED the kernels read
+ * page-locked caller memory in place instead (see there). Asynchronous with TTS_DEVICE_PTRS
+ * (the buffers must stay valid until the stream passes this work). */
 int tts_push_frame(tts_handle* h, const tts_c64* y_rows, const uint8_t* line_mask, int flags);
 
 /* Reconstructed frame X_t = A[t] diag(gamma_t) B[t]^T (Nx x Ny, row-major; the
