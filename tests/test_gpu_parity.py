@@ -150,6 +150,21 @@ def test_small_cine_jacobi(tts):
     assert nrmse_per_frame(got, ref).max() < NRMSE_TOL
 
 
+@pytest.mark.parametrize("Nx,Ny,R", [(128, 128, 16), (64, 192, 12)])
+def test_band_row_transform_lengths(tts, Nx, Ny, R):
+    """Line lengths whose acquired rows the frame kernel transforms with the register
+    four-step FFT (Ny = 128: eight threads a row; 192: sixteen; 256 is the cine workload),
+    fully sampled and undersampled frames, against the FP64 oracle."""
+    w = inputs.Workload(name="band", Nx=Nx, Ny=Ny, R=R, T=5, n_ellipses=4, sigma=0.01, lambda_forget=0.9,
+                        mu=1e-2, mm_iters=2, policy="uniform", rate=0.25, central_lines=8, seed=5)
+    L, Y, A0, B0 = workload_inputs(w, w.T)
+    masks = inputs.uniform_line_masks(w)
+    masks[0] = 1
+    ref, _, _ = run_oracle(w, w.T, Y, A0, B0, masks=masks)
+    _, got = run_gpu(tts, w, w.T, Y, A0, B0, masks)
+    assert nrmse_per_frame(got, ref).max() < NRMSE_TOL
+
+
 @pytest.mark.parametrize("Nx,Ny,R,K,C", [(60, 45, 5, 2, 4), (30, 50, 1, 3, 2), (64, 32, 33, 2, 8),
                                          (48, 40, 48, 1, 16), (40, 24, 64, 2, 5), (16, 16, 3, 4, 16)])
 def test_ragged_shapes(tts, Nx, Ny, R, K, C):
