@@ -469,6 +469,19 @@ def oracle_sample(n_frames, probs=False):
     return el, imgs, masks, ps, Y, A0, B0
 
 
+def oracle_single_thread(n_frames):
+    """Frames per second of the FP64 oracle on one host core: oracle_sample(n_frames) in a
+    fresh interpreter (fork and exec, no CUDA) whose BLAS is limited to one thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", VECLIB_MAXIMUM_THREADS="1")
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps({'el': bench.oracle_sample(%d)[0]}))" % (ROOT, n_frames))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return n_frames / json.loads(r.stdout.strip().splitlines()[-1])["el"]
+
+
 def image_errors(x, ref):
     """Per-frame NRMSE and worst-element error max|x - ref| / max|ref|."""
     return (float(np.linalg.norm(x - ref) / np.linalg.norm(ref)),
@@ -497,6 +510,13 @@ def cpu_baseline(args, T, record=None, launch=0, cluster=0):
            "sample": f"frames 0-{n - 1} of the {w.T}-frame 256x256 R=32 sequence ({min(n, w.warmup_frames)} "
                      f"fully sampled warm-up frames, the rest at 32/256 lines drawn by the oracle); numpy FP64, "
                      f"dense DFT matrices, BLAS on all host cores; timed: frame updates and draws"}
+    n1 = min(T, 10)
+    try:
+        res["single_thread"] = {"value": oracle_single_thread(n1), "unit": UNIT, "cores": 1,
+                                "sample": f"frames 0-{n1 - 1} ({min(n1, w.warmup_frames)} fully sampled) of the "
+                                          f"same sequence, the oracle in its own process with BLAS on one thread"}
+    except Exception as e:   # the one-core figure is context; its failure does not void the line
+        res["single_thread"] = {"error": str(e)[-300:]}
     # (a) the oracle's masks fed to both sides
     g = tts.Tracker(w.Nx, w.Ny, w.R, w.lambda_forget, w.mu, mm_iters=w.mm_iters, central_lines=w.central_lines,
                     launch=launch, cluster_ctas=cluster)

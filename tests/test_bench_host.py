@@ -103,3 +103,10 @@ def test_profile_commands_parse_with_the_bench(monkeypatch):
         assert name in summaries, name
         monkeypatch.setattr("sys.argv", ["bench.py", *shlex.split(args)])
         bench.parse()
+
+
+def test_oracle_single_thread_timing_runs_in_its_own_process():
+    """The one-core oracle timing of the cpu_baseline leg: a fresh interpreter with BLAS on
+    one thread, no CUDA; one fully sampled frame gives a positive rate."""
+    v = bench.oracle_single_thread(1)
+    assert 0.0 < v < 100.0
